@@ -1,0 +1,213 @@
+/*
+ * gs.h - C ABI of the B300 (sm_103a) differentiable tile-based 3D Gaussian
+ * splatting rasterizer of Gaussian-LIC2 (arxiv 2507.04004).
+ *
+ * The library renders RGB, depth and opacity of a Gaussian map at a batch of
+ * camera poses (Sec. "3D Gaussian Splatting Representation": projection,
+ * Eq. alpha, Eq. rendered_rgb, Eq. rendered_depth, Eq. rendered_opacity), with
+ * the tile culling of Sec. "Fast Tile-based Culling", and back-propagates the
+ * depth-regularised loss of Eq. depth_loss (L1 colour term plus the
+ * opacity-normalised sparse LiDAR depth term) to the Gaussian parameters and to
+ * the camera pose (Eq. 3dgs_jacobi under the right perturbation T Exp(xi)).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev, and every array argument unless stated otherwise,
+ *     are device pointers owned by the caller; the library never allocates,
+ *     frees or retains them beyond the call.  gs_map, gs_frame, gs_config and
+ *     gs_workspace are host structs passed by pointer and read during the call.
+ *   - Every call is asynchronous on the given CUDA stream (NULL = legacy
+ *     default stream) and only enqueues work; argument errors are returned
+ *     synchronously and enqueue nothing.  Conditions found on the device
+ *     (pair-buffer overflow) are written to the workspace status word, read
+ *     with gs_read_status() after the stream has been synchronised.
+ *   - Nothing is thrown across the ABI and no device code traps or asserts.
+ *   - Images are planar: rgb is [V][3][H][W], depth/opacity/t_final/n_contrib
+ *     are [V][H][W], row-major, pixel (i, j) sampled at (i + 0.5, j + 0.5).
+ *   - Gaussian parameters are structure-of-arrays, channel-major: mean [3][N],
+ *     log_scale [3][N], quat [4][N] as (w, x, y, z) (normalised inside),
+ *     logit_opacity [N], sh_dc [3][N], sh_rest [K-1][3][N] with
+ *     K = (sh_degree + 1)^2 and the real SH basis (Condon-Shortley phase,
+ *     m = -l..l inside each degree).  SH arrays are FP32, or BF16 when
+ *     sh_bf16 != 0; all arithmetic is FP32.
+ *   - A camera is the world-to-camera transform (row-major R, t) and pinhole
+ *     intrinsics.  All views of one call share width and height.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_ARG = 1,         /* invalid argument (null pointer, size, degree, ...) */
+  GS_ERR_CAPACITY = 2,    /* (device status) pair buffer too small; see gs_read_status */
+  GS_ERR_OOM = 3,         /* reserved for callers' allocators; never returned by the library */
+  GS_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed */
+  GS_ERR_TIMEOUT = 5,     /* (device status) a bounded device wait gave up */
+  GS_ERR_UNSUPPORTED = 6  /* valid request outside the supported envelope */
+} gs_status;
+
+/* One camera; an array of these lives in device memory (64 bytes each). */
+typedef struct {
+  float R[9]; /* world-to-camera rotation, row-major */
+  float t[3]; /* world-to-camera translation */
+  float fx, fy, cx, cy;
+} gs_camera;
+
+/* Gaussian map: host struct holding caller-owned device pointers. */
+typedef struct {
+  int64_t n;              /* number of Gaussians, >= 1, < 2^31 */
+  int32_t sh_degree;      /* 0..3 */
+  int32_t sh_bf16;        /* 0: SH arrays are float, 1: __nv_bfloat16 */
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+  const float* logit_opacity;
+  const void* sh_dc;
+  const void* sh_rest;    /* may be NULL when sh_degree == 0 */
+} gs_map;
+
+/* Batch geometry: n_views images of width x height (1..8192 each). */
+typedef struct {
+  int32_t n_views, width, height;
+} gs_frame;
+
+/* Rasterization constants (readings of the 3DGS rasterizer the paper builds
+ * on): defaults 1/255, 0.99, 1e-4, 0.2, 0.3, 1.3, black background. */
+typedef struct {
+  float alpha_min;  /* skip a Gaussian at a pixel below this alpha; tile culling threshold */
+  float alpha_max;  /* clamp of alpha */
+  float t_min;      /* stop before a Gaussian that would take transmittance below this */
+  float near_z;     /* cut Gaussians whose depth key is <= near_z */
+  float dilation;   /* added to the diagonal of the 2D covariance, px^2 */
+  float fov_clamp;  /* x/z, y/z clamp inside the affine Jacobian, in half fields of view */
+  float bg[3];      /* background colour blended with the final transmittance */
+} gs_config;
+
+/* Workspace: one caller-allocated device buffer of gs_workspace_size() bytes
+ * (256-byte aligned) holding projected Gaussians, tile bins, sort keys, 2D
+ * adjoints and the device status word of one batch geometry.  It is written by
+ * gs_project / gs_bin_sort and read by the later calls of the same batch. */
+typedef struct {
+  void* ptr;
+  int64_t n;              /* Gaussians the workspace was sized for */
+  int64_t pair_capacity;  /* (Gaussian, tile) pairs it can hold, < 2^31 */
+  gs_frame frame;
+} gs_workspace;
+
+/* Byte offsets of the workspace's parts (for inspection and tests). */
+typedef struct {
+  size_t counters;    /* uint32[16]: [0] status, [1] pairs needed, [2] visible entries, [3] long tiles */
+  size_t records;     /* float4[V*N][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
+  size_t rects;       /* uint32[V*N][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
+  size_t adjoints;    /* float4[V*N][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */
+  size_t visible;     /* uint32[V*N]: indices v*N + g of projected Gaussians with a non-empty box */
+  size_t tile_count;  /* uint32[V*T]: pairs per tile, T = ceil(W/16) * ceil(H/16) */
+  size_t tile_start;  /* uint32[V*T]: first pair of each tile in the sorted order */
+  size_t tile_cursor; /* uint32[V*T]: fill cursor used while binning */
+  size_t long_tiles;  /* uint32[V*T]: tiles too long for the single-CTA shared-memory sort */
+  size_t keys;        /* uint64[cap]: (depth key bits << 32 | Gaussian index), binned by tile */
+  size_t keys_alt;    /* uint64[cap]: merge buffer for very long tiles */
+  size_t sorted_ids;  /* uint32[cap]: Gaussian index of each pair, sorted by (tile, depth key, index) */
+  size_t view_stats;  /* float[V][4]: per-view loss accumulators and valid-depth counts */
+  size_t total;       /* bytes */
+} gs_layout;
+
+/* Workspace bytes and layout for n Gaussians, a batch geometry and a pair
+ * capacity.  Return 0 / GS_ERR_ARG on invalid sizes. */
+size_t gs_workspace_size(int64_t n, const gs_frame* frame, int64_t pair_capacity);
+gs_status gs_workspace_layout(int64_t n, const gs_frame* frame, int64_t pair_capacity, gs_layout* out);
+
+/* Copy the workspace status word and pairs-needed counter to the host
+ * (synchronous on the stream).  status_out: GS_OK, or GS_ERR_CAPACITY when the
+ * last gs_bin_sort needed more than pair_capacity pairs (needed in
+ * pairs_needed_out; render outputs of that batch are then invalid). */
+gs_status gs_read_status(const gs_workspace* ws, gs_stream_t stream, int32_t* status_out, int64_t* pairs_needed_out);
+
+/* Projection, colour and tile culling (the equations for mu_hat, mu' and
+ * Sigma' before Eq. alpha; SH colour after Eq. rendered_opacity; Sec. "Fast
+ * Tile-based Culling").  Per (view, Gaussian): mean2d, conic, opacity,
+ * colour, depth, tile box, and the per-tile pair counts.  cams_dev: device
+ * array of frame->n_views cameras.  Clears the workspace status and the 2D
+ * adjoints of every projected Gaussian. */
+gs_status gs_project(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                     gs_stream_t stream);
+
+/* Binning and sorting: exclusive scan of the per-tile counts (tile ranges),
+ * one key (depth key bits << 32 | Gaussian index) per kept (Gaussian, tile)
+ * pair written into its tile's bin, and a sort of every bin, giving the
+ * Gaussians of each tile in (depth key, index) order.  On overflow the status
+ * word becomes GS_ERR_CAPACITY and the later calls of the batch do nothing. */
+gs_status gs_bin_sort(const gs_workspace* ws, gs_stream_t stream);
+
+/* Front-to-back compositing per 16x16 tile (Eq. alpha, Eq. rendered_rgb,
+ * rendered_depth, rendered_opacity): alpha = min(alpha_max, o exp(-q/2)),
+ * skipped below alpha_min, stop before T would fall below t_min.  Outputs:
+ * rgb [V][3][H][W] (with background), depth [V][H][W] (sum d alpha T, not
+ * normalised), opac [V][H][W] (= 1 - T_final), t_final [V][H][W], n_contrib
+ * [V][H][W] (1 + position in the tile list of the last blended Gaussian,
+ * 0 if none).  Any output pointer except t_final and n_contrib may be NULL. */
+gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb, float* depth, float* opac,
+                        float* t_final, uint32_t* n_contrib, gs_stream_t stream);
+
+/* Backward pass (Eq. depth_loss back through Eq. rendered_* and the
+ * projection).  Pixel adjoints are either the fused loss (tgt_rgb != NULL):
+ *   L_v = w_rgb mean_{3HW} |C^ - C| + w_depth / |M_d| sum_{D_s>0, O^>0} |D^/O^ - D_s|,
+ *   |M_d| = #(D_s > 0) per view, L = sum_v L_v, sign(0) = 0;
+ * or the caller's dL/dC^ [V][3][H][W], dL/dD^ [V][H][W], dL/dO^ [V][H][W]
+ * (tgt_rgb == NULL; any of the three may be NULL = zero).  Recomputes each
+ * pixel's blending state back to front from t_final and n_contrib.
+ * Gradients are ADDED to grad_* (caller zeroes them): grad_mean [3][N],
+ * grad_log_scale [3][N], grad_quat [4][N], grad_logit_opacity [N],
+ * grad_sh_dc [3][N], grad_sh_rest [K-1][3][N] (FP32 even for BF16 SH; may be
+ * NULL when sh_degree == 0), grad_pose [V][6] = dL/d(rho, theta) of
+ * T_v Exp(xi) (may be NULL), loss_out [V] (may be NULL; added to). */
+gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                        const float* rgb, const float* depth, const float* opac, const float* t_final,
+                        const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
+                        float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
+                        float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                        float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
+                        gs_stream_t stream);
+
+/* Pose Jacobian rows (Eq. 3dgs_jacobi, right perturbation T Exp(xi),
+ * xi = (rho, theta)): for n_pix listed pixels per view (pix_idx [V][n_pix],
+ * linear index y*W + x, device), J [V][n_pix][3][6] = dC^/dxi by forward-mode
+ * tangents through projection, SH colour and compositing, and the rendered
+ * colour at those pixels in rgb_out [V][n_pix][3] (may be NULL).  Needs the
+ * t_final/n_contrib of gs_render_fwd for the same batch. */
+gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                           const gs_workspace* ws, const int32_t* pix_idx, int32_t n_pix, float* J, float* rgb_out,
+                           gs_stream_t stream);
+
+/* Per-kernel tracing (timing support; no counterpart in the paper).  While
+ * active, each kernel the library launches is bracketed by
+ * cudaEventRecord(events[2k]) / cudaEventRecord(events[2k+1]) on its stream,
+ * k = 0, 1, ... in launch order, and kernel_ids[k] (may be NULL) receives the
+ * kernel's id (see gs_kernel_name).  events: caller-created cudaEvent_t
+ * handles, 2 * capacity of them, owned by the caller; launches beyond
+ * capacity are counted but not recorded.  gs_trace_stop ends tracing and
+ * returns the number of launches seen.  Drive the library from one host
+ * thread while tracing. */
+gs_status gs_trace_start(void* const* events, int32_t capacity, int32_t* kernel_ids);
+int32_t gs_trace_stop(void);
+const char* gs_kernel_name(int32_t id);
+
+/* Static description of a status code. */
+const char* gs_status_str(gs_status s);
+
+/* Library version string ("gsb300 <major>.<minor>"). */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

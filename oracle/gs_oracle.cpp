@@ -377,8 +377,9 @@ struct ViewCache {
   std::vector<int> bx0, bx1;
 };
 
+/* Only the pixel rectangle [rx0, rx0+rw) x [ry0, ry0+rh) is filled in. */
 void build_view(const ocl_map& m, const ocl_camera& cam, const ocl_config& cfg, double margin_eps, bool brute,
-                ViewCache* vc) {
+                int rx0, int ry0, int rw, int rh, ViewCache* vc) {
   const int64_t n = m.n;
   vc->proj.resize(n);
   vc->bx0.assign(n, 0);
@@ -397,8 +398,9 @@ void build_view(const ocl_map& m, const ocl_camera& cam, const ocl_config& cfg, 
       hit = footprint(vc->proj[i], a_lo, cam.width, cam.height, &x0, &x1, &y0, &y1);
     }
     if (!hit) continue;
+    if (x1 < rx0 || x0 >= rx0 + rw) continue;
     vc->bx0[i] = x0; vc->bx1[i] = x1;
-    for (int y = y0; y <= y1; ++y) vc->rows[y].push_back((int32_t)i);
+    for (int y = std::max(y0, ry0); y <= std::min(y1, ry0 + rh - 1); ++y) vc->rows[y].push_back((int32_t)i);
   }
 }
 
@@ -411,16 +413,19 @@ struct PixelState {
   int flags = 0;
 };
 
+/* Candidates are the Gaussians with o exp(-q/2) >= alpha_min in depth-key
+ * order; ones just below the threshold (within margin_eps) are walked too, only
+ * to flag the pixel when such a near-threshold decision comes before the stop. */
 void composite_pixel(const ViewCache& vc, const ocl_config& cfg, int px, int py, double margin_eps, PixelState* st) {
   std::vector<Cand> cand;
   const double cxp = px + 0.5, cyp = py + 0.5;
+  const double a_lo = cfg.alpha_min * (1.0 - margin_eps);
   for (int32_t i : vc.rows[py]) {
     if (px < vc.bx0[i] || px > vc.bx1[i]) continue;
     const Proj<double>& p = vc.proj[i];
     double q = quad_form(p, cxp, cyp);
     double a = p.o * std::exp(-0.5 * q);
-    if (std::fabs(a / cfg.alpha_min - 1.0) <= margin_eps) st->flags |= FLAG_SKIP;
-    if (a >= cfg.alpha_min) cand.push_back({p.depth32, i});
+    if (a >= a_lo) cand.push_back({p.depth32, i});
   }
   std::sort(cand.begin(), cand.end(), [](const Cand& u, const Cand& v) {
     return u.key < v.key || (u.key == v.key && u.gid < v.gid);
@@ -431,6 +436,8 @@ void composite_pixel(const ViewCache& vc, const ocl_config& cfg, int px, int py,
     double q = quad_form(p, cxp, cyp);
     double G = std::exp(-0.5 * q);
     double a_raw = p.o * G;
+    if (std::fabs(a_raw / cfg.alpha_min - 1.0) <= margin_eps) st->flags |= FLAG_SKIP;
+    if (!(a_raw >= cfg.alpha_min)) continue;
     bool clamped = a_raw > cfg.alpha_max;
     if (std::fabs(a_raw / cfg.alpha_max - 1.0) <= margin_eps) st->flags |= FLAG_CLAMP;
     double a = clamped ? cfg.alpha_max : a_raw;
@@ -540,7 +547,7 @@ int32_t ocl_render(const ocl_map* m, const ocl_camera* cam, const ocl_config* cf
                    int32_t h, int32_t brute, double margin_eps, double* rgb, double* depth, double* opac,
                    double* t_final, int32_t* n_contrib, int32_t* last_gid, int32_t* flags) {
   ViewCache vc;
-  build_view(*m, *cam, *cfg, margin_eps, brute != 0, &vc);
+  build_view(*m, *cam, *cfg, margin_eps, brute != 0, x0, y0, w, h, &vc);
   const int64_t hw = (int64_t)w * h;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < h; ++j) {
@@ -594,7 +601,7 @@ int32_t ocl_backward(const ocl_map* m, int32_t n_views, const ocl_camera* cams, 
     const int W = cam.width, H = cam.height;
     const int64_t HW = (int64_t)W * H;
     ViewCache vc;
-    build_view(*m, cam, *cfg, 0.0, false, &vc);
+    build_view(*m, cam, *cfg, 0.0, false, x0, y0, w, h, &vc);
     std::vector<double> adj((size_t)n * kAdj, 0.0);
     double n_depth = 0.0;
     if (tgt_rgb && tgt_depth)
@@ -756,7 +763,7 @@ int32_t ocl_pose_jacobian(const ocl_map* m, const ocl_camera* cam, const ocl_con
                           int32_t n_pix, double* J, double* rgb) {
   const int64_t n = m->n;
   ViewCache vc;
-  build_view(*m, *cam, *cfg, 0.0, false, &vc);
+  build_view(*m, *cam, *cfg, 0.0, false, 0, 0, cam->width, cam->height, &vc);
   std::vector<Proj<Dual<6>>> pd(n);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t gi = 0; gi < n; ++gi) {

@@ -1,0 +1,171 @@
+"""ctypes binding of ``libgsb300.so`` (argument marshalling only).
+
+The entry points keep the C names of ``include/gs.h``.  Loading fails loudly
+when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgsb300.so")
+
+GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(7)
+
+EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
+            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_trace_start", "gs_trace_stop",
+            "gs_kernel_name", "gs_status_str", "gs_version")
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float)]
+
+
+class gs_map(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("sh_bf16", C.c_int32),
+                ("mean", C.c_void_p), ("log_scale", C.c_void_p), ("quat", C.c_void_p),
+                ("logit_opacity", C.c_void_p), ("sh_dc", C.c_void_p), ("sh_rest", C.c_void_p)]
+
+
+class gs_frame(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gs_config(C.Structure):
+    _fields_ = [("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("near_z", C.c_float),
+                ("dilation", C.c_float), ("fov_clamp", C.c_float), ("bg", C.c_float * 3)]
+
+
+class gs_workspace(C.Structure):
+    _fields_ = [("ptr", C.c_void_p), ("n", C.c_int64), ("pair_capacity", C.c_int64), ("frame", gs_frame)]
+
+
+class gs_layout(C.Structure):
+    _fields_ = [(k, C.c_size_t) for k in ("counters", "records", "rects", "adjoints", "visible", "tile_count",
+                                          "tile_start", "tile_cursor", "long_tiles", "keys", "keys_alt",
+                                          "sorted_ids", "view_stats", "total")]
+
+
+class GsError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {status_str(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2507_04004_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, F = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+        L.gs_workspace_size.argtypes = [I64, C.POINTER(gs_frame), I64]
+        L.gs_workspace_size.restype = C.c_size_t
+        L.gs_workspace_layout.argtypes = [I64, C.POINTER(gs_frame), I64, C.POINTER(gs_layout)]
+        L.gs_read_status.argtypes = [C.POINTER(gs_workspace), P, C.POINTER(I32), C.POINTER(I64)]
+        L.gs_project.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace), P]
+        L.gs_bin_sort.argtypes = [C.POINTER(gs_workspace), P]
+        L.gs_render_fwd.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace), P, P, P, P, P, P]
+        L.gs_render_bwd.argtypes = ([C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace)]
+                                    + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P])
+        L.gs_pose_jacobian.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace), P, I32,
+                                       P, P, P]
+        L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
+        L.gs_trace_start.restype = I32
+        L.gs_trace_stop.argtypes = []
+        L.gs_trace_stop.restype = I32
+        L.gs_kernel_name.argtypes = [I32]
+        L.gs_kernel_name.restype = C.c_char_p
+        L.gs_status_str.argtypes = [I32]
+        L.gs_status_str.restype = C.c_char_p
+        L.gs_version.restype = C.c_char_p
+        for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
+                     "gs_pose_jacobian", "gs_workspace_layout"):
+            getattr(L, name).restype = I32
+        _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    return lib().gs_status_str(int(code)).decode()
+
+
+def check(fn: str, code: int) -> None:
+    if code != GS_OK:
+        raise GsError(fn, code)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def gs_workspace_size(n: int, frame: gs_frame, pair_capacity: int) -> int:
+    return int(lib().gs_workspace_size(int(n), C.byref(frame), int(pair_capacity)))
+
+
+def gs_workspace_layout(n: int, frame: gs_frame, pair_capacity: int) -> gs_layout:
+    L = gs_layout()
+    check("gs_workspace_layout", lib().gs_workspace_layout(int(n), C.byref(frame), int(pair_capacity), C.byref(L)))
+    return L
+
+
+def gs_read_status(ws: gs_workspace, stream: int):
+    s, p = C.c_int32(0), C.c_int64(0)
+    check("gs_read_status", lib().gs_read_status(C.byref(ws), C.c_void_p(stream), C.byref(s), C.byref(p)))
+    return int(s.value), int(p.value)
+
+
+def gs_project(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, stream: int) -> None:
+    check("gs_project", lib().gs_project(C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), C.c_void_p(stream)))
+
+
+def gs_bin_sort(ws: gs_workspace, stream: int) -> None:
+    check("gs_bin_sort", lib().gs_bin_sort(C.byref(ws), C.c_void_p(stream)))
+
+
+def gs_render_fwd(cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib, stream: int) -> None:
+    check("gs_render_fwd", lib().gs_render_fwd(C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac),
+                                               _ptr(t_final), _ptr(n_contrib), C.c_void_p(stream)))
+
+
+def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib,
+                  tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale,
+                  grad_quat, grad_logit, grad_sh_dc, grad_sh_rest, grad_pose, loss, stream: int) -> None:
+    check("gs_render_bwd", lib().gs_render_bwd(
+        C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac), _ptr(t_final),
+        _ptr(n_contrib), _ptr(tgt_rgb), _ptr(tgt_depth), C.c_float(w_rgb), C.c_float(w_depth), _ptr(dl_drgb),
+        _ptr(dl_ddepth), _ptr(dl_dopac), _ptr(grad_mean), _ptr(grad_log_scale), _ptr(grad_quat), _ptr(grad_logit),
+        _ptr(grad_sh_dc), _ptr(grad_sh_rest), _ptr(grad_pose), _ptr(loss), C.c_void_p(stream)))
+
+
+def gs_pose_jacobian(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, pix, n_pix: int, J, rgb, stream: int) -> None:
+    check("gs_pose_jacobian", lib().gs_pose_jacobian(C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(pix),
+                                                     int(n_pix), _ptr(J), _ptr(rgb), C.c_void_p(stream)))
+
+
+def gs_trace_start(event_handles, kernel_ids) -> None:
+    """event_handles: list of 2*capacity cudaEvent_t ints; kernel_ids: int32 numpy array of capacity."""
+    arr = (C.c_void_p * len(event_handles))(*event_handles)
+    _trace_keep[:] = [arr, kernel_ids]
+    check("gs_trace_start", lib().gs_trace_start(arr, len(event_handles) // 2, kernel_ids.ctypes.data))
+
+
+def gs_trace_stop() -> int:
+    return int(lib().gs_trace_stop())
+
+
+def gs_kernel_name(i: int) -> str:
+    return lib().gs_kernel_name(int(i)).decode()
+
+
+_trace_keep: list = []
+
+
+def gs_version() -> str:
+    return lib().gs_version().decode()

@@ -1,0 +1,263 @@
+// C ABI of the rasterizer: argument checks, workspace layout, launches.
+// The operations themselves are defined in the header next to each entry
+// point (arxiv 2507.04004 references there).
+#include <cstring>
+
+#include "gs_internal.h"
+
+namespace gsb {
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool frame_ok(const gs_frame* f) {
+  return f && f->n_views >= 1 && f->n_views <= 65535 && f->width >= 1 && f->width <= 8192 && f->height >= 1 &&
+         f->height <= 8192;
+}
+
+static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L) {
+  if (!L || !frame_ok(f) || n < 1 || n >= (int64_t(1) << 31) || cap < 1 || cap >= (int64_t(1) << 31))
+    return GS_ERR_ARG;
+  const int64_t V = f->n_views;
+  const int64_t E = V * n;
+  if (E >= (int64_t(1) << 32)) return GS_ERR_UNSUPPORTED;
+  const int64_t T = (int64_t)((f->width + 15) / 16) * ((f->height + 15) / 16);
+  if (V * T >= (int64_t(1) << 31)) return GS_ERR_UNSUPPORTED;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  L->counters = take(16 * sizeof(uint32_t));
+  L->records = take((size_t)E * 3 * sizeof(float4));
+  L->rects = take((size_t)E * sizeof(uint2));
+  L->adjoints = take((size_t)E * 3 * sizeof(float4));
+  L->visible = take((size_t)E * sizeof(uint32_t));
+  L->tile_count = take((size_t)(V * T) * sizeof(uint32_t));
+  L->tile_start = take((size_t)(V * T) * sizeof(uint32_t));
+  L->tile_cursor = take((size_t)(V * T) * sizeof(uint32_t));
+  L->long_tiles = take((size_t)(V * T) * sizeof(uint32_t));
+  L->keys = take((size_t)cap * sizeof(unsigned long long));
+  L->keys_alt = take((size_t)cap * sizeof(unsigned long long));
+  L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
+  L->view_stats = take((size_t)V * 4 * sizeof(float));
+  L->total = off;
+  return GS_OK;
+}
+
+Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
+  char* b = static_cast<char*>(w->ptr);
+  Ws ws;
+  ws.counters = reinterpret_cast<uint32_t*>(b + L.counters);
+  ws.records = reinterpret_cast<float4*>(b + L.records);
+  ws.rects = reinterpret_cast<uint2*>(b + L.rects);
+  ws.adjoints = reinterpret_cast<float4*>(b + L.adjoints);
+  ws.visible = reinterpret_cast<uint32_t*>(b + L.visible);
+  ws.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
+  ws.tile_start = reinterpret_cast<uint32_t*>(b + L.tile_start);
+  ws.tile_cursor = reinterpret_cast<uint32_t*>(b + L.tile_cursor);
+  ws.long_tiles = reinterpret_cast<uint32_t*>(b + L.long_tiles);
+  ws.keys = reinterpret_cast<unsigned long long*>(b + L.keys);
+  ws.keys_alt = reinterpret_cast<unsigned long long*>(b + L.keys_alt);
+  ws.sorted_ids = reinterpret_cast<uint32_t*>(b + L.sorted_ids);
+  ws.view_stats = reinterpret_cast<float*>(b + L.view_stats);
+  ws.n = w->n;
+  ws.cap = w->pair_capacity;
+  ws.views = w->frame.n_views;
+  ws.width = w->frame.width;
+  ws.height = w->frame.height;
+  ws.tiles_x = (ws.width + 15) / 16;
+  ws.tiles_y = (ws.height + 15) / 16;
+  ws.tiles_per_view = ws.tiles_x * ws.tiles_y;
+  return ws;
+}
+
+int sm_count() {
+  int dev = 0, n = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+static gs_status check_ws(const gs_workspace* w, gs_layout* L) {
+  if (!w || !w->ptr) return GS_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(w->ptr) & 255u) != 0) return GS_ERR_ARG;
+  return layout(w->n, &w->frame, w->pair_capacity, L);
+}
+
+static gs_status check_map(const gs_map* m, const gs_workspace* w) {
+  if (!m || m->n != w->n || m->sh_degree < 0 || m->sh_degree > 3 || (m->sh_bf16 != 0 && m->sh_bf16 != 1))
+    return GS_ERR_ARG;
+  if (!m->mean || !m->log_scale || !m->quat || !m->logit_opacity || !m->sh_dc) return GS_ERR_ARG;
+  if (m->sh_degree > 0 && !m->sh_rest) return GS_ERR_ARG;
+  return GS_OK;
+}
+
+static gs_status check_cfg(const gs_config* c) {
+  if (!c) return GS_ERR_ARG;
+  if (!(c->alpha_min > 0.f && c->alpha_min < 1.f) || !(c->alpha_max >= c->alpha_min && c->alpha_max < 1.f) ||
+      !(c->t_min > 0.f && c->t_min < 1.f) || !(c->near_z > 0.f) || !(c->dilation >= 0.f) || !(c->fov_clamp > 0.f))
+    return GS_ERR_ARG;
+  return GS_OK;
+}
+
+static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+// Tracing state (single host thread drives the library while tracing).
+static struct {
+  cudaEvent_t* events = nullptr;
+  int32_t* ids = nullptr;
+  int32_t capacity = 0;
+  int32_t count = 0;
+  bool on = false;
+} g_trace;
+
+void trace_begin(int kernel_id, cudaStream_t st) {
+  if (!g_trace.on) return;
+  const int k = g_trace.count;
+  if (k < g_trace.capacity) {
+    cudaEventRecord(g_trace.events[2 * k], st);
+    if (g_trace.ids) g_trace.ids[k] = kernel_id;
+  }
+}
+
+void trace_end(cudaStream_t st) {
+  if (!g_trace.on) return;
+  const int k = g_trace.count++;
+  if (k < g_trace.capacity) cudaEventRecord(g_trace.events[2 * k + 1], st);
+}
+
+}  // namespace gsb
+
+using namespace gsb;
+
+extern "C" {
+
+size_t gs_workspace_size(int64_t n, const gs_frame* frame, int64_t pair_capacity) {
+  gs_layout L;
+  return layout(n, frame, pair_capacity, &L) == GS_OK ? L.total : 0;
+}
+
+gs_status gs_workspace_layout(int64_t n, const gs_frame* frame, int64_t pair_capacity, gs_layout* out) {
+  return layout(n, frame, pair_capacity, out);
+}
+
+gs_status gs_read_status(const gs_workspace* ws, gs_stream_t stream, int32_t* status_out, int64_t* pairs_needed_out) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  uint32_t c[2] = {0, 0};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(c, static_cast<char*>(ws->ptr) + L.counters, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (status_out) *status_out = (int32_t)c[0];
+  if (pairs_needed_out) *pairs_needed_out = (int64_t)c[1];
+  return GS_OK;
+}
+
+gs_status gs_project(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                     gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_map(map, ws)) != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!cams_dev) return GS_ERR_ARG;
+  const Ws w = resolve_ws(ws, L);
+  return cuda_status(launch_project(*map, cams_dev, *cfg, w, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_bin_sort(const gs_workspace* ws, gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  return cuda_status(launch_bin_sort(resolve_ws(ws, L), reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb, float* depth, float* opac,
+                        float* t_final, uint32_t* n_contrib, gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!t_final || !n_contrib) return GS_ERR_ARG;
+  return cuda_status(launch_render_fwd(*cfg, resolve_ws(ws, L), rgb, depth, opac, t_final, n_contrib,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                        const float* rgb, const float* depth, const float* opac, const float* t_final,
+                        const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
+                        float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
+                        float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                        float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
+                        gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_map(map, ws)) != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!cams_dev || !t_final || !n_contrib) return GS_ERR_ARG;
+  if (!grad_mean || !grad_log_scale || !grad_quat || !grad_logit_opacity || !grad_sh_dc) return GS_ERR_ARG;
+  if (map->sh_degree > 0 && !grad_sh_rest) return GS_ERR_ARG;
+  if (tgt_rgb) {
+    if (!rgb) return GS_ERR_ARG;
+    if (tgt_depth && w_depth != 0.f && (!depth || !opac)) return GS_ERR_ARG;
+  }
+  BwdArgs a;
+  a.rgb = rgb; a.depth = depth; a.opac = opac; a.t_final = t_final; a.n_contrib = n_contrib;
+  a.tgt_rgb = tgt_rgb; a.tgt_depth = tgt_depth; a.w_rgb = w_rgb; a.w_depth = w_depth;
+  a.dl_drgb = dl_drgb; a.dl_ddepth = dl_ddepth; a.dl_dopac = dl_dopac;
+  a.grad_mean = grad_mean; a.grad_log_scale = grad_log_scale; a.grad_quat = grad_quat;
+  a.grad_logit = grad_logit_opacity; a.grad_sh_dc = grad_sh_dc; a.grad_sh_rest = grad_sh_rest;
+  a.grad_pose = grad_pose; a.loss = loss_out;
+  return cuda_status(launch_render_bwd(*map, cams_dev, *cfg, resolve_ws(ws, L), a,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                           const gs_workspace* ws, const int32_t* pix_idx, int32_t n_pix, float* J, float* rgb_out,
+                           gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_map(map, ws)) != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!cams_dev || !pix_idx || !J || n_pix < 1) return GS_ERR_ARG;
+  return cuda_status(launch_pose_jacobian(*map, cams_dev, *cfg, resolve_ws(ws, L), pix_idx, n_pix, J, rgb_out,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_trace_start(void* const* events, int32_t capacity, int32_t* kernel_ids) {
+  if (!events || capacity < 1) return GS_ERR_ARG;
+  g_trace.events = reinterpret_cast<cudaEvent_t*>(const_cast<void**>(events));
+  g_trace.ids = kernel_ids;
+  g_trace.capacity = capacity;
+  g_trace.count = 0;
+  g_trace.on = true;
+  return GS_OK;
+}
+
+int32_t gs_trace_stop(void) {
+  g_trace.on = false;
+  return g_trace.count;
+}
+
+const char* gs_kernel_name(int32_t id) {
+  static const char* names[kKNumKernels] = {"project", "scan", "emit", "sort_small", "sort_long", "render_fwd",
+                                            "count_depth", "render_bwd", "preprocess_bwd", "pose_jacobian"};
+  return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
+}
+
+const char* gs_status_str(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "pair buffer too small";
+    case GS_ERR_OOM: return "out of memory";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_TIMEOUT: return "device wait timed out";
+    case GS_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char* gs_version(void) { return "gsb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gs.h"
+#include "gs_device.cuh"
+
+namespace gsb {
+
+// Kernel ids reported by the tracing hook (gs_trace_start).
+enum KernelId {
+  kKProject = 0, kKScan, kKEmit, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
+  kKPreprocessBwd, kKPoseJacobian, kKNumKernels
+};
+// Bracket one kernel launch with the caller's trace events (no-op when off).
+void trace_begin(int kernel_id, cudaStream_t st);
+void trace_end(cudaStream_t st);
+
+// Resolve the device view of a caller workspace (layout must be valid).
+Ws resolve_ws(const gs_workspace* ws, const gs_layout& L);
+int sm_count();
+
+cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                           cudaStream_t st);
+cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st);
+cudaError_t launch_render_fwd(const gs_config& cfg, const Ws& ws, float* rgb, float* depth, float* opac,
+                              float* t_final, uint32_t* n_contrib, cudaStream_t st);
+
+struct BwdArgs {
+  const float *rgb, *depth, *opac, *t_final;
+  const uint32_t* n_contrib;
+  const float *tgt_rgb, *tgt_depth;
+  float w_rgb, w_depth;
+  const float *dl_drgb, *dl_ddepth, *dl_dopac;
+  float *grad_mean, *grad_log_scale, *grad_quat, *grad_logit, *grad_sh_dc, *grad_sh_rest, *grad_pose, *loss;
+};
+cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                              const BwdArgs& a, cudaStream_t st);
+cudaError_t launch_pose_jacobian(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                 const int32_t* pix, int32_t n_pix, float* J, float* rgb, cudaStream_t st);
+
+}  // namespace gsb

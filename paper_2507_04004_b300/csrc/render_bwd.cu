@@ -1,0 +1,478 @@
+// Backward pass of the rasterizer (arxiv 2507.04004):
+//   - pixel adjoints of the depth-regularised loss of Eq. depth_loss
+//     (L1 colour mean plus the opacity-normalised L1 depth term on the valid
+//     LiDAR pixels), fused into the blend backward;
+//   - the adjoint of front-to-back compositing (Eq. rendered_rgb,
+//     rendered_depth, rendered_opacity) per tile, walking each pixel's
+//     contributors back to front and recovering the transmittance before each
+//     Gaussian from the final one, T_i = T_{i+1} / (1 - alpha_i), so no
+//     per-pixel lists are stored;
+//   - per-Gaussian 2D adjoints reduced across each warp with shuffles, then
+//     across the CTA in shared memory, then one vector atomic per
+//     (Gaussian, tile) into the workspace;
+//   - the chain through the projection (Sec. "3D Gaussian Splatting
+//     Representation") to mean, log-scale, quaternion, opacity logit and SH,
+//     and the per-view pose derivative under T Exp(xi) (Eq. 3dgs_jacobi).
+#include "gs_internal.h"
+
+namespace gsb {
+
+// Count of valid LiDAR pixels (D_s > 0) per view: |M_d| of Eq. depth_loss.
+__global__ void __launch_bounds__(256) k_count_depth(const float* __restrict__ tgt_depth, int64_t hw,
+                                                     float* view_stats) {
+  const int v = blockIdx.y;
+  uint32_t c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hw; i += (int64_t)gridDim.x * blockDim.x)
+    c += tgt_depth[v * hw + i] > 0.f ? 1u : 0u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  __shared__ uint32_t s[8];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int i = 0; i < 8; ++i) tot += s[i];
+    if (tot) atomicAdd(view_stats + 4 * v + 1, (float)tot);
+  }
+}
+
+// Warp reduce-scatter of 10 values: after the call, lane l with (l & 1) == 0
+// and *slot >= 0 holds the warp-wide sum of value *slot (10 lanes in all).
+__device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int lane, int* slot) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float w[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float keep = b4 ? v[i + 5] : v[i];
+    const float send = b4 ? v[i] : v[i + 5];
+    w[i] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+  float x[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float hi = (i + 3 < 5) ? w[i + 3] : 0.f;
+    const float keep = b3 ? hi : w[i];
+    const float send = b3 ? w[i] : hi;
+    x[i] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float y[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float hi = (i + 2 < 3) ? x[i + 2] : 0.f;
+    const float keep = b2 ? hi : x[i];
+    const float send = b2 ? x[i] : hi;
+    y[i] = keep + __shfl_xor_sync(kFull, send, 4);
+  }
+  float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(kFull, b1 ? y[0] : y[1], 2);
+  z += __shfl_xor_sync(kFull, z, 1);
+  const int idx3 = (b2 ? 2 : 0) + (b1 ? 1 : 0);
+  const bool valid = idx3 < (b3 ? 2 : 3);
+  *slot = valid ? (b4 ? 5 : 0) + (b3 ? 3 : 0) + idx3 : -1;
+  return z;
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+  __shared__ float4 s_r0[256], s_r1[256], s_r2[256];
+  __shared__ uint32_t s_gid[256];
+  __shared__ float s_acc[256][10];
+  __shared__ float s_red[8];
+  __shared__ uint32_t s_max[8];
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t tile = blockIdx.x;
+  const int v = (int)(tile / ws.tiles_per_view);
+  const int t = (int)(tile - (int64_t)v * ws.tiles_per_view);
+  const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
+  const int x = tx * kTile + (threadIdx.x & 15), y = ty * kTile + (threadIdx.x >> 4);
+  const bool inside = x < ws.width && y < ws.height;
+  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t HW = (int64_t)ws.width * ws.height;
+  const int64_t p = (int64_t)y * ws.width + x;
+  const uint32_t start = ws.tile_start[tile];
+  const uint32_t cnt = ws.tile_count[tile];
+  const float4* rec = ws.records + 3 * (int64_t)v * ws.n;
+  float4* adj = ws.adjoints + 3 * (int64_t)v * ws.n;
+
+  // ---- pixel adjoints (dL/dC, dL/dD, dL/dO) and loss
+  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gO = 0.f, T = 1.f, loss = 0.f;
+  uint32_t last = 0;
+  if (inside) {
+    T = a.t_final[v * HW + p];
+    last = min(a.n_contrib[v * HW + p], cnt);  // never walk past the tile's list
+    if (FUSED) {
+      const float inv3hw = a.w_rgb / (3.f * (float)HW);
+      float r = a.rgb[(3 * (int64_t)v + 0) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 0) * HW + p];
+      gC0 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      r = a.rgb[(3 * (int64_t)v + 1) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 1) * HW + p];
+      gC1 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      r = a.rgb[(3 * (int64_t)v + 2) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 2) * HW + p];
+      gC2 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      if (a.tgt_depth && a.w_depth != 0.f) {
+        const float ds = a.tgt_depth[v * HW + p];
+        const float O = a.opac[v * HW + p], Dp = a.depth[v * HW + p];
+        const float nd = ws.view_stats[4 * v + 1];
+        if (ds > 0.f && O > 0.f && nd > 0.f) {
+          const float rd = Dp / O - ds;
+          const float sg = (float)((rd > 0.f) - (rd < 0.f));
+          gD = a.w_depth * sg / (O * nd);
+          gO = -a.w_depth * sg * Dp / (O * O * nd);
+          loss += a.w_depth * fabsf(rd) / nd;
+        }
+      }
+    } else {
+      if (a.dl_drgb) {
+        gC0 = a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
+        gC1 = a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
+        gC2 = a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
+      }
+      if (a.dl_ddepth) gD = a.dl_ddepth[v * HW + p];
+      if (a.dl_dopac) gO = a.dl_dopac[v * HW + p];
+    }
+  }
+  // CTA reductions: loss sum and the longest contributor prefix
+  uint32_t mx = last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    loss += __shfl_xor_sync(kFull, loss, o);
+    mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  if (lane == 0) { s_red[warp] = loss; s_max[warp] = mx; }
+  __syncthreads();
+  uint32_t max_last = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) max_last = max(max_last, s_max[i]);
+  if (FUSED && a.loss && threadIdx.x == 0) {
+    float tot = 0.f;
+    for (int i = 0; i < 8; ++i) tot += s_red[i];
+    if (tot != 0.f) atomicAdd(a.loss + v, tot);
+  }
+
+  // ---- back-to-front walk
+  float acc0 = cfg.bg[0], acc1 = cfg.bg[1], acc2 = cfg.bg[2], accD = 0.f, accO = 0.f;
+  const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+  for (int64_t end = max_last; end > 0; end -= 256) {
+    const int64_t beg = end > 256 ? end - 256 : 0;
+    const int nb = (int)(end - beg);
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+      const uint32_t gid = ws.sorted_ids[start + beg + threadIdx.x];
+      s_gid[threadIdx.x] = gid;
+      const float4* r = rec + 3 * (int64_t)gid;
+      s_r0[threadIdx.x] = r[0];
+      s_r1[threadIdx.x] = r[1];
+      s_r2[threadIdx.x] = r[2];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) s_acc[threadIdx.x][k] = 0.f;
+    }
+    __syncthreads();
+    for (int j = nb - 1; j >= 0; --j) {
+      const float4 r0 = s_r0[j], r1 = s_r1[j];
+      bool act = inside && (uint64_t)(beg + j) < last;
+      AlphaEval ev;
+      if (act) {
+        ev = eval_alpha(r0, r1, px, py, a_min, a_max);
+        act = ev.pass;
+      }
+      if (!__any_sync(kFull, act)) continue;
+      float val[10];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) val[k] = 0.f;
+      if (act) {
+        const float4 c = s_r2[j];
+        const float al = ev.alpha;
+        T = T / (1.f - al);  // transmittance in front of this Gaussian
+        const float w = al * T;
+        const float dA = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (r1.z - accD) +
+                              gO * (1.f - accO));
+        const float om = 1.f - al;
+        acc0 = al * c.x + om * acc0;
+        acc1 = al * c.y + om * acc1;
+        acc2 = al * c.z + om * acc2;
+        accD = al * r1.z + om * accD;
+        accO = al + om * accO;
+        val[6] = gD * w;
+        val[7] = gC0 * w;
+        val[8] = gC1 * w;
+        val[9] = gC2 * w;
+        if (!ev.clamped) {
+          const float dpow = dA * al;  // dL/d(power), alpha = o exp(power)
+          const float dx = px - r0.x, dy = py - r0.y;
+          val[0] = dpow * (r0.z * dx + r0.w * dy);
+          val[1] = dpow * (r0.w * dx + r1.x * dy);
+          val[2] = -0.5f * dpow * dx * dx;
+          val[3] = -dpow * dx * dy;
+          val[4] = -0.5f * dpow * dy * dy;
+          val[5] = dA * ev.G;
+        }
+      }
+      int slot;
+      const float sum = warp_reduce_scatter10(val, lane, &slot);
+      if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) atomicAdd(&s_acc[j][slot], sum);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+      const float* q = s_acc[threadIdx.x];
+      float4* dst = adj + 3 * (int64_t)s_gid[threadIdx.x];
+      if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f) atomicAdd(dst, make_float4(q[0], q[1], q[2], q[3]));
+      if (q[4] != 0.f || q[5] != 0.f || q[6] != 0.f) atomicAdd(dst + 1, make_float4(q[4], q[5], q[6], 0.f));
+      if (q[7] != 0.f || q[8] != 0.f || q[9] != 0.f) atomicAdd(dst + 2, make_float4(q[7], q[8], q[9], 0.f));
+    }
+  }
+}
+
+// Chain of the 2D adjoints through the projection, per Gaussian over all
+// views; parameter gradients are added once per Gaussian (no atomics), pose
+// partials are reduced per view across the CTA.
+template <int DEG, bool BF16>
+__global__ void __launch_bounds__(256) k_preprocess_bwd(gs_map map, const gs_camera* __restrict__ cams,
+                                                        gs_config cfg, Ws ws, BwdArgs a) {
+  __shared__ float s_pose[8][6];
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const int64_t n = ws.n;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_range = g < n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (ws.counters[kStatus] != 0) return;
+
+  bool any = false;
+  if (in_range)
+    for (int v = 0; v < ws.views; ++v) any |= !rect_empty(ws.rects[(int64_t)v * n + g]);
+  const bool want_pose = a.grad_pose != nullptr;
+  if (!want_pose && !__any_sync(kFull, any)) return;
+
+  float mu[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, logit = 0.f;
+  if (any) {
+    mu[0] = map.mean[g]; mu[1] = map.mean[n + g]; mu[2] = map.mean[2 * n + g];
+    ls[0] = map.log_scale[g]; ls[1] = map.log_scale[n + g]; ls[2] = map.log_scale[2 * n + g];
+    q[0] = map.quat[g]; q[1] = map.quat[n + g]; q[2] = map.quat[2 * n + g]; q[3] = map.quat[3 * n + g];
+    logit = map.logit_opacity[g];
+  }
+  const float qi = rsqrtf(fmaxf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3], 1e-30f));
+  const float qw = q[0] * qi, qx = q[1] * qi, qy = q[2] * qi, qz = q[3] * qi;
+  float Rg[3][3];
+  quat_to_rot(qw, qx, qy, qz, Rg);
+  float s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s[k] = expf(ls[k]);
+  const float o = 1.f / (1.f + expf(-logit));
+
+  float g_mu[3] = {0.f, 0.f, 0.f}, g_s[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {{0.f}}, g_o = 0.f;
+  float g_sh[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+
+  for (int v = 0; v < ws.views; ++v) {
+    float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int64_t e = (int64_t)v * n + g;
+    const bool vis = in_range && !rect_empty(ws.rects[e]);
+    if (vis) {
+      float4* ad = ws.adjoints + 3 * e;
+      const float4 A0 = ad[0], A1 = ad[1], A2 = ad[2];
+      // consume: leave the adjoint area zero for the next backward of this projection
+      ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
+      const float gcol[3] = {A2.x, A2.y, A2.z};
+      const Cam cam = load_cam(cams, v);
+      const float3 mh = to_camera(cam, mu[0], mu[1], mu[2]);
+      const float iz = 1.f / mh.z;
+      const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
+      const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
+      const float txr = mh.x * iz, tyr = mh.y * iz;
+      const bool clx = txr > limx || txr < -limx, cly = tyr > limy || tyr < -limy;
+      const float txc = fminf(limx, fmaxf(-limx, txr)), tyc = fminf(limy, fmaxf(-limy, tyr));
+      const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz, j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
+      float m0[3], m1[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
+        m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
+      }
+      float U[3], Vv[3], rm0[3], rm1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        rm0[k] = Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2];
+        rm1[k] = Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2];
+        U[k] = s[k] * rm0[k];
+        Vv[k] = s[k] * rm1[k];
+      }
+      // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
+      const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
+      const float qa = R0.z, qb = R0.w, qc = R1.x;
+      // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
+      const float hb = 0.5f * gb;
+      const float P00 = qa * ga + qb * hb, P01 = qa * hb + qb * gc, P10 = qb * ga + qc * hb, P11 = qb * hb + qc * gc;
+      const float gA = -(P00 * qa + P01 * qb);
+      const float gBh = -(P00 * qb + P01 * qc);  // d/dSigma'_01 (one of the two symmetric entries)
+      const float gCc = -(P10 * qb + P11 * qc);
+      const float gB = 2.f * gBh;
+      // A = U.U + dil, B = U.V, C = V.V + dil
+      float gU[3], gV[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gU[k] = 2.f * gA * U[k] + gB * Vv[k];
+        gV[k] = gB * U[k] + 2.f * gCc * Vv[k];
+      }
+      float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
+          gm0[i] += s[k] * gU[k] * Rg[i][k];
+          gm1[i] += s[k] * gV[k] * Rg[i][k];
+        }
+      }
+      // m0 = R^T J0, m1 = R^T J1  ->  dL/dJ0 = R gm0, dL/dJ1 = R gm1
+      float gJ0[3], gJ1[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        gJ0[i] = cam.R[3 * i] * gm0[0] + cam.R[3 * i + 1] * gm0[1] + cam.R[3 * i + 2] * gm0[2];
+        gJ1[i] = cam.R[3 * i] * gm1[0] + cam.R[3 * i + 1] * gm1[1] + cam.R[3 * i + 2] * gm1[2];
+      }
+      const float iz2 = iz * iz;
+      float gx = gmx * cam.fx * iz, gy = gmy * cam.fy * iz;
+      float gz = gdep - gmx * cam.fx * mh.x * iz2 - gmy * cam.fy * mh.y * iz2;
+      gz += -gJ0[0] * cam.fx * iz2 - gJ1[1] * cam.fy * iz2;
+      // J02 = -fx txc / z: unclamped txc = x/z, clamped txc constant
+      gz += gJ0[2] * cam.fx * txc * iz2 * (clx ? 1.f : 2.f);
+      if (!clx) gx += -gJ0[2] * cam.fx * iz2;
+      gz += gJ1[2] * cam.fy * tyc * iz2 * (cly ? 1.f : 2.f);
+      if (!cly) gy += -gJ1[2] * cam.fy * iz2;
+      // dL/dmu through mu_hat = R mu + t
+      float gWm[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gWm[j] = cam.R[j] * gx + cam.R[3 + j] * gy + cam.R[6 + j] * gz;
+      // colour: raw = sum_k SH_k Y_k(dir) + 0.5, clamped at 0
+      const float3 cw = camera_centre(cam);
+      float dv[3] = {mu[0] - cw.x, mu[1] - cw.y, mu[2] - cw.z};
+      const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
+      float Y[16];
+      float3 dY[16];
+      sh_basis<DEG>(dx, dy, dz, Y);
+      sh_basis_grad<DEG>(dx, dy, dz, dY);
+      float graw[3];
+      float gdir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float raw = 0.5f;
+        float3 gd = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float c = sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
+          raw += c * Y[k];
+          gd.x += c * dY[k].x; gd.y += c * dY[k].y; gd.z += c * dY[k].z;
+        }
+        graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
+        gdir[0] += graw[ch] * gd.x; gdir[1] += graw[ch] * gd.y; gdir[2] += graw[ch] * gd.z;
+#pragma unroll
+        for (int k = 0; k < K; ++k) g_sh[k][ch] += graw[ch] * Y[k];
+      }
+      const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
+      const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) g_mu[j] += gWm[j] + gv[j];
+      g_o += gop;
+      if (want_pose) {
+        // right perturbation T Exp(xi), xi = (rho, theta):
+        //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
+        const float gcw[3] = {-gv[0], -gv[1], -gv[2]};
+        pose[0] = gWm[0] - gcw[0];
+        pose[1] = gWm[1] - gcw[1];
+        pose[2] = gWm[2] - gcw[2];
+        // theta: mu x (R^T g_mu_hat) + gm0 x m0 + gm1 x m1 + g_cw x c_w
+        const float c_w[3] = {cw.x, cw.y, cw.z};
+        pose[3] = mu[1] * gWm[2] - mu[2] * gWm[1] + gm0[1] * m0[2] - gm0[2] * m0[1] + gm1[1] * m1[2] -
+                  gm1[2] * m1[1] + gcw[1] * c_w[2] - gcw[2] * c_w[1];
+        pose[4] = mu[2] * gWm[0] - mu[0] * gWm[2] + gm0[2] * m0[0] - gm0[0] * m0[2] + gm1[2] * m1[0] -
+                  gm1[0] * m1[2] + gcw[2] * c_w[0] - gcw[0] * c_w[2];
+        pose[5] = mu[0] * gWm[1] - mu[1] * gWm[0] + gm0[0] * m0[1] - gm0[1] * m0[0] + gm1[0] * m1[1] -
+                  gm1[1] * m1[0] + gcw[0] * c_w[1] - gcw[1] * c_w[0];
+      }
+    }
+    if (want_pose) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float val = pose[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(kFull, val, off);
+        if (lane == 0) s_pose[warp][k] = val;
+      }
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        float tot = 0.f;
+        for (int w8 = 0; w8 < 8; ++w8) tot += s_pose[w8][threadIdx.x];
+        if (tot != 0.f) atomicAdd(a.grad_pose + 6 * v + threadIdx.x, tot);
+      }
+      __syncthreads();
+    }
+  }
+  if (!any) return;
+  // quaternion: R(q^) entries -> q^ -> q (normalisation)
+  const float gw = 2.f * (-qz * g_R[0][1] + qy * g_R[0][2] + qz * g_R[1][0] - qx * g_R[1][2] - qy * g_R[2][0] +
+                          qx * g_R[2][1]);
+  const float gxq = 2.f * (qy * g_R[0][1] + qz * g_R[0][2] + qy * g_R[1][0] - 2.f * qx * g_R[1][1] - qw * g_R[1][2] +
+                           qz * g_R[2][0] + qw * g_R[2][1] - 2.f * qx * g_R[2][2]);
+  const float gyq = 2.f * (-2.f * qy * g_R[0][0] + qx * g_R[0][1] + qw * g_R[0][2] + qx * g_R[1][0] + qz * g_R[1][2] -
+                           qw * g_R[2][0] + qz * g_R[2][1] - 2.f * qy * g_R[2][2]);
+  const float gzq = 2.f * (-2.f * qz * g_R[0][0] - qw * g_R[0][1] + qx * g_R[0][2] + qw * g_R[1][0] -
+                           2.f * qz * g_R[1][1] + qy * g_R[1][2] + qx * g_R[2][0] + qy * g_R[2][1]);
+  const float dq = qw * gw + qx * gxq + qy * gyq + qz * gzq;
+  a.grad_quat[g] += (gw - qw * dq) * qi;
+  a.grad_quat[n + g] += (gxq - qx * dq) * qi;
+  a.grad_quat[2 * n + g] += (gyq - qy * dq) * qi;
+  a.grad_quat[3 * n + g] += (gzq - qz * dq) * qi;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    a.grad_mean[j * n + g] += g_mu[j];
+    a.grad_log_scale[j * n + g] += g_s[j] * s[j];
+  }
+  a.grad_logit[g] += g_o * o * (1.f - o);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) a.grad_sh_dc[ch * n + g] += g_sh[0][ch];
+#pragma unroll
+  for (int k = 1; k < K; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) a.grad_sh_rest[((int64_t)(k - 1) * 3 + ch) * n + g] += g_sh[k][ch];
+}
+
+template <int DEG, bool BF16>
+static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                  const BwdArgs& a, cudaStream_t st) {
+  trace_begin(kKPreprocessBwd, st);
+  k_preprocess_bwd<DEG, BF16><<<(unsigned)((ws.n + 255) / 256), 256, 0, st>>>(map, cams, cfg, ws, a);
+  trace_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                              const BwdArgs& a, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(ws.view_stats, 0, (size_t)ws.views * 4 * sizeof(float), st);
+  if (err != cudaSuccess) return err;
+  const bool fused = a.tgt_rgb != nullptr;
+  const int64_t hw = (int64_t)ws.width * ws.height;
+  if (fused && a.tgt_depth && a.w_depth != 0.f) {
+    const int64_t nblk = (hw + 255) / 256;
+    dim3 grid((unsigned)(nblk < 1024 ? nblk : 1024), (unsigned)ws.views);
+    trace_begin(kKCountDepth, st);
+    k_count_depth<<<grid, 256, 0, st>>>(a.tgt_depth, hw, ws.view_stats);
+    trace_end(st);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  trace_begin(kKRenderBwd, st);
+  if (fused) k_render_bwd<true><<<ntiles, 256, 0, st>>>(cfg, ws, a);
+  else k_render_bwd<false><<<ntiles, 256, 0, st>>>(cfg, ws, a);
+  trace_end(st);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const bool bf = map.sh_bf16 != 0;
+  switch (map.sh_degree) {
+    case 0: return bf ? launch_pre_bwd<0, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<0, false>(map, cams, cfg, ws, a, st);
+    case 1: return bf ? launch_pre_bwd<1, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<1, false>(map, cams, cfg, ws, a, st);
+    case 2: return bf ? launch_pre_bwd<2, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<2, false>(map, cams, cfg, ws, a, st);
+    default: return bf ? launch_pre_bwd<3, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<3, false>(map, cams, cfg, ws, a, st);
+  }
+}
+
+}  // namespace gsb

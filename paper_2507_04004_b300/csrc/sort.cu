@@ -1,0 +1,192 @@
+// Tile binning and sorting of (Gaussian, tile) pairs by the 64-bit key
+// (tile id << 32 | depth key bits), ties by Gaussian index.
+//
+// The sort is a two-level most-significant-digit radix sort: the first digit
+// is the whole (view, tile) id, done as a counting sort (per-tile counts from
+// the projection, an exclusive scan here, and binning by per-tile cursors in
+// the emit kernel); the remaining 64 bits (depth key bits << 32 | Gaussian
+// index) are unique inside a bin and are sorted per tile in shared memory
+// (bitonic network), with a merge of sorted runs for the rare bins longer
+// than one CTA's shared memory.  The result for each tile is its Gaussians in
+// front-to-back order, as the compositing of Eq. rendered_rgb needs.
+#include "gs_internal.h"
+
+namespace gsb {
+
+constexpr int kScanThreads = 1024;
+constexpr int kSmallCap = 2048;      // keys sorted by a 256-thread CTA (16 KB)
+constexpr int kLongCap = 16384;      // keys sorted by a 1024-thread CTA (128 KB)
+
+// Exclusive scan of the per-tile counts (single CTA), capacity check, cursor
+// initialisation.  Counts fit in 32 bits; the total is checked in 64 bits.
+__global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws) {
+  __shared__ unsigned long long part[kScanThreads];
+  const int64_t nt = (int64_t)ws.views * ws.tiles_per_view;
+  const int64_t per = (nt + kScanThreads - 1) / kScanThreads;
+  const int64_t b = threadIdx.x * per, e = min(nt, b + per);
+  unsigned long long s = 0;
+  for (int64_t i = b; i < e; ++i) s += ws.tile_count[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the partial sums
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    unsigned long long add = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned long long run = part[threadIdx.x] - s;
+  for (int64_t i = b; i < e; ++i) {
+    const uint32_t c = ws.tile_count[i];
+    const uint32_t st = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+    ws.tile_start[i] = st;
+    ws.tile_cursor[i] = st;
+    run += c;
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    const unsigned long long total = part[kScanThreads - 1];
+    ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    ws.counters[kLongCount] = 0;
+    if (total > (unsigned long long)ws.cap) ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// In-place ascending bitonic sort of s[0, np2) by the whole CTA.
+__device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np2) {
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
+        const int lo = 2 * j * (i / j) + (i % j);
+        const int hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const unsigned long long a = s[lo], c = s[hi];
+        if ((a > c) == up) { s[lo] = c; s[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sort one tile's keys held in shared memory and write the Gaussian indices.
+__device__ __forceinline__ void sort_tile_smem(const Ws& ws, unsigned long long* s, uint32_t start, int cnt) {
+  const int np2 = next_pow2(cnt);
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) s[i] = i < cnt ? ws.keys[start + i] : ~0ull;
+  __syncthreads();
+  bitonic_smem(s, np2);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws.sorted_ids[start + i] = (uint32_t)(s[i] & 0xffffffffull);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_sort_small(Ws ws) {
+  __shared__ unsigned long long s[kSmallCap];
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t t = blockIdx.x;
+  const uint32_t cnt = ws.tile_count[t];
+  if (cnt == 0) return;
+  const uint32_t start = ws.tile_start[t];
+  if (cnt == 1) {
+    if (threadIdx.x == 0) ws.sorted_ids[start] = (uint32_t)(ws.keys[start] & 0xffffffffull);
+    return;
+  }
+  if (cnt > (uint32_t)kSmallCap) {
+    if (threadIdx.x == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
+    return;
+  }
+  sort_tile_smem(ws, s, start, (int)cnt);
+}
+
+// Merge-path split: number of elements of A among the first d outputs of
+// merge(A, B) (keys are unique).
+__device__ __forceinline__ int merge_split(const unsigned long long* A, int la, const unsigned long long* B, int lb,
+                                           int d) {
+  int lo = max(0, d - lb), hi = min(d, la);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (A[mid] < B[d - mid - 1]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Long tiles: one 1024-thread CTA per tile.  Up to kLongCap keys are sorted
+// in shared memory; longer bins are sorted in kLongCap chunks and the sorted
+// runs merged pairwise (merge path) between keys and keys_alt.
+__global__ void __launch_bounds__(1024) k_sort_long(Ws ws) {
+  extern __shared__ unsigned long long sl[];
+  if (ws.counters[kStatus] != 0) return;
+  const uint32_t nl = ws.counters[kLongCount];
+  for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
+    const uint32_t t = ws.long_tiles[li];
+    const int cnt = (int)ws.tile_count[t];
+    const uint32_t start = ws.tile_start[t];
+    if (cnt <= kLongCap) {
+      sort_tile_smem(ws, sl, start, cnt);
+      continue;
+    }
+    // sort chunks in place
+    for (int c0 = 0; c0 < cnt; c0 += kLongCap) {
+      const int m = min(kLongCap, cnt - c0);
+      const int np2 = next_pow2(m);
+      for (int i = threadIdx.x; i < np2; i += blockDim.x) sl[i] = i < m ? ws.keys[start + c0 + i] : ~0ull;
+      __syncthreads();
+      bitonic_smem(sl, np2);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) ws.keys[start + c0 + i] = sl[i];
+      __syncthreads();
+    }
+    unsigned long long* src = ws.keys + start;
+    unsigned long long* dst = ws.keys_alt + start;
+    for (int run = kLongCap; run < cnt; run <<= 1) {
+      for (int lo = 0; lo < cnt; lo += 2 * run) {
+        const int mid = min(cnt, lo + run), hi = min(cnt, lo + 2 * run);
+        const unsigned long long* A = src + lo;
+        const unsigned long long* B = src + mid;
+        const int la = mid - lo, lb = hi - mid, m = hi - lo;
+        const int per = (m + blockDim.x - 1) / blockDim.x;
+        const int d0 = min(m, (int)threadIdx.x * per), d1 = min(m, d0 + per);
+        int ia = merge_split(A, la, B, lb, d0);
+        int ib = d0 - ia;
+        for (int d = d0; d < d1; ++d) {
+          const bool takeA = ia < la && (ib >= lb || A[ia] < B[ib]);
+          dst[lo + d] = takeA ? A[ia++] : B[ib++];
+        }
+      }
+      __syncthreads();
+      unsigned long long* tmp = src; src = dst; dst = tmp;
+    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws.sorted_ids[start + i] = (uint32_t)(src[i] & 0xffffffffull);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_emit(const Ws& ws, cudaStream_t st);
+
+cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
+  trace_begin(kKScan, st);
+  k_scan<<<1, kScanThreads, 0, st>>>(ws);
+  trace_end(st);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  err = launch_emit(ws, st);
+  if (err != cudaSuccess) return err;
+  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  trace_begin(kKSortSmall, st);
+  k_sort_small<<<ntiles, 256, 0, st>>>(ws);
+  trace_end(st);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t smem = (size_t)kLongCap * sizeof(unsigned long long);
+  err = cudaFuncSetAttribute(k_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  trace_begin(kKSortLong, st);
+  k_sort_long<<<sm_count(), 1024, smem, st>>>(ws);
+  trace_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace gsb

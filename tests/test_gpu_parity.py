@@ -1,0 +1,282 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs (needs a GPU).
+
+Every call goes through the C ABI (``libgsb300.so`` via ctypes).  Tolerances:
+RGB and opacity max abs error <= 1e-4, raw depth <= 1e-4 * max(1, max depth),
+gradients <= 1e-3 relative (inf-norm per parameter block); tile lists and
+their order bit-exact outside the oracle's 1e-4 threshold margin.  Pixels
+whose oracle decisions sit within 1e-4 (relative) of a threshold are counted
+and excluded from the element-wise image check.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_04004_b300 import synth
+from tests.gpu_cases import (GRAD_TOL, IMG_TOL, assert_grads_close, compare_tiles, gpu_render, grads_to_numpy,
+                             host_map, rel_err)
+from tests.oracle_cases import logit, one_gaussian_map
+
+pytestmark = pytest.mark.gpu
+
+GRAD_KEYS = ("mean", "log_scale", "quat", "logit_opacity", "sh_dc", "sh_rest")
+
+
+def _check_images(o_r, out, view, label=""):
+    rgb = out.rgb[view].cpu().numpy()
+    dep = out.depth[view].cpu().numpy()
+    opa = out.opac[view].cpu().numpy()
+    ok = o_r["flags"] == 0
+    assert ok.mean() > 0.98, f"{label}: too many margin pixels ({(~ok).sum()})"
+    e_rgb = np.abs(rgb - o_r["rgb"])[:, ok].max()
+    e_o = np.abs(opa - o_r["opac"])[ok].max()
+    dmax = max(1.0, float(np.abs(o_r["depth"]).max()))
+    e_d = np.abs(dep - o_r["depth"])[ok].max()
+    assert e_rgb <= IMG_TOL, f"{label}: rgb max abs {e_rgb:.3e}"
+    assert e_o <= IMG_TOL, f"{label}: opacity max abs {e_o:.3e}"
+    assert e_d <= IMG_TOL * dmax, f"{label}: depth max abs {e_d:.3e} (scale {dmax:.1f})"
+    return e_rgb, e_o, e_d
+
+
+def _check_last_contributor(rast, out, o_r, view):
+    """The GPU's last blended Gaussian (tile-list position n_contrib - 1) is
+    the oracle's last contributor at every unflagged pixel."""
+    start, count, ids = (t.cpu().numpy() for t in rast.tile_lists())
+    nc = out.n_contrib[view].cpu().numpy()
+    H, W = nc.shape
+    tw = (W + 15) // 16
+    T = tw * ((H + 15) // 16)
+    ys, xs = np.nonzero(o_r["flags"] == 0)
+    tiles = view * T + (ys // 16) * tw + xs // 16
+    pos = start[tiles] + nc[ys, xs].astype(np.int64) - 1
+    gpu_last = np.where(nc[ys, xs] > 0, ids[np.maximum(pos, 0)], -1)
+    np.testing.assert_array_equal(gpu_last, o_r["last_gid"][ys, xs])
+
+
+def _mapping_small(seed=11, n=20000, width=200, height=120, n_views=3, sh_degree=3, degenerate=0.0):
+    rng = np.random.default_rng(seed)
+    g = synth.random_map(rng, n, (-6, -3, -6), (6, 3, 6), sh_degree, log_scale_mean=-2.3,
+                         degenerate_frac=degenerate)
+    cams = []
+    for v in range(n_views):
+        R, t = synth.pose_from_centre(synth.yaw_pitch_rotation(0.4 * v - 0.3, 0.05 * v, 0.02), (0.2 * v, 0.1, -0.3))
+        cams.append(synth.camera(R, t, 120.0, 118.0, width / 2 + 0.7, height / 2 - 1.3, width, height))
+    return g, cams
+
+
+# ------------------------------------------------------------------ forward
+def test_tiny_forward_tiles_and_images(oracle):
+    w = synth.tiny()
+    m = host_map(w.gmap)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    assert rast.status()[0] == 0
+    n_margin = compare_tiles(oracle, m, w.cams[0], rast, 0)
+    assert n_margin <= 5
+    o_r = oracle.render(m, w.cams[0])
+    _check_images(o_r, out, 0, "tiny")
+    np.testing.assert_allclose(out.t_final[0].cpu().numpy()[o_r["flags"] == 0], o_r["t_final"][o_r["flags"] == 0],
+                               atol=IMG_TOL)
+    _check_last_contributor(rast, out, o_r, 0)
+
+
+def test_projection_records_match_oracle(oracle):
+    g, cams = _mapping_small(n=5000)
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, cams)
+    rec = rast.records().cpu().numpy()
+    vis = rast.rects().cpu().numpy()
+    for v, cam in enumerate(cams):
+        p = oracle.project(m, cam)
+        x0, x1 = vis[v, :, 0] & 0xFFFF, vis[v, :, 1] & 0xFFFF
+        on = x0 <= x1
+        assert on.sum() > 100
+        assert np.all(p["valid"][on] == 1)
+        np.testing.assert_allclose(rec[v, on, 0], p["mean2d"][0, on], rtol=1e-5, atol=1e-3)
+        np.testing.assert_allclose(rec[v, on, 1], p["mean2d"][1, on], rtol=1e-5, atol=1e-3)
+        for k, slot in ((0, 2), (1, 3), (2, 4)):
+            np.testing.assert_allclose(rec[v, on, slot], p["conic"][k, on], rtol=2e-4,
+                                       atol=2e-4 * np.abs(p["conic"][:, on]).max())
+        np.testing.assert_allclose(rec[v, on, 5], p["opacity"][on], rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(rec[v, on, 6], p["depth"][on], rtol=1e-6)
+        np.testing.assert_array_equal(rec[v, on, 6].astype(np.float32), p["depth32"][on])
+        for c in range(3):
+            np.testing.assert_allclose(rec[v, on, 8 + c], p["rgb"][c, on], atol=2e-6)
+
+
+@pytest.mark.parametrize("sh_bf16,degenerate", [(False, 0.0), (True, 0.01)])
+def test_multiview_ragged_sh3(oracle, sh_bf16, degenerate):
+    g, cams = _mapping_small(degenerate=degenerate)
+    m = host_map(g, sh_bf16)
+    rast, gm, ct, out = gpu_render(g, cams, sh_bf16=sh_bf16)
+    for v, cam in enumerate(cams):
+        compare_tiles(oracle, m, cam, rast, v)
+        o_r = oracle.render(m, cam)
+        _check_images(o_r, out, v, f"view {v}")
+        _check_last_contributor(rast, out, o_r, v)
+
+
+def test_long_tiles_and_merge_path(oracle):
+    """Bins longer than one CTA's shared memory (> 2,048 and > 16,384 keys)."""
+    rng = np.random.default_rng(5)
+    n = 24000
+    g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
+    cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 40.0, 24.0, 20.0, 48, 40)
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, [cam])
+    _, count, _ = rast.tile_lists()
+    assert int(count.max()) > 16384
+    compare_tiles(oracle, m, cam, rast, 0)
+    o_r = oracle.render(m, cam)
+    _check_images(o_r, out, 0, "long tiles")
+
+
+def test_capacity_overflow_reports_and_retries(oracle):
+    w = synth.tiny()
+    m = host_map(w.gmap)
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
+    gm = GaussianMap.from_host(w.gmap)
+    rast = Rasterizer(gm.n, 1, 128, 96, pair_capacity=64)
+    ct = cameras_tensor(w.cams)
+    rast.project_and_sort(gm, ct, check=False)
+    code, needed = rast.status()
+    assert code == 2  # GS_ERR_CAPACITY
+    tile, gid, margin = oracle.tiles(m, w.cams[0])
+    assert abs(needed - int((margin != 2).sum())) <= int((margin != 0).sum())
+    out = rast.render(gm, ct)  # grows the buffer and redoes the batch
+    assert rast.capacity >= needed and rast.status()[0] == 0
+    _check_images(oracle.render(m, w.cams[0]), out, 0, "after retry")
+
+
+def test_degenerate_scenes(oracle):
+    cam = synth.camera(np.eye(3), np.zeros(3), 50, 50, 32, 24, 64, 48)
+    # every Gaussian behind the near plane: background only
+    m = one_gaussian_map([[0, 0, -1.0], [0.1, 0, 0.1]], [math.log(0.2)] * 2, [0.0] * 2, [[0.5] * 3] * 2)
+    g = synth.GaussianMap(**{k: np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v
+                             for k, v in m.items()})
+    rast, gm, ct, out = gpu_render(g, [cam], config=dict(bg=(0.1, 0.2, 0.3)))
+    rgb = out.rgb[0].cpu().numpy()
+    np.testing.assert_array_equal(rgb[0], np.float32(0.1))
+    np.testing.assert_array_equal(rgb[2], np.float32(0.3))
+    assert int(out.n_contrib.max()) == 0 and float(out.t_final.min()) == 1.0
+    # a single Gaussian
+    m = one_gaussian_map([[0.02, -0.01, 5.0]], [math.log(0.2)], [logit(0.8)], [[0.2, 0.5, 0.9]])
+    g = synth.GaussianMap(**{k: np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v
+                             for k, v in m.items()})
+    rast, gm, ct, out = gpu_render(g, [cam])
+    _check_images(oracle.render(m, cam), out, 0, "single")
+
+
+def test_forward_is_deterministic():
+    g, cams = _mapping_small(n=8000)
+    rast, gm, ct, out1 = gpu_render(g, cams)
+    a = (out1.rgb.clone(), out1.depth.clone(), out1.n_contrib.clone())
+    out2 = rast.render(gm, ct)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], out2.rgb) and torch.equal(a[1], out2.depth) and torch.equal(a[2], out2.n_contrib)
+
+
+# ------------------------------------------------------------------ backward
+def _tiny_depth_target(oracle, w, m):
+    r = oracle.render(m, w.cams[0])
+    mask = w.meta["depth_mask"][0] & (r["opac"] > 0)
+    d = np.where(mask, r["depth"] / np.where(mask, r["opac"], 1.0) + w.meta["depth_noise"][0], 0.0)
+    return d[None].astype(np.float32)
+
+
+def test_tiny_fused_loss_gradients(oracle):
+    w = synth.tiny()
+    m = host_map(w.gmap)
+    tgt_d = _tiny_depth_target(oracle, w, m)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    tr = torch.as_tensor(w.tgt_rgb, device="cuda")
+    td = torch.as_tensor(tgt_d, device="cuda")
+    g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth))
+    o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=tgt_d, w_rgb=w.w_rgb, w_depth=w.w_depth)
+    assert g["loss"][0] == pytest.approx(o["loss"][0], rel=1e-4)
+    assert_grads_close(g, o, GRAD_KEYS)
+    assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("sh_bf16", [False, True])
+def test_multiview_external_adjoint_gradients(oracle, sh_bf16):
+    g, cams = _mapping_small(n=12000, sh_degree=3)
+    m = host_map(g, sh_bf16)
+    rast, gm, ct, out = gpu_render(g, cams, sh_bf16=sh_bf16)
+    V, H, W = len(cams), cams[0]["height"], cams[0]["width"]
+    rng = np.random.default_rng(3)
+    er = rng.normal(size=(V, 3, H, W)).astype(np.float32)
+    ed = (0.05 * rng.normal(size=(V, H, W))).astype(np.float32)
+    eo = rng.normal(size=(V, H, W)).astype(np.float32)
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    gg = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
+    o = oracle.backward(m, cams, ext_rgb=er, ext_depth=ed, ext_opac=eo)
+    assert_grads_close(gg, o, GRAD_KEYS)
+    for v in range(V):
+        assert rel_err(gg["pose"][v], o["pose"][v]) <= GRAD_TOL, v
+
+
+def test_mapping_fused_loss_with_lidar_depth(oracle):
+    """Small copy of the mapping workload: LiDAR sparse depth, 0.8 L1 + 0.2 depth."""
+    w = synth.mapping(n=30000, width=160, height=96, focal=90.0, n_views=2)
+    m = host_map(w.gmap)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=t(w.tgt_rgb), tgt_depth=t(w.tgt_depth), w_rgb=w.w_rgb,
+                                     w_depth=w.w_depth))
+    o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=w.tgt_depth, w_rgb=w.w_rgb, w_depth=w.w_depth)
+    np.testing.assert_allclose(g["loss"], o["loss"], rtol=1e-4)
+    assert_grads_close(g, o, GRAD_KEYS)
+    assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
+
+
+def test_backward_twice_gives_same_gradients():
+    """The 2D adjoint area is consumed and cleared by each backward."""
+    g, cams = _mapping_small(n=6000)
+    rast, gm, ct, out = gpu_render(g, cams)
+    dl = torch.randn(len(cams), 3, cams[0]["height"], cams[0]["width"], device="cuda")
+    g1 = rast.backward(gm, ct, out, dl_drgb=dl)
+    g2 = rast.backward(gm, ct, out, dl_drgb=dl)
+    torch.cuda.synchronize()
+    # equal up to the summation order of float atomics
+    for a, b in ((g1.mean, g2.mean), (g1.sh_rest, g2.sh_rest), (g1.pose, g2.pose)):
+        assert rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 1e-4
+
+
+def test_autograd_function_matches_backward():
+    from paper_2507_04004_b300.raster import rasterize
+    g, cams = _mapping_small(n=6000, n_views=2)
+    rast, gm, ct, out = gpu_render(g, cams)
+    params = {k: getattr(gm, k).clone().requires_grad_(True) for k in
+              ("mean", "log_scale", "quat", "logit_opacity", "sh_dc", "sh_rest")}
+    xi = torch.zeros(2, 6, device="cuda", requires_grad=True)
+    rgb, dep, opa = rasterize(rast, ct, xi, params, gm.sh_degree)
+    wgt = torch.randn_like(rgb)
+    loss = (wgt * rgb).sum() + 0.01 * dep.sum() + opa.sum()
+    loss.backward()
+    ref = rast.backward(gm, ct, rast.render(gm, ct), dl_drgb=wgt, dl_ddepth=torch.full_like(dep, 0.01),
+                        dl_dopac=torch.ones_like(opa))
+    torch.cuda.synchronize()
+    # equal up to the summation order of float atomics
+    for a, b in ((params["mean"].grad, ref.mean), (params["sh_rest"].grad, ref.sh_rest), (xi.grad, ref.pose)):
+        assert rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 1e-4
+
+
+# ------------------------------------------------------------------ pose Jacobian
+def test_pose_jacobian_rows_match_oracle(oracle):
+    g, cams = _mapping_small(n=10000, n_views=2, sh_degree=1)
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, cams)
+    H, W = cams[0]["height"], cams[0]["width"]
+    rng = np.random.default_rng(8)
+    pix = np.stack([np.sort(rng.choice(H * W, 500, replace=False)) for _ in cams]).astype(np.int32)
+    J, rgb = rast.pose_jacobian(gm, ct, torch.as_tensor(pix, device="cuda"))
+    J, rgb = J.cpu().numpy(), rgb.cpu().numpy()
+    for v, cam in enumerate(cams):
+        Jo, rgbo = oracle.pose_jacobian(m, cam, pix[v])
+        r = oracle.render(m, cam)
+        ok = r["flags"].reshape(-1)[pix[v]] == 0
+        np.testing.assert_allclose(rgb[v][ok], rgbo[ok], atol=IMG_TOL)
+        scale = np.abs(Jo[ok]).max()
+        err = np.abs(J[v][ok] - Jo[ok]).max() / scale
+        assert err <= GRAD_TOL, f"view {v}: J relative error {err:.3e}"
