@@ -44,7 +44,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=WORKLOAD["n_gaussians"])
+    p.add_argument("--views", type=int, default=WORKLOAD["views"], help="keyframes per batch (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
     return p.parse_args()
 
@@ -179,11 +181,11 @@ def traffic_for(kernel: str):
     return d.get("bytes_per_launch_full_workload")
 
 
-def make_workload(n: int, seed_offset: int = 0):
+def make_workload(n: int, seed_offset: int = 0, views: int = WORKLOAD["views"]):
     from paper_2507_04004_b300 import synth
     return synth.mapping(seed=synth.SEED_BASE + 20 + seed_offset, n=n, width=WORKLOAD["width"],
                          height=WORKLOAD["height"], focal=WORKLOAD["focal"], sh_degree=WORKLOAD["sh_degree"],
-                         n_views=WORKLOAD["views"])
+                         n_views=views)
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -253,13 +255,50 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(args, d, rast, gm, w, px_step):
+    """Same metric through the public API from host buffers: every step
+    uploads its keyframes (targets, depth maps, cameras) from pinned memory on
+    a copy stream (double-buffered) and reads the loss back."""
+    import torch
+
+    from paper_2507_04004_b300.pipeline import MappingStep
+    from paper_2507_04004_b300.raster import cameras_tensor
+    host_rgb = torch.as_tensor(w.tgt_rgb).pin_memory()
+    host_depth = torch.as_tensor(w.tgt_depth).pin_memory()
+    host_cams = cameras_tensor(w.cams, device="cpu").pin_memory()
+    ms_step = MappingStep(rast, gm, w.w_rgb, w.w_depth)
+    e_steps = max(10, min(args.steps, 50))
+    slot = ms_step.upload(host_rgb, host_depth, host_cams)
+    for _ in range(3):
+        nxt = ms_step.upload(host_rgb, host_depth, host_cams)
+        ms_step.step(slot)
+        slot = nxt
+    torch.cuda.synchronize()
+    d.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    slot = ms_step.upload(host_rgb, host_depth, host_cams)
+    for i in range(e_steps):
+        nxt = ms_step.upload(host_rgb, host_depth, host_cams) if i + 1 < e_steps else None
+        ms_step.step(slot)
+        slot = nxt
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+    e2e_s = d.max(e2e_s)
+    d.barrier()
+    val = d.sum(px_step * e_steps) / e2e_s / 1e6
+    return {"value": round(val, 2), "unit": "Mpix/s", "h2d_bytes_per_step": ms_step.h2d_bytes,
+            "d2h_bytes_per_step": ms_step.d2h_bytes}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_ours(args):
     import numpy as np
     import torch
 
     from paper_2507_04004_b300 import _native as N
-    from paper_2507_04004_b300.pipeline import MappingStep
     from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
 
     if not torch.cuda.is_available():
@@ -268,9 +307,9 @@ def run_ours(args):
     torch.cuda.set_device(d.dev)
     N.lib()
 
-    w = make_workload(args.n, seed_offset=d.rank)
+    w = make_workload(args.n, seed_offset=d.rank, views=args.views)
     gm = GaussianMap.from_host(w.gmap, device=d.dev)
-    V, H, W = WORKLOAD["views"], WORKLOAD["height"], WORKLOAD["width"]
+    V, H, W = args.views, WORKLOAD["height"], WORKLOAD["width"]
     rast = Rasterizer(gm.n, V, W, H, device=d.dev)
     cams = cameras_tensor(w.cams, device=d.dev)
     tgt_rgb = torch.as_tensor(w.tgt_rgb, device=d.dev)
@@ -351,6 +390,7 @@ def run_ours(args):
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOP
     # algorithmic counts per launch ("Roofline accounting")
     sh_bytes = 4 * 3 * (WORKLOAD["sh_degree"] + 1) ** 2
+    V = args.views
     alg = {
         "project": ("hbm", V * args.n * 12 + n_visible * (12 + 16 + 4 + sh_bytes + 48 + 48) + V * args.n * 8),
         "emit": ("hbm", n_visible * (32 + 8) + n_pairs * 8),
@@ -372,35 +412,9 @@ def run_ours(args):
                                 (n_sm, sm_mhz)) if bound == "alu" else f"{peaks['source']} HBM copy bandwidth"}
 
     # end to end: host keyframes -> device, fwd+bwd, loss back to host
-    host_rgb = torch.as_tensor(w.tgt_rgb).pin_memory()
-    host_depth = torch.as_tensor(w.tgt_depth).pin_memory()
-    host_cams = cameras_tensor(w.cams, device="cpu").pin_memory()
-    ms_step = MappingStep(rast, gm, w.w_rgb, w.w_depth)
-    e_steps = max(10, min(args.steps, 50))
-    slot = ms_step.upload(host_rgb, host_depth, host_cams)
-    for _ in range(3):
-        nxt = ms_step.upload(host_rgb, host_depth, host_cams)
-        ms_step.step(slot)
-        slot = nxt
-    torch.cuda.synchronize()
-    d.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    e0.record()
-    slot = ms_step.upload(host_rgb, host_depth, host_cams)
-    for i in range(e_steps):
-        nxt = ms_step.upload(host_rgb, host_depth, host_cams) if i + 1 < e_steps else None
-        ms_step.step(slot)
-        slot = nxt
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
-    e2e_s = d.max(e2e_s)
-    d.barrier()
-
+    e2e = None if args.no_e2e else run_e2e(args, d, rast, gm, w, px_step)
     total_px = d.sum(px_step * args.steps)
     value = total_px / (ms / 1e3) / 1e6
-    e2e_val = d.sum(px_step * e_steps) / e2e_s / 1e6
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
@@ -414,11 +428,11 @@ def run_ours(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": d.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, parallelism=f"replicas x{d.world}" if d.world > 1 else "single GPU",
+                "config": dict(WORKLOAD, views=args.views, n_gaussians=args.n,
+                               parallelism=f"replicas x{d.world}" if d.world > 1 else "single GPU",
                                l2="inputs larger than L2: 236 MB of Gaussian parameters, 192 MB of projected records"),
                 "clocks": clocks,
-                "e2e": {"value": round(e2e_val, 2), "unit": "Mpix/s", "h2d_bytes_per_step": ms_step.h2d_bytes,
-                        "d2h_bytes_per_step": ms_step.d2h_bytes},
+                "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": roofline,
                 "cpu_baseline": cpu,
