@@ -187,6 +187,35 @@ gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const g
                            const gs_workspace* ws, const int32_t* pix_idx, int32_t n_pix, float* J, float* rgb_out,
                            gs_stream_t stream);
 
+/* Forward render that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc - code running
+ * inside a host framework that owns all device memory (an inference-engine
+ * plugin, a middleware node that is handed fixed buffers) or a real-time loop
+ * that cannot afford cudaMalloc's implicit device synchronisation.
+ *
+ * It does what gs_project + gs_bin_sort + gs_render_fwd do, with the same
+ * kernels and outputs (rgb, depth, opac may be NULL; t_final and n_contrib
+ * may not), but instead of a caller workspace it uses a file-scope device
+ * array of GS_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
+ * library holds until the process exits.  The caller passes the map, the
+ * device cameras, the batch geometry and every output; status_dev (device
+ * int32) receives GS_OK or GS_ERR_CAPACITY (the pair buffer left in the array
+ * was too small; the images are then background only).  Requests whose
+ * per-Gaussian and per-tile parts do not fit in the array are rejected with
+ * GS_ERR_UNSUPPORTED before anything is enqueued (about V*N*108 bytes plus
+ * V*T*16 bytes must stay well below 64 MiB; the rest holds 20 bytes per pair).
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call clears what must start at zero): calls that
+ * overlap on the GPU - on two streams, or from two host threads - race. */
+#define GS_NOALLOC_SCRATCH_BYTES (64u << 20)
+gs_status gs_render_fwd_noalloc(const gs_map* map, const gs_camera* cams_dev, const gs_frame* frame,
+                                const gs_config* cfg, float* rgb, float* depth, float* opac, float* t_final,
+                                uint32_t* n_contrib, int32_t* status_dev, gs_stream_t stream);
+
 /* Per-kernel tracing (timing support; no counterpart in the paper).  While
  * active, each kernel the library launches is bracketed by
  * cudaEventRecord(events[2k]) / cudaEventRecord(events[2k+1]) on its stream,

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_PKG, "libgsb300.so")
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(7)
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_trace_start", "gs_trace_stop",
+            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_trace_start",
+            "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
 
 
@@ -76,6 +77,9 @@ def lib():
                                     + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P])
         L.gs_pose_jacobian.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace), P, I32,
                                        P, P, P]
+        L.gs_render_fwd_noalloc.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_frame), C.POINTER(gs_config),
+                                            P, P, P, P, P, P, P]
+        L.gs_render_fwd_noalloc.restype = I32
         L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
         L.gs_trace_start.restype = I32
         L.gs_trace_stop.argtypes = []
@@ -147,6 +151,14 @@ def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth,
 def gs_pose_jacobian(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, pix, n_pix: int, J, rgb, stream: int) -> None:
     check("gs_pose_jacobian", lib().gs_pose_jacobian(C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(pix),
                                                      int(n_pix), _ptr(J), _ptr(rgb), C.c_void_p(stream)))
+
+
+def gs_render_fwd_noalloc(m: gs_map, cams, frame: gs_frame, cfg: gs_config, rgb, depth, opac, t_final, n_contrib,
+                          status_dev, stream: int) -> int:
+    """Allocation-free forward render; returns the synchronous status code."""
+    return int(lib().gs_render_fwd_noalloc(C.byref(m), _ptr(cams), C.byref(frame), C.byref(cfg), _ptr(rgb),
+                                           _ptr(depth), _ptr(opac), _ptr(t_final), _ptr(n_contrib),
+                                           _ptr(status_dev), C.c_void_p(stream)))
 
 
 def gs_trace_start(event_handles, kernel_ids) -> None:
