@@ -164,7 +164,8 @@ def source_hash(*names) -> str:
 
 
 # Which source file holds each kernel (for matching ncu traffic to source).
-KERNEL_SRC = {"project": "project.cu", "emit": "project.cu", "scan": "sort.cu", "sort_small": "sort.cu",
+KERNEL_SRC = {"project": "project.cu", "scatter_rows": "project.cu", "rows_count": "project.cu",
+              "rows_emit": "project.cu", "scan_buckets": "sort.cu", "scan": "sort.cu", "sort_small": "sort.cu",
               "sort_long": "sort.cu", "render_fwd": "render_fwd.cu", "count_depth": "render_bwd.cu",
               "render_bwd": "render_bwd.cu", "preprocess_bwd": "render_bwd.cu", "pose_jacobian": "jacobian.cu"}
 
@@ -334,7 +335,7 @@ def run_ours(args):
         raise SystemExit(f"workspace status {code} after warm-up (pairs needed {needed})")
 
     # per-kernel trace events for the timed region
-    per_step = 9
+    per_step = 16
     cap = per_step * args.steps + 16
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * cap)]
     for e in evs:
@@ -380,8 +381,8 @@ def run_ours(args):
     dominant = next(iter(kernels))
 
     # work counters of one step (for the algorithmic roofline)
-    counters = rast._view(rast.layout.counters, 4, torch.int32).cpu().numpy()
-    n_visible, n_pairs = int(counters[2]), int(counters[1])
+    counters = rast._view(rast.layout.counters, 8, torch.int32).cpu().numpy()
+    n_visible, n_pairs, n_rows = int(counters[2]), int(counters[1]), int(counters[4])
     k_eval = float(out.n_contrib.to(torch.float64).sum().item())
     px_step = V * H * W
     peaks = measured_peaks()
@@ -393,7 +394,8 @@ def run_ours(args):
     V = args.views
     alg = {
         "project": ("hbm", V * args.n * 12 + n_visible * (12 + 16 + 4 + sh_bytes + 48 + 48) + V * args.n * 8),
-        "emit": ("hbm", n_visible * (32 + 8) + n_pairs * 8),
+        "rows_emit": ("hbm", n_pairs * 8 + n_rows * (8 + 4 + 16)),
+        "rows_count": ("hbm", n_rows * (8 + 32 + 4)),
         "sort_small": ("hbm", n_pairs * (8 + 4)),
         "render_fwd": ("alu", k_eval * 27.0),
         "render_bwd": ("alu", k_eval * 75.0),
@@ -437,7 +439,8 @@ def run_ours(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "kernels": kernels,
-                "work": {"visible_entries": n_visible, "pairs": n_pairs, "blend_evaluations": k_eval,
+                "work": {"visible_entries": n_visible, "pairs": n_pairs, "row_items": n_rows,
+                         "blend_evaluations": k_eval,
                          "lidar_valid_frac": [round(x, 4) for x in w.meta["depth_frac"]]}}
         print(json.dumps(line), flush=True)
     d.close()

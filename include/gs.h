@@ -98,13 +98,15 @@ typedef struct {
 typedef struct {
   void* ptr;
   int64_t n;              /* Gaussians the workspace was sized for */
-  int64_t pair_capacity;  /* (Gaussian, tile) pairs it can hold, < 2^31 */
+  int64_t pair_capacity;  /* (Gaussian, tile) pairs it can hold, < 2^31; also bounds the
+                             (Gaussian, tile row) items of the binning pass */
   gs_frame frame;
 } gs_workspace;
 
 /* Byte offsets of the workspace's parts (for inspection and tests). */
 typedef struct {
-  size_t counters;    /* uint32[16]: [0] status, [1] pairs needed, [2] visible entries, [3] long tiles */
+  size_t counters;    /* uint32[16]: [0] status, [1] pairs (or row items) needed, [2] visible entries,
+                         [3] long tiles, [4] row items */
   size_t records;     /* float4[V*N][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
   size_t rects;       /* uint32[V*N][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
   size_t adjoints;    /* float4[V*N][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */
@@ -113,6 +115,11 @@ typedef struct {
   size_t tile_start;  /* uint32[V*T]: first pair of each tile in the sorted order */
   size_t tile_cursor; /* uint32[V*T]: fill cursor used while binning */
   size_t long_tiles;  /* uint32[V*T]: tiles too long for the single-CTA shared-memory sort */
+  size_t bucket_count;  /* uint32[V*ceil(H/16)]: row items per (view, tile row) */
+  size_t bucket_start;  /* uint32[V*ceil(H/16)] */
+  size_t bucket_cursor; /* uint32[V*ceil(H/16)] */
+  size_t row_items;   /* uint32[cap][2]: (entry v*N + g, bucket), one per (Gaussian, tile row of its box) */
+  size_t row_span;    /* uint32[cap]: kept tile columns of each row item */
   size_t keys;        /* uint64[cap]: (depth key bits << 32 | Gaussian index), binned by tile */
   size_t keys_alt;    /* uint64[cap]: merge buffer for very long tiles */
   size_t sorted_ids;  /* uint32[cap]: Gaussian index of each pair, sorted by (tile, depth key, index) */
@@ -203,7 +210,7 @@ gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const g
  * was too small; the images are then background only).  Requests whose
  * per-Gaussian and per-tile parts do not fit in the array are rejected with
  * GS_ERR_UNSUPPORTED before anything is enqueued (about V*N*108 bytes plus
- * V*T*16 bytes must stay well below 64 MiB; the rest holds 20 bytes per pair).
+ * V*T*16 bytes must stay well below 64 MiB; the rest holds 32 bytes per pair).
  * No cudaMalloc, cudaFree or allocating library routine is called.
  *
  * The first call on a device looks up the array's device address with

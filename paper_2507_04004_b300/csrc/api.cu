@@ -33,6 +33,12 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   L->tile_start = take((size_t)(V * T) * sizeof(uint32_t));
   L->tile_cursor = take((size_t)(V * T) * sizeof(uint32_t));
   L->long_tiles = take((size_t)(V * T) * sizeof(uint32_t));
+  const int64_t B = V * ((f->height + 15) / 16);
+  L->bucket_count = take((size_t)B * sizeof(uint32_t));
+  L->bucket_start = take((size_t)B * sizeof(uint32_t));
+  L->bucket_cursor = take((size_t)B * sizeof(uint32_t));
+  L->row_items = take((size_t)cap * sizeof(uint2));
+  L->row_span = take((size_t)cap * sizeof(uint32_t));
   L->keys = take((size_t)cap * sizeof(unsigned long long));
   L->keys_alt = take((size_t)cap * sizeof(unsigned long long));
   L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
@@ -53,6 +59,11 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.tile_start = reinterpret_cast<uint32_t*>(b + L.tile_start);
   ws.tile_cursor = reinterpret_cast<uint32_t*>(b + L.tile_cursor);
   ws.long_tiles = reinterpret_cast<uint32_t*>(b + L.long_tiles);
+  ws.bucket_count = reinterpret_cast<uint32_t*>(b + L.bucket_count);
+  ws.bucket_start = reinterpret_cast<uint32_t*>(b + L.bucket_start);
+  ws.bucket_cursor = reinterpret_cast<uint32_t*>(b + L.bucket_cursor);
+  ws.row_items = reinterpret_cast<uint2*>(b + L.row_items);
+  ws.row_span = reinterpret_cast<uint32_t*>(b + L.row_span);
   ws.keys = reinterpret_cast<unsigned long long*>(b + L.keys);
   ws.keys_alt = reinterpret_cast<unsigned long long*>(b + L.keys_alt);
   ws.sorted_ids = reinterpret_cast<uint32_t*>(b + L.sorted_ids);
@@ -240,8 +251,10 @@ int32_t gs_trace_stop(void) {
 }
 
 const char* gs_kernel_name(int32_t id) {
-  static const char* names[kKNumKernels] = {"project", "scan", "emit", "sort_small", "sort_long", "render_fwd",
-                                            "count_depth", "render_bwd", "preprocess_bwd", "pose_jacobian"};
+  static const char* names[kKNumKernels] = {"project",     "scan",           "scatter_rows",  "sort_small",
+                                            "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
+                                            "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
+                                            "rows_emit"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -17,6 +17,7 @@ namespace gsb {
 constexpr int kTile = 16;
 constexpr int kTilePixels = kTile * kTile;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlendPPT = 2;  // pixels per thread in the blend kernels (a tile is 256 / kBlendPPT threads)
 
 // Device view of the workspace parts (pointers resolved from gs_layout).
 struct Ws {
@@ -29,6 +30,11 @@ struct Ws {
   uint32_t* tile_start;   // [V*T]
   uint32_t* tile_cursor;  // [V*T]
   uint32_t* long_tiles;   // [V*T]
+  uint32_t* bucket_count;   // [V*tiles_y] row items per (view, tile row)
+  uint32_t* bucket_start;   // [V*tiles_y]
+  uint32_t* bucket_cursor;  // [V*tiles_y]
+  uint2* row_items;         // [cap] (entry v*N + g, bucket v*tiles_y + ty), grouped by bucket
+  uint32_t* row_span;       // [cap] packed kept-tile span of each row item
   unsigned long long* keys;      // [cap]
   unsigned long long* keys_alt;  // [cap]
   uint32_t* sorted_ids;   // [cap]
@@ -38,7 +44,7 @@ struct Ws {
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
 
-enum CounterSlot { kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3 };
+enum CounterSlot { kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4 };
 
 struct Cam {
   float R[9], t[3], fx, fy, cx, cy;
@@ -145,6 +151,37 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float3*
   }
 }
 
+// sum_k w[k] grad Y_k(x, y, z) for the polynomials above, without forming
+// the per-k gradients as an array.
+template <int DEG>
+__device__ __forceinline__ float3 sh_weighted_grad(const float* w, float x, float y, float z) {
+  using namespace shc;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (DEG >= 1) {
+    gy -= k1 * w[1];
+    gz += k1 * w[2];
+    gx -= k1 * w[3];
+  }
+  if (DEG >= 2) {
+    gx += k2a * y * w[4]; gy += k2a * x * w[4];
+    gy -= k2a * z * w[5]; gz -= k2a * y * w[5];
+    gz += 6.f * k2b * z * w[6];
+    gx -= k2a * z * w[7]; gz -= k2a * x * w[7];
+    gx += 2.f * k2c * x * w[8]; gy -= 2.f * k2c * y * w[8];
+    if (DEG >= 3) {
+      const float xx = x * x, yy = y * y, zz = z * z;
+      gx -= 6.f * k3a * x * y * w[9]; gy -= k3a * (3.f * xx - 3.f * yy) * w[9];
+      gx += k3b * y * z * w[10]; gy += k3b * x * z * w[10]; gz += k3b * x * y * w[10];
+      gy -= k3c * (5.f * zz - 1.f) * w[11]; gz -= 10.f * k3c * y * z * w[11];
+      gz += k3d * (15.f * zz - 3.f) * w[12];
+      gx -= k3c * (5.f * zz - 1.f) * w[13]; gz -= 10.f * k3c * x * z * w[13];
+      gx += 2.f * k3e * x * z * w[14]; gy -= 2.f * k3e * y * z * w[14]; gz += k3e * (xx - yy) * w[14];
+      gx -= k3a * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * k3a * x * y * w[15];
+    }
+  }
+  return make_float3(gx, gy, gz);
+}
+
 // SH coefficient k of channel ch for Gaussian g (k = 0 is the DC array).
 template <bool BF16>
 __device__ __forceinline__ float sh_coeff(const void* dc, const void* rest, int64_t n, int64_t g, int k, int ch) {
@@ -158,29 +195,33 @@ __device__ __forceinline__ float sh_coeff(const void* dc, const void* rest, int6
 }
 
 // ----------------------------------------------------------------------------
-// Per-pixel weight (Eq. alpha): the same FP32 expression is used by the
-// forward, backward and Jacobian kernels so that their skip decisions agree.
-struct AlphaEval {
-  float alpha;  // min(alpha_max, o exp(power)), valid when pass
-  float G;      // exp(power)
-  float power;  // -q/2
-  bool pass;    // alpha >= alpha_min
-  bool clamped; // o exp(power) > alpha_max
+// Blend-kernel form of a projected Gaussian (Eq. alpha in the log2 domain):
+//   p2(px, py) = ha dx^2 + hb dx dy + hc dy^2 + log2(o),  dx = px - mx,
+//   ha = -a log2(e) / 2, hb = -b log2(e), hc = -c log2(e) / 2,
+// so o exp(-q/2) = 2^p2 and the alpha_min test is p2 >= log2(alpha_min),
+// taken before any exponential.  The forward, backward and Jacobian kernels
+// stage records through stage_gaussian() and evaluate p2 with blend_p2(),
+// both with explicit roundings, so their decisions are bit-identical.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+struct Staged {
+  float4 g0;  // mx, my, ha, hb
+  float4 g1;  // hc, log2(o), depth, 1/o
 };
 
-__device__ __forceinline__ AlphaEval eval_alpha(float4 r0, float4 r1, float px, float py, float a_min,
-                                                float a_max) {
-  AlphaEval e;
-  // explicit roundings: every kernel that includes this gets bit-identical alphas
-  const float dx = __fsub_rn(px, r0.x), dy = __fsub_rn(py, r0.y);
-  const float q2 = __fmaf_rn(__fmul_rn(r0.z, dx), dx, __fmul_rn(__fmul_rn(r1.x, dy), dy));
-  e.power = __fmaf_rn(-0.5f, q2, -__fmul_rn(__fmul_rn(r0.w, dx), dy));
-  e.G = __expf(e.power);
-  const float a = __fmul_rn(r1.y, e.G);
-  e.clamped = a > a_max;
-  e.alpha = fminf(a_max, a);
-  e.pass = (e.power <= 0.f) && (e.alpha >= a_min);
-  return e;
+__device__ __forceinline__ Staged stage_gaussian(float4 r0, float4 r1) {
+  Staged s;
+  s.g0 = make_float4(r0.x, r0.y, __fmul_rn(-0.5f * kLog2e, r0.z), __fmul_rn(-kLog2e, r0.w));
+  s.g1 = make_float4(__fmul_rn(-0.5f * kLog2e, r1.x), __log2f(r1.y), r1.z, __frcp_rn(r1.y));
+  return s;
+}
+
+__device__ __forceinline__ float blend_p2(float4 g0, float4 g1, float px, float py) {
+  const float dx = __fsub_rn(px, g0.x), dy = __fsub_rn(py, g0.y);
+  const float t = __fmaf_rn(g0.w, dy, __fmul_rn(g0.z, dx));  // ha dx + hb dy
+  const float u = __fmaf_rn(g1.x, __fmul_rn(dy, dy), g1.y);   // hc dy^2 + log2 o
+  return __fmaf_rn(t, dx, u);
 }
 
 // ----------------------------------------------------------------------------
@@ -198,64 +239,74 @@ struct Ellipse {
 __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
   Ellipse e;
   e.mx = r0.x; e.my = r0.y; e.a = r0.z; e.b = r0.w; e.c = r1.x; e.q_thr = r1.w;
-  // explicit round-to-nearest operations: the count and the emit kernels
-  // must take bit-identical decisions
-  e.inv_a = __fdiv_rn(1.f, e.a);
+  // explicit roundings and single-instruction approximations (no branches):
+  // every kernel that evaluates a chord takes bit-identical decisions
+  e.inv_a = __fdividef(1.f, e.a);
   e.det_c = __fsub_rn(__fmul_rn(e.a, e.c), __fmul_rn(e.b, e.b));
   return e;
 }
 
 // Tile-column range [*tl, *tr] of pixel centres inside the ellipse on pixel
-// row y; false if the row holds none.
+// row y; false if the row holds none.  Written without branches so that the
+// lanes of a warp stay converged across the 16 rows of a tile row.
 __device__ __forceinline__ bool row_tiles(const Ellipse& e, int y, int width, int* tl, int* tr) {
   const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), e.my);
   const float disc = __fsub_rn(__fmul_rn(e.a, e.q_thr), __fmul_rn(__fmul_rn(e.det_c, dy), dy));
-  if (!(disc >= 0.f)) return false;
-  const float half = __fmul_rn(__fsqrt_rn(disc), e.inv_a);
+  const float dpos = fmaxf(disc, 1e-30f);
+  const float half = __fmul_rn(__fmul_rn(dpos, rsqrtf(dpos)), e.inv_a);  // sqrt(disc) / a
   const float xc = __fsub_rn(e.mx, __fmul_rn(__fmul_rn(e.b, dy), e.inv_a));
+  const float wm1 = (float)(width - 1);
   const float xl = ceilf(__fsub_rn(__fsub_rn(xc, half), 0.5f));
   const float xr = floorf(__fsub_rn(__fadd_rn(xc, half), 0.5f));
-  if (!(xl <= xr) || xr < 0.f || xl > (float)(width - 1)) return false;
-  const int il = xl < 0.f ? 0 : (int)xl;
-  const int ir = xr > (float)(width - 1) ? width - 1 : (int)xr;
-  *tl = il >> 4;
-  *tr = ir >> 4;
-  return true;
+  const bool ok = (disc >= 0.f) & (xl <= xr) & (xr >= 0.f) & (xl <= wm1);
+  *tl = (int)fminf(fmaxf(xl, 0.f), wm1) >> 4;
+  *tr = (int)fminf(fmaxf(xr, 0.f), wm1) >> 4;
+  return ok;
 }
 
-// Calls f(tx, ty) for every kept tile inside the tile box, tile rows in
-// ascending order, tiles ascending within a row.
-template <class F>
-__device__ __forceinline__ void for_each_kept_tile(const Ellipse& e, int tx0, int ty0, int tx1, int ty1, int width,
-                                                   int height, F&& f) {
-  for (int ty = ty0; ty <= ty1; ++ty) {
-    const int y0 = ty * kTile, y1 = min(height - 1, y0 + kTile - 1);
-    int lo = 1 << 30, hi = -1;
-    bool gap = false;
-    for (int y = y0; y <= y1; ++y) {
-      int tl, tr;
-      if (!row_tiles(e, y, width, &tl, &tr)) continue;
-      if (hi >= 0 && (tl > hi + 1 || tr < lo - 1)) gap = true;
-      lo = min(lo, tl);
-      hi = max(hi, tr);
-    }
-    if (hi < 0) continue;
-    lo = max(lo, tx0);
-    hi = min(hi, tx1);
-    if (!gap) {
-      for (int tx = lo; tx <= hi; ++tx) f(tx, ty);
-    } else {
-      // rare: disjoint chords inside one tile row; test each tile exactly
-      for (int tx = lo; tx <= hi; ++tx) {
-        bool keep = false;
-        for (int y = y0; y <= y1 && !keep; ++y) {
-          int tl, tr;
-          if (row_tiles(e, y, width, &tl, &tr)) keep = (tl <= tx && tx <= tr);
-        }
-        if (keep) f(tx, ty);
-      }
-    }
+// Kept tiles of tile row ty: the columns [lo, hi] hull the 16 chords' tile
+// ranges; when the chords' ranges are disjoint (gap, rare: very thin tilted
+// ellipses) only the tiles that tile_kept() confirms belong to the set.
+struct RowSpan {
+  int lo, hi;
+  bool gap;
+};
+
+__device__ __forceinline__ RowSpan row_span(const Ellipse& e, int ty, int width, int height) {
+  const int y0 = ty * kTile, y1 = min(height - 1, y0 + kTile - 1);
+  RowSpan s{1 << 30, -1, false};
+#pragma unroll 4
+  for (int y = y0; y <= y1; ++y) {
+    int tl, tr;
+    const bool ok = row_tiles(e, y, width, &tl, &tr);
+    s.gap |= ok & (s.hi >= 0) & ((tl > s.hi + 1) | (tr < s.lo - 1));
+    s.lo = ok ? min(s.lo, tl) : s.lo;
+    s.hi = ok ? max(s.hi, tr) : s.hi;
   }
+  return s;
+}
+
+// Exact test of one tile of a gap row: one of its pixel rows' chords reaches it.
+__device__ __forceinline__ bool tile_kept(const Ellipse& e, int tx, int ty, int width, int height) {
+  const int y0 = ty * kTile, y1 = min(height - 1, y0 + kTile - 1);
+  for (int y = y0; y <= y1; ++y) {
+    int tl, tr;
+    if (row_tiles(e, y, width, &tl, &tr) && tl <= tx && tx <= tr) return true;
+  }
+  return false;
+}
+
+// Packed span of a row item: lo | hi << 12 | gap << 31 (lo > hi: empty).
+__device__ __forceinline__ uint32_t pack_span(const RowSpan& s) {
+  if (s.hi < 0) return 0xfffu;
+  return (uint32_t)s.lo | ((uint32_t)s.hi << 12) | (s.gap ? 0x80000000u : 0u);
+}
+__device__ __forceinline__ RowSpan unpack_span(uint32_t p) {
+  RowSpan s;
+  s.lo = (int)(p & 0xfffu);
+  s.hi = (int)((p >> 12) & 0xfffu);
+  s.gap = (p >> 31) != 0;
+  return s;
 }
 
 __device__ __forceinline__ uint2 pack_rect(int x0, int y0, int x1, int y1) {

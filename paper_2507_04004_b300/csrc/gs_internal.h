@@ -10,8 +10,8 @@ namespace gsb {
 
 // Kernel ids reported by the tracing hook (gs_trace_start).
 enum KernelId {
-  kKProject = 0, kKScan, kKEmit, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
-  kKPreprocessBwd, kKPoseJacobian, kKNumKernels
+  kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
+  kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);

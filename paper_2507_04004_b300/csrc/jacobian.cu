@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(128) k_pose_jacobian(gs_map map, const gs_came
   const uint32_t start = ws.tile_start[tile], cnt = ws.tile_count[tile];
   const Cam cam = load_cam(cams, v);
   const float4* rec = ws.records + 3 * (int64_t)v * ws.n;
+  const float lt = __log2f(cfg.alpha_min);
   float T = 1.f, C[3] = {0.f, 0.f, 0.f}, S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dC[3][6];
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch)
@@ -164,21 +165,24 @@ __global__ void __launch_bounds__(128) k_pose_jacobian(gs_map map, const gs_came
     const uint32_t gid = ws.sorted_ids[start + j];
     const float4* r = rec + 3 * (int64_t)gid;
     const float4 r0 = r[0], r1 = r[1];
-    const AlphaEval ev = eval_alpha(r0, r1, px, py, cfg.alpha_min, cfg.alpha_max);
-    if (!ev.pass) continue;
-    const float Tn = __fmul_rn(T, __fsub_rn(1.f, ev.alpha));
+    const Staged sg = stage_gaussian(r0, r1);
+    const float p2 = blend_p2(sg.g0, sg.g1, px, py);
+    if (!(p2 >= lt)) continue;
+    const float araw = exp2f(p2);
+    const bool clamped = araw > cfg.alpha_max;
+    const float al = fminf(cfg.alpha_max, araw);
+    const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
     if (Tn < cfg.t_min) break;
     const float4 c = r[2];
     const float col[3] = {c.x, c.y, c.z};
     Tangents tg;
     pose_tangents<DEG, BF16>(map, gid, cam, cfg, ws.width, ws.height, r0, r1, tg);
-    const float al = ev.alpha;
     const float dx = px - r0.x, dy = py - r0.y;
     const float w = al * T;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       float dal = 0.f;
-      if (!ev.clamped) {
+      if (!clamped) {
         const float dpow = (r0.z * dx + r0.w * dy) * tg.mx[i] + (r0.w * dx + r1.x * dy) * tg.my[i] -
                            0.5f * dx * dx * tg.a[i] - dx * dy * tg.b[i] - 0.5f * dy * dy * tg.c[i];
         dal = al * dpow;

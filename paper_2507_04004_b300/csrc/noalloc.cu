@@ -64,9 +64,15 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_map* map, const gs_camera* c
   if (gs_workspace_layout(map->n, frame, 1, &L) != GS_OK) return GS_ERR_ARG;
   const size_t limit = (size_t)GS_NOALLOC_SCRATCH_BYTES;
   if (L.total > limit) return GS_ERR_UNSUPPORTED;
-  int64_t cap = (int64_t)((limit - L.total) / 20);
-  while (cap > 0 && (gs_workspace_layout(map->n, frame, cap, &L) != GS_OK || L.total > limit)) cap -= 64;
-  if (cap < 1) return GS_ERR_UNSUPPORTED;
+  // largest pair capacity whose layout fits (the layout grows with it)
+  int64_t lo = 1, hi = (int64_t)(limit - L.total);
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (gs_workspace_layout(map->n, frame, mid, &L) == GS_OK && L.total <= limit) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t cap = lo;
+  if (gs_workspace_layout(map->n, frame, cap, &L) != GS_OK || L.total > limit) return GS_ERR_UNSUPPORTED;
   void* base = nullptr;
   gs_status s = noalloc_scratch(&base);
   if (s != GS_OK) return s;

@@ -70,43 +70,57 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int la
   return z;
 }
 
-template <bool FUSED>
-__global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
-  __shared__ float4 s_r0[256], s_r1[256], s_r2[256];
+template <bool FUSED, int PPT>
+__global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+  constexpr int NT = 256 / PPT;  // threads per tile
+  constexpr int NW = NT / 32;    // warps per tile
+  constexpr int RS = 16 / PPT;   // row stride between a thread's pixels
+  __shared__ float4 s_g0[256], s_g1[256], s_c[256];
   __shared__ uint32_t s_gid[256];
   __shared__ float s_acc[256][10];
-  __shared__ float s_red[8];
-  __shared__ uint32_t s_max[8];
+  __shared__ float s_red[NW];
+  __shared__ uint32_t s_max[NW];
   if (ws.counters[kStatus] != 0) return;
   const int64_t tile = blockIdx.x;
   const int v = (int)(tile / ws.tiles_per_view);
   const int t = (int)(tile - (int64_t)v * ws.tiles_per_view);
   const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
-  const int x = tx * kTile + (threadIdx.x & 15), y = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = x < ws.width && y < ws.height;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const int x = tx * kTile + (threadIdx.x & 15);
+  const int yb = ty * kTile + (threadIdx.x >> 4);
+  const float px = (float)x + 0.5f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t HW = (int64_t)ws.width * ws.height;
-  const int64_t p = (int64_t)y * ws.width + x;
   const uint32_t start = ws.tile_start[tile];
   const uint32_t cnt = ws.tile_count[tile];
   const float4* rec = ws.records + 3 * (int64_t)v * ws.n;
   float4* adj = ws.adjoints + 3 * (int64_t)v * ws.n;
 
-  // ---- pixel adjoints (dL/dC, dL/dD, dL/dO) and loss
-  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gO = 0.f, T = 1.f, loss = 0.f;
-  uint32_t last = 0;
-  if (inside) {
-    T = a.t_final[v * HW + p];
-    last = min(a.n_contrib[v * HW + p], cnt);  // never walk past the tile's list
+  // ---- per-pixel adjoints (dL/dC, dL/dD, dL/dO) and loss
+  float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gO[PPT], T[PPT], py[PPT];
+  float acc0[PPT], acc1[PPT], acc2[PPT], accD[PPT], accO[PPT];
+  uint32_t last[PPT];
+  float loss = 0.f;
+  uint32_t mx = 0;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int y = yb + k * RS;
+    py[k] = (float)y + 0.5f;
+    gC0[k] = gC1[k] = gC2[k] = gD[k] = gO[k] = 0.f;
+    T[k] = 1.f;
+    last[k] = 0;
+    acc0[k] = cfg.bg[0]; acc1[k] = cfg.bg[1]; acc2[k] = cfg.bg[2]; accD[k] = 0.f; accO[k] = 0.f;
+    if (!(x < ws.width && y < ws.height)) continue;
+    const int64_t p = (int64_t)y * ws.width + x;
+    T[k] = a.t_final[v * HW + p];
+    last[k] = min(a.n_contrib[v * HW + p], cnt);  // never walk past the tile's list
     if (FUSED) {
       const float inv3hw = a.w_rgb / (3.f * (float)HW);
       float r = a.rgb[(3 * (int64_t)v + 0) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 0) * HW + p];
-      gC0 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      gC0[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
       r = a.rgb[(3 * (int64_t)v + 1) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 1) * HW + p];
-      gC1 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      gC1[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
       r = a.rgb[(3 * (int64_t)v + 2) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 2) * HW + p];
-      gC2 = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
+      gC2[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
       if (a.tgt_depth && a.w_depth != 0.f) {
         const float ds = a.tgt_depth[v * HW + p];
         const float O = a.opac[v * HW + p], Dp = a.depth[v * HW + p];
@@ -114,23 +128,23 @@ __global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArg
         if (ds > 0.f && O > 0.f && nd > 0.f) {
           const float rd = Dp / O - ds;
           const float sg = (float)((rd > 0.f) - (rd < 0.f));
-          gD = a.w_depth * sg / (O * nd);
-          gO = -a.w_depth * sg * Dp / (O * O * nd);
+          gD[k] = a.w_depth * sg / (O * nd);
+          gO[k] = -a.w_depth * sg * Dp / (O * O * nd);
           loss += a.w_depth * fabsf(rd) / nd;
         }
       }
     } else {
       if (a.dl_drgb) {
-        gC0 = a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
-        gC1 = a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
-        gC2 = a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
+        gC0[k] = a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
+        gC1[k] = a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
+        gC2[k] = a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
       }
-      if (a.dl_ddepth) gD = a.dl_ddepth[v * HW + p];
-      if (a.dl_dopac) gO = a.dl_dopac[v * HW + p];
+      if (a.dl_ddepth) gD[k] = a.dl_ddepth[v * HW + p];
+      if (a.dl_dopac) gO[k] = a.dl_dopac[v * HW + p];
     }
+    mx = max(mx, last[k]);
   }
   // CTA reductions: loss sum and the longest contributor prefix
-  uint32_t mx = last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     loss += __shfl_xor_sync(kFull, loss, o);
@@ -140,69 +154,80 @@ __global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArg
   __syncthreads();
   uint32_t max_last = 0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) max_last = max(max_last, s_max[i]);
+  for (int i = 0; i < NW; ++i) max_last = max(max_last, s_max[i]);
   if (FUSED && a.loss && threadIdx.x == 0) {
     float tot = 0.f;
-    for (int i = 0; i < 8; ++i) tot += s_red[i];
+    for (int i = 0; i < NW; ++i) tot += s_red[i];
     if (tot != 0.f) atomicAdd(a.loss + v, tot);
   }
 
   // ---- back-to-front walk
-  float acc0 = cfg.bg[0], acc1 = cfg.bg[1], acc2 = cfg.bg[2], accD = 0.f, accO = 0.f;
-  const float a_min = cfg.alpha_min, a_max = cfg.alpha_max;
+  const float a_max = cfg.alpha_max;
+  const float lt = __log2f(cfg.alpha_min);
   for (int64_t end = max_last; end > 0; end -= 256) {
     const int64_t beg = end > 256 ? end - 256 : 0;
     const int nb = (int)(end - beg);
     __syncthreads();
-    if ((int)threadIdx.x < nb) {
-      const uint32_t gid = ws.sorted_ids[start + beg + threadIdx.x];
-      s_gid[threadIdx.x] = gid;
+    for (int i = threadIdx.x; i < nb; i += NT) {
+      const uint32_t gid = ws.sorted_ids[start + beg + i];
+      s_gid[i] = gid;
       const float4* r = rec + 3 * (int64_t)gid;
-      s_r0[threadIdx.x] = r[0];
-      s_r1[threadIdx.x] = r[1];
-      s_r2[threadIdx.x] = r[2];
+      const Staged sg = stage_gaussian(r[0], r[1]);
+      s_g0[i] = sg.g0;
+      s_g1[i] = sg.g1;
+      s_c[i] = r[2];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) s_acc[threadIdx.x][k] = 0.f;
+      for (int q = 0; q < 10; ++q) s_acc[i][q] = 0.f;
     }
     __syncthreads();
     for (int j = nb - 1; j >= 0; --j) {
-      const float4 r0 = s_r0[j], r1 = s_r1[j];
-      bool act = inside && (uint64_t)(beg + j) < last;
-      AlphaEval ev;
-      if (act) {
-        ev = eval_alpha(r0, r1, px, py, a_min, a_max);
-        act = ev.pass;
+      const float4 g0 = s_g0[j], g1 = s_g1[j];
+      const uint64_t pos = (uint64_t)(beg + j);
+      float p2[PPT];
+      bool act[PPT];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        p2[k] = blend_p2(g0, g1, px, py[k]);
+        act[k] = pos < last[k] && p2[k] >= lt;
+        any |= act[k];
       }
-      if (!__any_sync(kFull, act)) continue;
+      if (!__any_sync(kFull, any)) continue;
       float val[10];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) val[k] = 0.f;
-      if (act) {
-        const float4 c = s_r2[j];
-        const float al = ev.alpha;
-        T = T / (1.f - al);  // transmittance in front of this Gaussian
-        const float w = al * T;
-        const float dA = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (r1.z - accD) +
-                              gO * (1.f - accO));
+      for (int q = 0; q < 10; ++q) val[q] = 0.f;
+      const float4 c = s_c[j];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!act[k]) continue;
+        const float araw = exp2f(p2[k]);
+        const bool clamped = araw > a_max;
+        const float al = fminf(a_max, araw);
+        T[k] = __fdividef(T[k], 1.f - al);  // transmittance in front of this Gaussian (1 - al >= 0.01)
+        const float w = al * T[k];
+        const float dA = T[k] * (gC0[k] * (c.x - acc0[k]) + gC1[k] * (c.y - acc1[k]) + gC2[k] * (c.z - acc2[k]) +
+                                 gD[k] * (g1.z - accD[k]) + gO[k] * (1.f - accO[k]));
         const float om = 1.f - al;
-        acc0 = al * c.x + om * acc0;
-        acc1 = al * c.y + om * acc1;
-        acc2 = al * c.z + om * acc2;
-        accD = al * r1.z + om * accD;
-        accO = al + om * accO;
-        val[6] = gD * w;
-        val[7] = gC0 * w;
-        val[8] = gC1 * w;
-        val[9] = gC2 * w;
-        if (!ev.clamped) {
-          const float dpow = dA * al;  // dL/d(power), alpha = o exp(power)
-          const float dx = px - r0.x, dy = py - r0.y;
-          val[0] = dpow * (r0.z * dx + r0.w * dy);
-          val[1] = dpow * (r0.w * dx + r1.x * dy);
-          val[2] = -0.5f * dpow * dx * dx;
-          val[3] = -dpow * dx * dy;
-          val[4] = -0.5f * dpow * dy * dy;
-          val[5] = dA * ev.G;
+        acc0[k] = al * c.x + om * acc0[k];
+        acc1[k] = al * c.y + om * acc1[k];
+        acc2[k] = al * c.z + om * acc2[k];
+        accD[k] = al * g1.z + om * accD[k];
+        accO[k] = al + om * accO[k];
+        val[6] += gD[k] * w;
+        val[7] += gC0[k] * w;
+        val[8] += gC1[k] * w;
+        val[9] += gC2[k] * w;
+        if (!clamped) {
+          // alpha = o exp(power): dL/dpower = dA alpha, dL/do = dA alpha / o
+          const float dpow = dA * al;
+          const float dx = px - g0.x, dy = py[k] - g0.y;
+          // a dx + b dy = -ln2 (2 ha dx + hb dy), b dx + c dy = -ln2 (hb dx + 2 hc dy)
+          val[0] -= dpow * kLn2 * (2.f * g0.z * dx + g0.w * dy);
+          val[1] -= dpow * kLn2 * (g0.w * dx + 2.f * g1.x * dy);
+          val[2] -= 0.5f * dpow * dx * dx;
+          val[3] -= dpow * dx * dy;
+          val[4] -= 0.5f * dpow * dy * dy;
+          val[5] += dpow * g1.w;
         }
       }
       int slot;
@@ -210,9 +235,9 @@ __global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArg
       if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) atomicAdd(&s_acc[j][slot], sum);
     }
     __syncthreads();
-    if ((int)threadIdx.x < nb) {
-      const float* q = s_acc[threadIdx.x];
-      float4* dst = adj + 3 * (int64_t)s_gid[threadIdx.x];
+    for (int i = threadIdx.x; i < nb; i += NT) {
+      const float* q = s_acc[i];
+      float4* dst = adj + 3 * (int64_t)s_gid[i];
       if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f) atomicAdd(dst, make_float4(q[0], q[1], q[2], q[3]));
       if (q[4] != 0.f || q[5] != 0.f || q[6] != 0.f) atomicAdd(dst + 1, make_float4(q[4], q[5], q[6], 0.f));
       if (q[7] != 0.f || q[8] != 0.f || q[9] != 0.f) atomicAdd(dst + 2, make_float4(q[7], q[8], q[9], 0.f));
@@ -224,10 +249,12 @@ __global__ void __launch_bounds__(256) k_render_bwd(gs_config cfg, Ws ws, BwdArg
 // views; parameter gradients are added once per Gaussian (no atomics), pose
 // partials are reduced per view across the CTA.
 template <int DEG, bool BF16>
-__global__ void __launch_bounds__(256) k_preprocess_bwd(gs_map map, const gs_camera* __restrict__ cams,
+__global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_camera* __restrict__ cams,
                                                         gs_config cfg, Ws ws, BwdArgs a) {
   __shared__ float s_pose[8][6];
   constexpr int K = (DEG + 1) * (DEG + 1);
+  // SH gradient accumulators live in shared memory (column per thread)
+  __shared__ float s_gsh[3 * K][256];
   const int64_t n = ws.n;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in_range = g < n;
@@ -257,9 +284,8 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(gs_map map, const gs_cam
   const float o = 1.f / (1.f + expf(-logit));
 
   float g_mu[3] = {0.f, 0.f, 0.f}, g_s[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {{0.f}}, g_o = 0.f;
-  float g_sh[K][3];
 #pragma unroll
-  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+  for (int k = 0; k < 3 * K; ++k) s_gsh[k][threadIdx.x] = 0.f;
 
   for (int v = 0; v < ws.views; ++v) {
     float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -349,26 +375,27 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(gs_map map, const gs_cam
       const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
       const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
       float Y[16];
-      float3 dY[16];
       sh_basis<DEG>(dx, dy, dz, Y);
-      sh_basis_grad<DEG>(dx, dy, dz, dY);
       float graw[3];
-      float gdir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float raw = 0.5f;
-        float3 gd = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float c = sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
-          raw += c * Y[k];
-          gd.x += c * dY[k].x; gd.y += c * dY[k].y; gd.z += c * dY[k].z;
-        }
+        for (int k = 0; k < K; ++k) raw += sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch) * Y[k];
         graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
-        gdir[0] += graw[ch] * gd.x; gdir[1] += graw[ch] * gd.y; gdir[2] += graw[ch] * gd.z;
 #pragma unroll
-        for (int k = 0; k < K; ++k) g_sh[k][ch] += graw[ch] * Y[k];
+        for (int k = 0; k < K; ++k) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
       }
+      // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
+      float wk[16];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        wk[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
+      }
+      const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
+      const float gdir[3] = {gd3.x, gd3.y, gd3.z};
       const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
       const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
 #pragma unroll
@@ -430,11 +457,12 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(gs_map map, const gs_cam
   }
   a.grad_logit[g] += g_o * o * (1.f - o);
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) a.grad_sh_dc[ch * n + g] += g_sh[0][ch];
+  for (int ch = 0; ch < 3; ++ch) a.grad_sh_dc[ch * n + g] += s_gsh[ch][threadIdx.x];
 #pragma unroll
   for (int k = 1; k < K; ++k)
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) a.grad_sh_rest[((int64_t)(k - 1) * 3 + ch) * n + g] += g_sh[k][ch];
+    for (int ch = 0; ch < 3; ++ch)
+      a.grad_sh_rest[((int64_t)(k - 1) * 3 + ch) * n + g] += s_gsh[3 * k + ch][threadIdx.x];
 }
 
 template <int DEG, bool BF16>
@@ -462,8 +490,8 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
   }
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKRenderBwd, st);
-  if (fused) k_render_bwd<true><<<ntiles, 256, 0, st>>>(cfg, ws, a);
-  else k_render_bwd<false><<<ntiles, 256, 0, st>>>(cfg, ws, a);
+  if (fused) k_render_bwd<true, kBlendPPT><<<ntiles, 256 / kBlendPPT, 0, st>>>(cfg, ws, a);
+  else k_render_bwd<false, kBlendPPT><<<ntiles, 256 / kBlendPPT, 0, st>>>(cfg, ws, a);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   const bool bf = map.sh_bf16 != 0;

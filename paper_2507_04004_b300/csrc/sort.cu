@@ -17,15 +17,14 @@ constexpr int kScanThreads = 1024;
 constexpr int kSmallCap = 2048;      // keys sorted by a 256-thread CTA (16 KB)
 constexpr int kLongCap = 16384;      // keys sorted by a 1024-thread CTA (128 KB)
 
-// Exclusive scan of the per-tile counts (single CTA), capacity check, cursor
-// initialisation.  Counts fit in 32 bits; the total is checked in 64 bits.
-__global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws) {
+// Exclusive scan of n counts by one CTA: start[i] = sum of counts before i,
+// cursor[i] = start[i]; returns the 64-bit total (to every thread).
+__device__ unsigned long long block_scan(const uint32_t* count, uint32_t* start, uint32_t* cursor, int64_t n) {
   __shared__ unsigned long long part[kScanThreads];
-  const int64_t nt = (int64_t)ws.views * ws.tiles_per_view;
-  const int64_t per = (nt + kScanThreads - 1) / kScanThreads;
-  const int64_t b = threadIdx.x * per, e = min(nt, b + per);
+  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
+  const int64_t b = threadIdx.x * per, e = min(n, b + per);
   unsigned long long s = 0;
-  for (int64_t i = b; i < e; ++i) s += ws.tile_count[i];
+  for (int64_t i = b; i < e; ++i) s += count[i];
   part[threadIdx.x] = s;
   __syncthreads();
   // Hillis-Steele inclusive scan of the partial sums
@@ -37,14 +36,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws) {
   }
   unsigned long long run = part[threadIdx.x] - s;
   for (int64_t i = b; i < e; ++i) {
-    const uint32_t c = ws.tile_count[i];
     const uint32_t st = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
-    ws.tile_start[i] = st;
-    ws.tile_cursor[i] = st;
-    run += c;
+    start[i] = st;
+    cursor[i] = st;
+    run += count[i];
   }
-  if (threadIdx.x == kScanThreads - 1) {
-    const unsigned long long total = part[kScanThreads - 1];
+  const unsigned long long total = part[kScanThreads - 1];
+  __syncthreads();
+  return total;
+}
+
+// Bucket (view, tile row) ranges of the row items; capacity check.
+__global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
+  const unsigned long long total =
+      block_scan(ws.bucket_count, ws.bucket_start, ws.bucket_cursor, (int64_t)ws.views * ws.tiles_y);
+  if (threadIdx.x == 0) {
+    ws.counters[kRowCount] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    if (total > (unsigned long long)ws.cap) {
+      ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+      ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
+    }
+  }
+}
+
+// Tile ranges of the pairs (exclusive scan of the per-tile counts), capacity
+// check, cursor initialisation.  Counts fit in 32 bits; the total is checked
+// in 64 bits.
+__global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws) {
+  if (ws.counters[kStatus] != 0) return;
+  const unsigned long long total =
+      block_scan(ws.tile_count, ws.tile_start, ws.tile_cursor, (int64_t)ws.views * ws.tiles_per_view);
+  if (threadIdx.x == 0) {
     ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     ws.counters[kLongCount] = 0;
     if (total > (unsigned long long)ws.cap) ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
@@ -62,7 +84,7 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np2) {
   for (int k = 2; k <= np2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < (np2 >> 1); i += blockDim.x) {
-        const int lo = 2 * j * (i / j) + (i % j);
+        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));  // j is a power of two
         const int hi = lo + j;
         const bool up = (lo & k) == 0;
         const unsigned long long a = s[lo], c = s[hi];
@@ -164,16 +186,21 @@ __global__ void __launch_bounds__(1024) k_sort_long(Ws ws) {
   }
 }
 
-cudaError_t launch_emit(const Ws& ws, cudaStream_t st);
+cudaError_t launch_rows(const Ws& ws, int phase, cudaStream_t st);
 
 cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
-  trace_begin(kKScan, st);
-  k_scan<<<1, kScanThreads, 0, st>>>(ws);
+  trace_begin(kKScanBuckets, st);
+  k_scan_buckets<<<1, kScanThreads, 0, st>>>(ws);
   trace_end(st);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  err = launch_emit(ws, st);
-  if (err != cudaSuccess) return err;
+  if ((err = launch_rows(ws, 0, st)) != cudaSuccess) return err;
+  if ((err = launch_rows(ws, 1, st)) != cudaSuccess) return err;
+  trace_begin(kKScan, st);
+  k_scan<<<1, kScanThreads, 0, st>>>(ws);
+  trace_end(st);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if ((err = launch_rows(ws, 2, st)) != cudaSuccess) return err;
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKSortSmall, st);
   k_sort_small<<<ntiles, 256, 0, st>>>(ws);
