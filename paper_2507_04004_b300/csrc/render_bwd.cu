@@ -74,7 +74,7 @@ template <bool FUSED, int PPT>
 __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
-  constexpr int RS = 16 / PPT;   // row stride between a thread's pixels
+  // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
   __shared__ float4 s_g0[256], s_g1[256], s_c[256];
   __shared__ uint32_t s_gid[256];
   __shared__ float s_acc[256][10];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
   const int t = (int)(tile - (int64_t)v * ws.tiles_per_view);
   const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
   const int x = tx * kTile + (threadIdx.x & 15);
-  const int yb = ty * kTile + (threadIdx.x >> 4);
+  const int yb = ty * kTile + PPT * (threadIdx.x >> 4);
   const float px = (float)x + 0.5f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t HW = (int64_t)ws.width * ws.height;
@@ -97,18 +97,20 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
 
   // ---- per-pixel adjoints (dL/dC, dL/dD, dL/dO) and loss
   float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gO[PPT], T[PPT], py[PPT];
-  float acc0[PPT], acc1[PPT], acc2[PPT], accD[PPT], accO[PPT];
+  // S = adjoint-weighted value of everything behind the current Gaussian:
+  // sum over later contributors j of (gC.c_j + gD d_j + gO) alpha_j T_j / T_next, plus gC.bg
+  float S[PPT];
   uint32_t last[PPT];
   float loss = 0.f;
   uint32_t mx = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int y = yb + k * RS;
+    const int y = yb + k;
     py[k] = (float)y + 0.5f;
     gC0[k] = gC1[k] = gC2[k] = gD[k] = gO[k] = 0.f;
     T[k] = 1.f;
     last[k] = 0;
-    acc0[k] = cfg.bg[0]; acc1[k] = cfg.bg[1]; acc2[k] = cfg.bg[2]; accD[k] = 0.f; accO[k] = 0.f;
+    S[k] = 0.f;
     if (!(x < ws.width && y < ws.height)) continue;
     const int64_t p = (int64_t)y * ws.width + x;
     T[k] = a.t_final[v * HW + p];
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
       if (a.dl_dopac) gO[k] = a.dl_dopac[v * HW + p];
     }
     mx = max(mx, last[k]);
+    S[k] = gC0[k] * cfg.bg[0] + gC1[k] * cfg.bg[1] + gC2[k] * cfg.bg[2];
   }
   // CTA reductions: loss sum and the longest contributor prefix
 #pragma unroll
@@ -205,14 +208,9 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
         const float al = fminf(a_max, araw);
         T[k] = __fdividef(T[k], 1.f - al);  // transmittance in front of this Gaussian (1 - al >= 0.01)
         const float w = al * T[k];
-        const float dA = T[k] * (gC0[k] * (c.x - acc0[k]) + gC1[k] * (c.y - acc1[k]) + gC2[k] * (c.z - acc2[k]) +
-                                 gD[k] * (g1.z - accD[k]) + gO[k] * (1.f - accO[k]));
-        const float om = 1.f - al;
-        acc0[k] = al * c.x + om * acc0[k];
-        acc1[k] = al * c.y + om * acc1[k];
-        acc2[k] = al * c.z + om * acc2[k];
-        accD[k] = al * g1.z + om * accD[k];
-        accO[k] = al + om * accO[k];
+        const float gx = fmaf(gC0[k], c.x, fmaf(gC1[k], c.y, fmaf(gC2[k], c.z, fmaf(gD[k], g1.z, gO[k]))));
+        const float dA = T[k] * (gx - S[k]);  // dL/dalpha
+        S[k] = fmaf(al, gx - S[k], S[k]);
         val[6] += gD[k] * w;
         val[7] += gC0[k] * w;
         val[8] += gC1[k] * w;

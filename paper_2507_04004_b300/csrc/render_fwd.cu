@@ -15,14 +15,14 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
                                                           float* __restrict__ t_final,
                                                           uint32_t* __restrict__ n_contrib) {
   constexpr int NT = 256 / PPT;  // threads per tile
-  constexpr int RS = 16 / PPT;   // row stride between a thread's pixels
+  // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
   __shared__ float4 s_g0[256], s_g1[256], s_c[256];
   const int64_t tile = blockIdx.x;
   const int v = (int)(tile / ws.tiles_per_view);
   const int t = (int)(tile - (int64_t)v * ws.tiles_per_view);
   const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
   const int x = tx * kTile + (threadIdx.x & 15);
-  const int yb = ty * kTile + (threadIdx.x >> 4);
+  const int yb = ty * kTile + PPT * (threadIdx.x >> 4);
   const float px = (float)x + 0.5f;
   const bool ok_status = ws.counters[kStatus] == 0;
   const uint32_t start = ok_status ? ws.tile_start[tile] : 0u;
@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     T[k] = 1.f; C0[k] = C1[k] = C2[k] = D[k] = 0.f; last[k] = 0;
-    py[k] = (float)(yb + k * RS) + 0.5f;
-    done[k] = !(x < ws.width && yb + k * RS < ws.height);
+    py[k] = (float)(yb + k) + 0.5f;
+    done[k] = !(x < ws.width && yb + k < ws.height);
     all_done &= done[k];
   }
   for (uint32_t b0 = 0; b0 < cnt; b0 += 256) {
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   const int64_t HW = (int64_t)ws.width * ws.height;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int y = yb + k * RS;
+    const int y = yb + k;
     if (!(x < ws.width && y < ws.height)) continue;
     const int64_t p = (int64_t)y * ws.width + x;
     if (rgb) {

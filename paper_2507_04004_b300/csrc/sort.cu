@@ -14,7 +14,6 @@
 namespace gsb {
 
 constexpr int kScanThreads = 1024;
-constexpr int kSmallCap = 2048;      // keys sorted by a 256-thread CTA (16 KB)
 constexpr int kLongCap = 16384;      // keys sorted by a 1024-thread CTA (128 KB)
 
 // Exclusive scan of n counts by one CTA: start[i] = sum of counts before i,
@@ -105,22 +104,72 @@ __device__ __forceinline__ void sort_tile_smem(const Ws& ws, unsigned long long*
   __syncthreads();
 }
 
+// Register bitonic sort of one bin of n <= 32 E keys by one warp.  Element
+// i = e * 32 + lane lives in register v[e] of that lane: compare distances
+// j < 32 exchange across lanes with shuffles, larger ones stay in-thread.
+template <int E>
+__device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int n, int lane) {
+  constexpr int N = 32 * E;
+  unsigned long long v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    v[e] = i < n ? ws.keys[start + i] : ~0ull;
+  }
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int je = j >> 5;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (e & je) continue;
+          const int f = e | je;
+          const bool asc = ((e * 32 + lane) & k) == 0;
+          const unsigned long long a = v[e], b = v[f];
+          if ((a > b) == asc) { v[e] = b; v[f] = a; }
+        }
+      } else {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const bool asc = ((e * 32 + lane) & k) == 0;
+          const unsigned long long b = __shfl_xor_sync(kFull, v[e], j);
+          const bool keep_min = lower == asc;
+          v[e] = keep_min ? (v[e] < b ? v[e] : b) : (v[e] < b ? b : v[e]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * 32 + lane;
+    if (i < n) ws.sorted_ids[start + i] = (uint32_t)(v[e] & 0xffffffffull);
+  }
+}
+
+constexpr int kWarpCap = 1024;  // bins sorted by one warp in registers
+
+// One warp per bin; bins longer than kWarpCap go to the long-bin list.
 __global__ void __launch_bounds__(256) k_sort_small(Ws ws) {
-  __shared__ unsigned long long s[kSmallCap];
   if (ws.counters[kStatus] != 0) return;
-  const int64_t t = blockIdx.x;
-  const uint32_t cnt = ws.tile_count[t];
-  if (cnt == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (t >= (int64_t)ws.views * ws.tiles_per_view) return;
+  const int n = (int)ws.tile_count[t];
+  if (n == 0) return;
   const uint32_t start = ws.tile_start[t];
-  if (cnt == 1) {
-    if (threadIdx.x == 0) ws.sorted_ids[start] = (uint32_t)(ws.keys[start] & 0xffffffffull);
+  if (n > kWarpCap) {
+    if (lane == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
     return;
   }
-  if (cnt > (uint32_t)kSmallCap) {
-    if (threadIdx.x == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
-    return;
-  }
-  sort_tile_smem(ws, s, start, (int)cnt);
+  if (n <= 32) warp_sort_bin<1>(ws, start, n, lane);
+  else if (n <= 64) warp_sort_bin<2>(ws, start, n, lane);
+  else if (n <= 128) warp_sort_bin<4>(ws, start, n, lane);
+  else if (n <= 256) warp_sort_bin<8>(ws, start, n, lane);
+  else if (n <= 512) warp_sort_bin<16>(ws, start, n, lane);
+  else warp_sort_bin<32>(ws, start, n, lane);
 }
 
 // Merge-path split: number of elements of A among the first d outputs of
@@ -203,7 +252,7 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   if ((err = launch_rows(ws, 2, st)) != cudaSuccess) return err;
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKSortSmall, st);
-  k_sort_small<<<ntiles, 256, 0, st>>>(ws);
+  k_sort_small<<<(ntiles + 7) / 8, 256, 0, st>>>(ws);
   trace_end(st);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
