@@ -17,7 +17,9 @@ namespace gsb {
 constexpr int kTile = 16;
 constexpr int kTilePixels = kTile * kTile;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBlendPPT = 2;  // pixels per thread in the blend kernels (a tile is 256 / kBlendPPT threads)
+// pixels per thread in the blend kernels (a tile is 256 / PPT threads)
+constexpr int kFwdPPT = 4;
+constexpr int kBwdPPT = 4;
 
 // Device view of the workspace parts (pointers resolved from gs_layout).
 struct Ws {

@@ -185,17 +185,24 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
     __syncthreads();
     for (int j = nb - 1; j >= 0; --j) {
       const float4 g0 = s_g0[j], g1 = s_g1[j];
-      const uint64_t pos = (uint64_t)(beg + j);
+      const uint32_t pos = (uint32_t)(beg + j);
+      const float dx = px - g0.x;
       float p2[PPT];
       bool act[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         p2[k] = blend_p2(g0, g1, px, py[k]);
-        act[k] = pos < last[k] && p2[k] >= lt;
+        act[k] = (pos < last[k]) & (p2[k] >= lt);
         any |= act[k];
       }
       if (!__any_sync(kFull, any)) continue;
+      // Per-Gaussian sums over this thread's pixels.  With dp = dL/dpower
+      // (power = -q/2, zero where alpha is clamped), the conic and opacity
+      // gradients need only the moments of dp; their constant factors are
+      // applied once per Gaussian when the CTA's sums are flushed:
+      //   val[0..5] = sum dp dx, dp dy, dp dx^2, dp dx dy, dp dy^2, dp
+      //   val[6..9] = sum gD w, gC w (w = alpha T)
       float val[10];
 #pragma unroll
       for (int q = 0; q < 10; ++q) val[q] = 0.f;
@@ -204,29 +211,25 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
       for (int k = 0; k < PPT; ++k) {
         if (!act[k]) continue;
         const float araw = exp2f(p2[k]);
-        const bool clamped = araw > a_max;
         const float al = fminf(a_max, araw);
         T[k] = __fdividef(T[k], 1.f - al);  // transmittance in front of this Gaussian (1 - al >= 0.01)
         const float w = al * T[k];
         const float gx = fmaf(gC0[k], c.x, fmaf(gC1[k], c.y, fmaf(gC2[k], c.z, fmaf(gD[k], g1.z, gO[k]))));
         const float dA = T[k] * (gx - S[k]);  // dL/dalpha
         S[k] = fmaf(al, gx - S[k], S[k]);
-        val[6] += gD[k] * w;
-        val[7] += gC0[k] * w;
-        val[8] += gC1[k] * w;
-        val[9] += gC2[k] * w;
-        if (!clamped) {
-          // alpha = o exp(power): dL/dpower = dA alpha, dL/do = dA alpha / o
-          const float dpow = dA * al;
-          const float dx = px - g0.x, dy = py[k] - g0.y;
-          // a dx + b dy = -ln2 (2 ha dx + hb dy), b dx + c dy = -ln2 (hb dx + 2 hc dy)
-          val[0] -= dpow * kLn2 * (2.f * g0.z * dx + g0.w * dy);
-          val[1] -= dpow * kLn2 * (g0.w * dx + 2.f * g1.x * dy);
-          val[2] -= 0.5f * dpow * dx * dx;
-          val[3] -= dpow * dx * dy;
-          val[4] -= 0.5f * dpow * dy * dy;
-          val[5] += dpow * g1.w;
-        }
+        val[6] = fmaf(gD[k], w, val[6]);
+        val[7] = fmaf(gC0[k], w, val[7]);
+        val[8] = fmaf(gC1[k], w, val[8]);
+        val[9] = fmaf(gC2[k], w, val[9]);
+        const float dp = araw > a_max ? 0.f : dA * al;  // alpha = o exp(power): dL/dpower = dL/dalpha alpha
+        const float dy = py[k] - g0.y;
+        const float t = dp * dx, u = dp * dy;
+        val[0] += t;
+        val[1] += u;
+        val[2] = fmaf(t, dx, val[2]);
+        val[3] = fmaf(t, dy, val[3]);
+        val[4] = fmaf(u, dy, val[4]);
+        val[5] += dp;
       }
       int slot;
       const float sum = warp_reduce_scatter10(val, lane, &slot);
@@ -235,9 +238,15 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += NT) {
       const float* q = s_acc[i];
+      const float4 g0 = s_g0[i], g1 = s_g1[i];
+      // d power / d mx = a dx + b dy, with a = -2 ln2 ha, b = -ln2 hb, c = -2 ln2 hc;
+      // d power / d(a, b, c) = (-dx^2/2, -dx dy, -dy^2/2); d alpha / d o = alpha / o
+      const float gmx = -kLn2 * (2.f * g0.z * q[0] + g0.w * q[1]);
+      const float gmy = -kLn2 * (g0.w * q[0] + 2.f * g1.x * q[1]);
+      const float ga = -0.5f * q[2], gb = -q[3], gc = -0.5f * q[4], go = q[5] * g1.w;
       float4* dst = adj + 3 * (int64_t)s_gid[i];
-      if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f) atomicAdd(dst, make_float4(q[0], q[1], q[2], q[3]));
-      if (q[4] != 0.f || q[5] != 0.f || q[6] != 0.f) atomicAdd(dst + 1, make_float4(q[4], q[5], q[6], 0.f));
+      if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f) atomicAdd(dst, make_float4(gmx, gmy, ga, gb));
+      if (q[4] != 0.f || q[5] != 0.f || q[6] != 0.f) atomicAdd(dst + 1, make_float4(gc, go, q[6], 0.f));
       if (q[7] != 0.f || q[8] != 0.f || q[9] != 0.f) atomicAdd(dst + 2, make_float4(q[7], q[8], q[9], 0.f));
     }
   }
@@ -251,8 +260,13 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
                                                         gs_config cfg, Ws ws, BwdArgs a) {
   __shared__ float s_pose[8][6];
   constexpr int K = (DEG + 1) * (DEG + 1);
-  // SH gradient accumulators live in shared memory (column per thread)
-  __shared__ float s_gsh[3 * K][256];
+  // SH gradient accumulators and the Gaussian's SH coefficients live in
+  // shared memory (one column per thread): coefficients are fetched once, with
+  // independent coalesced loads, and reused by every view
+  // (dynamic shared memory: 2 * 3K * 256 floats, up to 96 KB)
+  extern __shared__ float s_dyn[];
+  float(*s_gsh)[256] = reinterpret_cast<float(*)[256]>(s_dyn);
+  float(*s_sh)[256] = reinterpret_cast<float(*)[256]>(s_dyn + 3 * K * 256);
   const int64_t n = ws.n;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in_range = g < n;
@@ -271,6 +285,10 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
     ls[0] = map.log_scale[g]; ls[1] = map.log_scale[n + g]; ls[2] = map.log_scale[2 * n + g];
     q[0] = map.quat[g]; q[1] = map.quat[n + g]; q[2] = map.quat[2 * n + g]; q[3] = map.quat[3 * n + g];
     logit = map.logit_opacity[g];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) s_sh[3 * k + ch][threadIdx.x] = sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
   }
   const float qi = rsqrtf(fmaxf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3], 1e-30f));
   const float qw = q[0] * qi, qx = q[1] * qi, qy = q[2] * qi, qz = q[3] * qi;
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
       for (int ch = 0; ch < 3; ++ch) {
         float raw = 0.5f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) raw += sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch) * Y[k];
+        for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
         graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
       for (int k = 0; k < K; ++k) {
         wk[k] = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
+        for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * s_sh[3 * k + ch][threadIdx.x];
       }
       const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
       const float gdir[3] = {gd3.x, gd3.y, gd3.z};
@@ -466,8 +484,13 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
 template <int DEG, bool BF16>
 static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                   const BwdArgs& a, cudaStream_t st) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const size_t smem = (size_t)2 * 3 * K * 256 * sizeof(float);
+  cudaError_t err =
+      cudaFuncSetAttribute(k_preprocess_bwd<DEG, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
   trace_begin(kKPreprocessBwd, st);
-  k_preprocess_bwd<DEG, BF16><<<(unsigned)((ws.n + 255) / 256), 256, 0, st>>>(map, cams, cfg, ws, a);
+  k_preprocess_bwd<DEG, BF16><<<(unsigned)((ws.n + 255) / 256), 256, smem, st>>>(map, cams, cfg, ws, a);
   trace_end(st);
   return cudaGetLastError();
 }
@@ -488,8 +511,8 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
   }
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKRenderBwd, st);
-  if (fused) k_render_bwd<true, kBlendPPT><<<ntiles, 256 / kBlendPPT, 0, st>>>(cfg, ws, a);
-  else k_render_bwd<false, kBlendPPT><<<ntiles, 256 / kBlendPPT, 0, st>>>(cfg, ws, a);
+  if (fused) k_render_bwd<true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  else k_render_bwd<false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   const bool bf = map.sh_bf16 != 0;

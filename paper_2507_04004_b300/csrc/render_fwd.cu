@@ -105,7 +105,7 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const Ws& ws, float* rgb, fl
                               float* t_final, uint32_t* n_contrib, cudaStream_t st) {
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKRenderFwd, st);
-  k_render_fwd<kBlendPPT><<<ntiles, 256 / kBlendPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib);
+  k_render_fwd<kFwdPPT><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib);
   trace_end(st);
   return cudaGetLastError();
 }

@@ -107,6 +107,22 @@ __device__ __forceinline__ void sort_tile_smem(const Ws& ws, unsigned long long*
 // Register bitonic sort of one bin of n <= 32 E keys by one warp.  Element
 // i = e * 32 + lane lives in register v[e] of that lane: compare distances
 // j < 32 exchange across lanes with shuffles, larger ones stay in-thread.
+// Stage loops run at run time (small code); only the loops over a thread's E
+// elements are unrolled.
+template <int E, int JE>
+__device__ __forceinline__ void warp_sort_intra(unsigned long long* v, int k, int lane) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e & JE) continue;
+    const int f = e | JE;
+    const bool asc = ((e * 32 + lane) & k) == 0;
+    const unsigned long long a = v[e], b = v[f];
+    const bool swap = (a > b) == asc;
+    v[e] = swap ? b : a;
+    v[f] = swap ? a : b;
+  }
+}
+
 template <int E>
 __device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int n, int lane) {
   constexpr int N = 32 * E;
@@ -116,19 +132,17 @@ __device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int 
     const int i = e * 32 + lane;
     v[e] = i < n ? ws.keys[start + i] : ~0ull;
   }
-#pragma unroll
+#pragma unroll 1
   for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
     for (int j = k >> 1; j > 0; j >>= 1) {
       if (j >= 32) {
-        const int je = j >> 5;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (e & je) continue;
-          const int f = e | je;
-          const bool asc = ((e * 32 + lane) & k) == 0;
-          const unsigned long long a = v[e], b = v[f];
-          if ((a > b) == asc) { v[e] = b; v[f] = a; }
+        switch (j >> 5) {
+          case 1: warp_sort_intra<E, 1>(v, k, lane); break;
+          case 2: warp_sort_intra<E, (E > 2 ? 2 : 1)>(v, k, lane); break;
+          case 4: warp_sort_intra<E, (E > 4 ? 4 : 1)>(v, k, lane); break;
+          case 8: warp_sort_intra<E, (E > 8 ? 8 : 1)>(v, k, lane); break;
+          default: warp_sort_intra<E, (E > 16 ? 16 : 1)>(v, k, lane); break;
         }
       } else {
         const bool lower = (lane & j) == 0;
@@ -152,7 +166,7 @@ __device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int 
 constexpr int kWarpCap = 1024;  // bins sorted by one warp in registers
 
 // One warp per bin; bins longer than kWarpCap go to the long-bin list.
-__global__ void __launch_bounds__(256) k_sort_small(Ws ws) {
+__global__ void __launch_bounds__(256, 2) k_sort_small(Ws ws) {
   if (ws.counters[kStatus] != 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
