@@ -310,8 +310,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
     if (vis) {
       float4* ad = ws.adjoints + 3 * e;
       const float4 A0 = ad[0], A1 = ad[1], A2 = ad[2];
-      // consume: leave the adjoint area zero for the next backward of this projection
-      ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
       const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
       const float gcol[3] = {A2.x, A2.y, A2.z};
       const Cam cam = load_cam(cams, v);
@@ -338,7 +337,6 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
         Vv[k] = s[k] * rm1[k];
       }
       // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
-      const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
       const float qa = R0.z, qb = R0.w, qc = R1.x;
       // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
       const float hb = 0.5f * gb;
@@ -417,6 +415,8 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
 #pragma unroll
       for (int j = 0; j < 3; ++j) g_mu[j] += gWm[j] + gv[j];
       g_o += gop;
+      // consume: leave the adjoint area zero for the next backward of this projection
+      ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (want_pose) {
         // right perturbation T Exp(xi), xi = (rho, theta):
         //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
@@ -462,23 +462,41 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   const float gzq = 2.f * (-2.f * qz * g_R[0][0] - qw * g_R[0][1] + qx * g_R[0][2] + qw * g_R[1][0] -
                            2.f * qz * g_R[1][1] + qy * g_R[1][2] + qx * g_R[2][0] + qy * g_R[2][1]);
   const float dq = qw * gw + qx * gxq + qy * gyq + qz * gzq;
-  a.grad_quat[g] += (gw - qw * dq) * qi;
-  a.grad_quat[n + g] += (gxq - qx * dq) * qi;
-  a.grad_quat[2 * n + g] += (gyq - qy * dq) * qi;
-  a.grad_quat[3 * n + g] += (gzq - qz * dq) * qi;
+  // Add to the caller's gradients.  The loads of a group are issued before
+  // any of its stores: the gradient arrays may alias as far as the compiler
+  // knows, so interleaved read-modify-writes would serialise on memory latency.
+  {
+    float* dst[11] = {a.grad_quat + g,         a.grad_quat + n + g,     a.grad_quat + 2 * n + g,
+                      a.grad_quat + 3 * n + g, a.grad_mean + g,         a.grad_mean + n + g,
+                      a.grad_mean + 2 * n + g, a.grad_log_scale + g,    a.grad_log_scale + n + g,
+                      a.grad_log_scale + 2 * n + g, a.grad_logit + g};
+    const float add[11] = {(gw - qw * dq) * qi, (gxq - qx * dq) * qi, (gyq - qy * dq) * qi, (gzq - qz * dq) * qi,
+                           g_mu[0], g_mu[1], g_mu[2], g_s[0] * s[0], g_s[1] * s[1], g_s[2] * s[2],
+                           g_o * o * (1.f - o)};
+    float cur[11];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    a.grad_mean[j * n + g] += g_mu[j];
-    a.grad_log_scale[j * n + g] += g_s[j] * s[j];
+    for (int i = 0; i < 11; ++i) cur[i] = *dst[i];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) *dst[i] = cur[i] + add[i];
   }
-  a.grad_logit[g] += g_o * o * (1.f - o);
+  constexpr int kGroup = 8;
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) a.grad_sh_dc[ch * n + g] += s_gsh[ch][threadIdx.x];
+  for (int q0 = 0; q0 < 3 * K; q0 += kGroup) {
+    float cur[kGroup];
 #pragma unroll
-  for (int k = 1; k < K; ++k)
+    for (int i = 0; i < kGroup; ++i) {
+      const int q = q0 + i;
+      if (q < 3 * K) cur[i] = q < 3 ? a.grad_sh_dc[q * n + g] : a.grad_sh_rest[(int64_t)(q - 3) * n + g];
+    }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-      a.grad_sh_rest[((int64_t)(k - 1) * 3 + ch) * n + g] += s_gsh[3 * k + ch][threadIdx.x];
+    for (int i = 0; i < kGroup; ++i) {
+      const int q = q0 + i;
+      if (q >= 3 * K) continue;
+      const float v = cur[i] + s_gsh[q][threadIdx.x];
+      if (q < 3) a.grad_sh_dc[q * n + g] = v;
+      else a.grad_sh_rest[(int64_t)(q - 3) * n + g] = v;
+    }
+  }
 }
 
 template <int DEG, bool BF16>
