@@ -163,27 +163,126 @@ __device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int 
   }
 }
 
-constexpr int kWarpCap = 1024;  // bins sorted by one warp in registers
+constexpr int kRadixCap = 2048;  // bins sorted by one CTA's radix sort in shared memory
+constexpr int kRadixThreads = 256;
 
-// One warp per bin; bins longer than kWarpCap go to the long-bin list.
-__global__ void __launch_bounds__(256, 2) k_sort_small(Ws ws) {
+// One CTA per bin.  Bins of up to 64 keys: warp register bitonic on the full
+// 64-bit key.  Up to kRadixCap keys: stable LSD radix sort on the 32-bit depth
+// key (four 8-bit digits; a pass whose digit is the same for every key is
+// skipped), each warp ranking its contiguous share with __match_any_sync, then
+// runs of equal depth keys (rare) ordered by Gaussian index.  Longer bins go to
+// the long-bin list.
+__global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
+  constexpr int NW = kRadixThreads / 32;
+  __shared__ uint32_t s_key[2][kRadixCap];
+  __shared__ uint32_t s_val[2][kRadixCap];
+  __shared__ uint32_t s_hist[NW][256];
+  __shared__ uint32_t s_tot[256];
+  __shared__ int s_skip[4];  // one flag per pass: no thread can still be reading a reset flag
   if (ws.counters[kStatus] != 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (t >= (int64_t)ws.views * ws.tiles_per_view) return;
+  const int64_t t = blockIdx.x;
   const int n = (int)ws.tile_count[t];
   if (n == 0) return;
   const uint32_t start = ws.tile_start[t];
-  if (n > kWarpCap) {
-    if (lane == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (n > kRadixCap) {
+    if (threadIdx.x == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
     return;
   }
-  if (n <= 32) warp_sort_bin<1>(ws, start, n, lane);
-  else if (n <= 64) warp_sort_bin<2>(ws, start, n, lane);
-  else if (n <= 128) warp_sort_bin<4>(ws, start, n, lane);
-  else if (n <= 256) warp_sort_bin<8>(ws, start, n, lane);
-  else if (n <= 512) warp_sort_bin<16>(ws, start, n, lane);
-  else warp_sort_bin<32>(ws, start, n, lane);
+  if (n <= 64) {
+    if (warp == 0) {
+      if (n <= 32) warp_sort_bin<1>(ws, start, n, lane);
+      else warp_sort_bin<2>(ws, start, n, lane);
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+    const unsigned long long k = ws.keys[start + i];
+    s_key[0][i] = (uint32_t)(k >> 32);
+    s_val[0][i] = (uint32_t)(k & 0xffffffffull);
+  }
+  if (threadIdx.x < 4) s_skip[threadIdx.x] = 0;
+  const int chunk = ((n + NW - 1) / NW + 31) & ~31;  // each warp's contiguous share, whole rounds
+  const int w0 = min(n, warp * chunk), w1 = min(n, w0 + chunk);
+  int src = 0;
+  for (int shift = 0; shift < 32; shift += 8) {
+    const int pass = shift >> 3;
+    for (int i = threadIdx.x; i < NW * 256; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
+    __syncthreads();
+    for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&s_hist[warp][(s_key[src][i] >> shift) & 255u], 1u);
+    __syncthreads();
+    {
+      // digit-major exclusive scan: offsets[w][d] = sum_{d' < d} tot[d'] + sum_{w' < w} hist[w'][d]
+      const int d = threadIdx.x;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t h = s_hist[w][d];
+        s_hist[w][d] = run;
+        run += h;
+      }
+      s_tot[d] = run;
+      if (run == (uint32_t)n) s_skip[pass] = 1;
+    }
+    __syncthreads();
+    if (s_skip[pass]) continue;  // every key has this digit: the pass keeps the order
+    {
+      // exclusive scan of s_tot over the 256 digits (one warp)
+      if (warp == 0) {
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { v[q] = s_tot[lane * 8 + q]; sum += v[q]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, inc, o);
+          if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { const uint32_t c = v[q]; s_tot[lane * 8 + q] = run; run += c; }
+      }
+      __syncthreads();
+      const int d = threadIdx.x;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s_hist[w][d] += s_tot[d];
+    }
+    __syncthreads();
+    const int dst = src ^ 1;
+    for (int base = w0; base < w1; base += 32) {
+      const int i = base + lane;
+      const unsigned active = __ballot_sync(kFull, i < w1);
+      if (i < w1) {
+        const uint32_t key = s_key[src][i];
+        const uint32_t dg = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(active, dg);
+        const uint32_t pos = s_hist[warp][dg] + __popc(peers & ((1u << lane) - 1u));
+        s_key[dst][pos] = key;
+        s_val[dst][pos] = s_val[src][i];
+        __syncwarp(active);
+        if (lane == __ffs(peers) - 1) s_hist[warp][dg] += __popc(peers);
+      }
+      __syncwarp();
+    }
+    src = dst;
+    __syncthreads();
+  }
+  // runs of equal depth keys: order by Gaussian index (insertion sort per run)
+  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+    const uint32_t k = s_key[src][i];
+    if ((i == 0 || s_key[src][i - 1] != k) && i + 1 < n && s_key[src][i + 1] == k) {
+      int e = i + 1;
+      while (e < n && s_key[src][e] == k) ++e;
+      for (int a = i + 1; a < e; ++a) {
+        const uint32_t v = s_val[src][a];
+        int b = a - 1;
+        while (b >= i && s_val[src][b] > v) { s_val[src][b + 1] = s_val[src][b]; --b; }
+        s_val[src][b + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kRadixThreads) ws.sorted_ids[start + i] = s_val[src][i];
 }
 
 // Merge-path split: number of elements of A among the first d outputs of
@@ -266,7 +365,7 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   if ((err = launch_rows(ws, 2, st)) != cudaSuccess) return err;
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKSortSmall, st);
-  k_sort_small<<<(ntiles + 7) / 8, 256, 0, st>>>(ws);
+  k_sort_small<<<ntiles, kRadixThreads, 0, st>>>(ws);
   trace_end(st);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
