@@ -219,11 +219,28 @@ __device__ __forceinline__ Staged stage_gaussian(float4 r0, float4 r1) {
   return s;
 }
 
+// p2 = dy (hc dy + hb dx) + (ha dx^2 + log2 o): the bracketed terms depend on
+// the pixel column only, so a thread that owns a column of pixels forms them
+// once (col_terms) and pays three operations per pixel (col_p2).
+struct ColTerms {
+  float A;   // ha dx^2 + log2 o
+  float B;   // hb dx
+  float hc;
+  float my;
+};
+
+__device__ __forceinline__ ColTerms col_terms(float4 g0, float4 g1, float px) {
+  const float dx = __fsub_rn(px, g0.x);
+  return ColTerms{__fmaf_rn(__fmul_rn(g0.z, dx), dx, g1.y), __fmul_rn(g0.w, dx), g1.x, g0.y};
+}
+
+__device__ __forceinline__ float col_p2(const ColTerms& c, float py) {
+  const float dy = __fsub_rn(py, c.my);
+  return __fmaf_rn(dy, __fmaf_rn(c.hc, dy, c.B), c.A);
+}
+
 __device__ __forceinline__ float blend_p2(float4 g0, float4 g1, float px, float py) {
-  const float dx = __fsub_rn(px, g0.x), dy = __fsub_rn(py, g0.y);
-  const float t = __fmaf_rn(g0.w, dy, __fmul_rn(g0.z, dx));  // ha dx + hb dy
-  const float u = __fmaf_rn(g1.x, __fmul_rn(dy, dy), g1.y);   // hc dy^2 + log2 o
-  return __fmaf_rn(t, dx, u);
+  return col_p2(col_terms(g0, g1, px), py);
 }
 
 // ----------------------------------------------------------------------------

@@ -187,12 +187,13 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
       const float4 g0 = s_g0[j], g1 = s_g1[j];
       const uint32_t pos = (uint32_t)(beg + j);
       const float dx = px - g0.x;
+      const ColTerms ct = col_terms(g0, g1, px);
       float p2[PPT];
       bool act[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        p2[k] = blend_p2(g0, g1, px, py[k]);
+        p2[k] = col_p2(ct, py[k]);
         act[k] = (pos < last[k]) & (p2[k] >= lt);
         any |= act[k];
       }

@@ -56,11 +56,12 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     __syncthreads();
     for (uint32_t j = 0; j < nb && !all_done; ++j) {
       const float4 g0 = s_g0[j], g1 = s_g1[j];
+      const ColTerms ct = col_terms(g0, g1, px);
       all_done = true;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
+        const float p2 = col_p2(ct, py[k]);
         if (!done[k]) {
-          const float p2 = blend_p2(g0, g1, px, py[k]);
           if (p2 >= lt) {
             const float al = fminf(a_max, exp2f(p2));
             const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));

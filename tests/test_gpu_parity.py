@@ -281,3 +281,20 @@ def test_pose_jacobian_rows_match_oracle(oracle):
         scale = np.abs(Jo[ok]).max()
         err = np.abs(J[v][ok] - Jo[ok]).max() / scale
         assert err <= GRAD_TOL, f"view {v}: J relative error {err:.3e}"
+
+
+@pytest.mark.parametrize("n", [40, 600])
+def test_equal_depth_keys_sort_by_index(oracle, n):
+    """Many Gaussians at exactly the same depth (identity pose, equal z): the
+    per-tile order must fall back to the Gaussian index, both for short bins
+    (warp sort) and for radix-sorted bins."""
+    rng = np.random.default_rng(n)
+    means = np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), np.full(n, 5.0)], 1)
+    m = one_gaussian_map(means, np.full(n, math.log(0.08)), rng.normal(0, 1, n), rng.random((n, 3)))
+    g = synth.GaussianMap(**{k: np.asarray(v, np.float32) if isinstance(v, np.ndarray) else v
+                             for k, v in m.items()})
+    cam = synth.camera(np.eye(3), np.zeros(3), 60.0, 60.0, 24.0, 24.0, 48, 48)
+    rast, gm, ct, out = gpu_render(g, [cam])
+    assert len(set(oracle.depth_keys(host_map(g), cam).tolist())) == 1
+    compare_tiles(oracle, host_map(g), cam, rast, 0)
+    _check_images(oracle.render(host_map(g), cam), out, 0, "equal depths")
