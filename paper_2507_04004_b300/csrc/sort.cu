@@ -168,17 +168,17 @@ constexpr int kRadixThreads = 256;
 
 // One CTA per bin.  Bins of up to 64 keys: warp register bitonic on the full
 // 64-bit key.  Up to kRadixCap keys: stable LSD radix sort on the 32-bit depth
-// key (four 8-bit digits; a pass whose digit is the same for every key is
-// skipped), each warp ranking its contiguous share with __match_any_sync, then
-// runs of equal depth keys (rare) ordered by Gaussian index.  Longer bins go to
-// the long-bin list.
+// key (8-bit digits; a pass whose digit is the same for every key is skipped),
+// each warp ranking its contiguous share with __match_any_sync, then short
+// runs of equal keys ordered by (key, Gaussian index).  Longer bins go to the
+// long-bin list.
 __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
   constexpr int NW = kRadixThreads / 32;
   __shared__ uint32_t s_key[2][kRadixCap];
   __shared__ uint32_t s_val[2][kRadixCap];
   __shared__ uint32_t s_hist[NW][256];
   __shared__ uint32_t s_tot[256];
-  __shared__ int s_skip[4];  // one flag per pass: no thread can still be reading a reset flag
+  __shared__ int s_skip[8];  // one flag per pass: no thread can still be reading a reset flag
   if (ws.counters[kStatus] != 0) return;
   const int64_t t = blockIdx.x;
   const int n = (int)ws.tile_count[t];
@@ -201,12 +201,12 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
     s_key[0][i] = (uint32_t)(k >> 32);
     s_val[0][i] = (uint32_t)(k & 0xffffffffull);
   }
-  if (threadIdx.x < 4) s_skip[threadIdx.x] = 0;
+  if (threadIdx.x < 8) s_skip[threadIdx.x] = 0;
   const int chunk = ((n + NW - 1) / NW + 31) & ~31;  // each warp's contiguous share, whole rounds
   const int w0 = min(n, warp * chunk), w1 = min(n, w0 + chunk);
-  int src = 0;
-  for (int shift = 0; shift < 32; shift += 8) {
-    const int pass = shift >> 3;
+  int src = 0, pass = 0;
+  // one stable LSD pass on the 8-bit digit at `shift`
+  auto radix_pass = [&](int shift) {
     for (int i = threadIdx.x; i < NW * 256; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&s_hist[warp][(s_key[src][i] >> shift) & 255u], 1u);
@@ -225,7 +225,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
       if (run == (uint32_t)n) s_skip[pass] = 1;
     }
     __syncthreads();
-    if (s_skip[pass]) continue;  // every key has this digit: the pass keeps the order
+    if (s_skip[pass]) {  // every key has this digit: the pass keeps the order
+      ++pass;
+      return;
+    }
     {
       // exclusive scan of s_tot over the 256 digits (one warp)
       if (warp == 0) {
@@ -266,18 +269,50 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
     }
     src = dst;
     __syncthreads();
-  }
-  // runs of equal depth keys: order by Gaussian index (insertion sort per run)
+    ++pass;
+  };
+  // Two passes order the bin by the top 16 bits of the depth key; runs that
+  // share those bits are then finished by insertion on (key, index).  A run
+  // longer than 32 keys (near-constant depth) sends the bin through all four
+  // passes instead, so the fix-up stays short.
+  radix_pass(16);
+  radix_pass(24);
+  if (threadIdx.x == 0) s_tot[0] = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += kRadixThreads) {
-    const uint32_t k = s_key[src][i];
-    if ((i == 0 || s_key[src][i - 1] != k) && i + 1 < n && s_key[src][i + 1] == k) {
+    const uint32_t hi = s_key[src][i] >> 16;
+    if (i == 0 || (s_key[src][i - 1] >> 16) != hi) {
       int e = i + 1;
-      while (e < n && s_key[src][e] == k) ++e;
+      while (e < n && (s_key[src][e] >> 16) == hi && e - i <= 32) ++e;
+      if (e - i > 32) atomicMax(&s_tot[0], (uint32_t)(e - i));
+    }
+  }
+  __syncthreads();
+  const bool full = s_tot[0] > 32;
+  __syncthreads();
+  if (full) {
+    radix_pass(0);
+    radix_pass(8);
+    radix_pass(16);
+    radix_pass(24);
+  }
+  const uint32_t mask = full ? 0xffffffffu : 0xffff0000u;
+  // runs of equal (masked) keys: insertion sort on (key, Gaussian index)
+  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+    const uint32_t k = s_key[src][i] & mask;
+    if ((i == 0 || (s_key[src][i - 1] & mask) != k) && i + 1 < n && (s_key[src][i + 1] & mask) == k) {
+      int e = i + 1;
+      while (e < n && (s_key[src][e] & mask) == k) ++e;
       for (int a = i + 1; a < e; ++a) {
-        const uint32_t v = s_val[src][a];
+        const uint32_t ka = s_key[src][a], va = s_val[src][a];
         int b = a - 1;
-        while (b >= i && s_val[src][b] > v) { s_val[src][b + 1] = s_val[src][b]; --b; }
-        s_val[src][b + 1] = v;
+        while (b >= i && (s_key[src][b] > ka || (s_key[src][b] == ka && s_val[src][b] > va))) {
+          s_key[src][b + 1] = s_key[src][b];
+          s_val[src][b + 1] = s_val[src][b];
+          --b;
+        }
+        s_key[src][b + 1] = ka;
+        s_val[src][b + 1] = va;
       }
     }
   }
