@@ -397,8 +397,12 @@ def run_ours(args):
         "rows_emit": ("hbm", n_pairs * 8 + n_rows * (8 + 4 + 16)),
         "rows_count": ("hbm", n_rows * (8 + 32 + 4)),
         "sort_small": ("hbm", n_pairs * (8 + 4)),
-        "render_fwd": ("alu", k_eval * 27.0),
-        "render_bwd": ("alu", k_eval * 75.0),
+        # FP32 FLOP per (pixel, list position up to its last contributor), FMA = 2 (roofline):
+        # forward: weight 6, exp2 1, clamp 1, transmittance 2, w 1, colour+depth 8  -> 19
+        # backward: weight 6, exp2 1, clamp 1, 1-alpha 1, T recovery 1, w 1, adjoint dot 8,
+        #           dL/dalpha 2, behind-sum 2, colour+depth sums 8, dL/dpower 1, moments 11 -> 43
+        "render_fwd": ("alu", k_eval * 19.0),
+        "render_bwd": ("alu", k_eval * 43.0),
         "preprocess_bwd": ("hbm", n_visible * (48 + 48) + args.n * V * 8 + n_visible * (236 + 2 * 236) / V),
     }
     bound, amount = alg.get(dominant, ("hbm", 0))

@@ -71,13 +71,14 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int la
 }
 
 template <bool FUSED, int PPT>
-__global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+__global__ void __launch_bounds__(256 / PPT, 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
-  __shared__ float4 s_g0[256], s_g1[256], s_c[256];
-  __shared__ uint32_t s_gid[256];
-  __shared__ float s_acc[256][10];
+  constexpr int NB = kBwdBatch;  // Gaussians staged per batch
+  __shared__ float4 s_g0[NB], s_g1[NB], s_c[NB];
+  __shared__ uint32_t s_gid[NB];
+  __shared__ float s_acc[NB][10];
   __shared__ float s_red[NW];
   __shared__ uint32_t s_max[NW];
   if (ws.counters[kStatus] != 0) return;
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(256 / PPT) k_render_bwd(gs_config cfg, Ws ws, 
   // ---- back-to-front walk
   const float a_max = cfg.alpha_max;
   const float lt = __log2f(cfg.alpha_min);
-  for (int64_t end = max_last; end > 0; end -= 256) {
-    const int64_t beg = end > 256 ? end - 256 : 0;
+  for (int64_t end = max_last; end > 0; end -= NB) {
+    const int64_t beg = end > NB ? end - NB : 0;
     const int nb = (int)(end - beg);
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += NT) {
