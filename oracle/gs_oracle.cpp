@@ -764,26 +764,34 @@ int32_t ocl_pose_jacobian(const ocl_map* m, const ocl_camera* cam, const ocl_con
   const int64_t n = m->n;
   ViewCache vc;
   build_view(*m, *cam, *cfg, 0.0, false, 0, 0, cam->width, cam->height, &vc);
-  std::vector<Proj<Dual<6>>> pd(n);
+  // dual-number projections only for the Gaussians that contribute to a listed pixel
+  std::vector<PixelState> states(n_pix);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int32_t k = 0; k < n_pix; ++k)
+    composite_pixel(vc, *cfg, pix[k] % cam->width, pix[k] / cam->width, 0.0, &states[k]);
+  std::vector<int32_t> slot(n, -1), used;
+  for (int32_t k = 0; k < n_pix; ++k)
+    for (int32_t g : states[k].gid)
+      if (slot[g] < 0) { slot[g] = (int32_t)used.size(); used.push_back(g); }
+  std::vector<Proj<Dual<6>>> pd(used.size());
 #pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t gi = 0; gi < n; ++gi) {
-    if (!vc.proj[gi].valid) continue;
+  for (int64_t u = 0; u < (int64_t)used.size(); ++u) {
+    const int64_t gi = used[u];
     GaussIn<Dual<6>> g = load_gauss<Dual<6>>(*m, gi);
     Dual<6> xi[6], Wd[9], td[3];
     for (int k = 0; k < 6; ++k) { xi[k] = Dual<6>(0.0); xi[k].d[k] = 1.0; }
     perturb_pose<Dual<6>>(cam->R, cam->t, xi, Wd, td);
-    pd[gi] = project_one<Dual<6>>(g, m->sh_degree, Wd, td, *cam, *cfg, key_of(*m, *cam, gi));
+    pd[u] = project_one<Dual<6>>(g, m->sh_degree, Wd, td, *cam, *cfg, key_of(*m, *cam, gi));
   }
 #pragma omp parallel for schedule(dynamic, 16)
   for (int32_t k = 0; k < n_pix; ++k) {
     const int px = pix[k] % cam->width, py = pix[k] / cam->width;
-    PixelState st;
-    composite_pixel(vc, *cfg, px, py, 0.0, &st);
+    const PixelState& st = states[k];
     Dual<6> C[3] = {Dual<6>(0.0), Dual<6>(0.0), Dual<6>(0.0)};
     Dual<6> T(1.0);
     const double cxp = px + 0.5, cyp = py + 0.5;
     for (size_t c = 0; c < st.gid.size(); ++c) {
-      const Proj<Dual<6>>& p = pd[st.gid[c]];
+      const Proj<Dual<6>>& p = pd[slot[st.gid[c]]];
       Dual<6> dx = cxp - p.mx, dy = cyp - p.my;
       Dual<6> q = p.ca * dx * dx + 2.0 * p.cb * dx * dy + p.cc * dy * dy;
       Dual<6> a = st.clamped[c] ? Dual<6>(cfg->alpha_max) : p.o * exp(-0.5 * q);

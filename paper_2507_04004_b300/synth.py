@@ -265,3 +265,39 @@ def top_gradient_pixels(img, k) -> np.ndarray:
     vals = mag.reshape(-1)[lin]
     order = np.lexsort((lin, -vals))
     return np.sort(lin[order[:k]]).astype(np.int32)
+
+
+def se3_right_perturb(R, t, xi) -> tuple[np.ndarray, np.ndarray]:
+    """World-to-camera (R, t) composed with Exp(xi) on the right, xi = (rho, theta)."""
+    from scipy.linalg import expm
+    X = np.zeros((4, 4))
+    rho, th = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    X[:3, :3] = [[0, -th[2], th[1]], [th[2], 0, -th[0]], [-th[1], th[0], 0]]
+    X[:3, 3] = rho
+    T = np.eye(4)
+    T[:3, :3], T[:3, 3] = R, t
+    Tp = T @ expm(X)
+    return Tp[:3, :3].astype(np.float32), Tp[:3, 3].astype(np.float32)
+
+
+def tracking(seed=SEED_BASE + 4, n=1_000_000, n_frames=32, width=640, height=512, focal=500.0, sh_degree=1,
+             n_pix=20_000) -> Workload:
+    """Tracking frames: a map in the 60x20x60 m box, ground-truth poses in the
+    central half of the box, query poses GT Exp(xi) with theta ~ N(0, 0.02 rad)
+    and rho ~ N(0, 0.05 m) per axis, smooth random targets and, per frame, the
+    n_pix interior pixels with the largest target-image gradient."""
+    rng = np.random.default_rng(seed)
+    lo, hi = (-30.0, -10.0, -30.0), (30.0, 10.0, 30.0)
+    g = random_map(rng, n, lo, hi, sh_degree)
+    gt, cams, tgts, pix = [], [], [], []
+    xis = pose_perturbations(rng, n_frames)
+    for f, (centre, Rc) in enumerate(tracking_poses(rng, n_frames, lo, hi)):
+        R, t = pose_from_centre(Rc, centre)
+        gt.append(camera(R, t, focal, focal, width / 2, height / 2, width, height))
+        Rq, tq = se3_right_perturb(np.asarray(R, np.float64), np.asarray(t, np.float64), xis[f])
+        cams.append(camera(Rq, tq, focal, focal, width / 2, height / 2, width, height))
+        img = smooth_target(rng, height, width)
+        tgts.append(img)
+        pix.append(top_gradient_pixels(img, n_pix))
+    return Workload("tracking", g, cams, np.stack(tgts), None, 1.0, 0.0,
+                    meta=dict(gt_cams=gt, xi=xis, pix=np.stack(pix)))
