@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
+    p.add_argument("--serving-requests", type=int, default=400,
+                   help="requests in the serving measurement (0 skips it); the full serving workload has 10,000")
     return p.parse_args()
 
 
@@ -294,6 +296,130 @@ def run_e2e(args, d, rast, gm, w, px_step):
             "d2h_bytes_per_step": ms_step.d2h_bytes}
 
 
+def serving_workload(n_requests: int, seed: int = 2507_04004 + 5):
+    """3M-Gaussian map (SH 3, BF16), requests: 70 % renders at 640x360,
+    1280x720 or 1920x1080 (focal 0.52 W) and 30 % tracking-Jacobian requests at
+    640x512 with the 20k highest-gradient pixels, random poses inside the map,
+    Poisson arrivals at 200 requests/s."""
+    import numpy as np
+
+    from paper_2507_04004_b300 import synth
+    from paper_2507_04004_b300.serve import Request
+    rng = np.random.default_rng(seed)
+    lo, hi = (-30.0, -10.0, -30.0), (30.0, 10.0, 30.0)
+    g = synth.random_map(rng, 3_000_000, lo, hi, 3)
+    pool = []
+    for _ in range(4):  # a few tracking targets / pixel selections, reused
+        img = synth.smooth_target(rng, 512, 640)
+        pix = synth.top_gradient_pixels(img, 20_000)
+        pool.append((pix, img.reshape(3, -1)[:, pix].T.copy()))
+    sizes = [(640, 360), (1280, 720), (1920, 1080)]
+    reqs = []
+    for i, (centre, Rc) in enumerate(synth.tracking_poses(rng, n_requests, lo, hi)):
+        R, t = synth.pose_from_centre(Rc, centre)
+        if rng.random() < 0.3:
+            pix, tgt = pool[i % len(pool)]
+            reqs.append(Request("jacobian", synth.camera(R, t, 500.0, 500.0, 320, 256, 640, 512), pix=pix, target=tgt))
+        else:
+            W, H = sizes[int(rng.integers(0, 3))]
+            reqs.append(Request("render", synth.camera(R, t, 0.52 * W, 0.52 * W, W / 2, H / 2, W, H)))
+    gaps = rng.exponential(1.0 / 200.0, n_requests)
+    return g, reqs, np.cumsum(gaps)
+
+
+def run_serving(args, dev):
+    """p50/p99 latency under Poisson arrivals and closed-loop throughput,
+    batched server vs plain one-request-at-a-time rendering."""
+    import copy
+    import threading
+
+    import torch
+
+    from paper_2507_04004_b300.raster import GaussianMap
+    from paper_2507_04004_b300.serve import PlainRenderer, Server, latency_stats
+    g, reqs, arrivals = serving_workload(args.serving_requests)
+    gm = GaussianMap.from_host(g, device=dev, sh_bf16=True)
+    fresh = lambda: [copy.copy(r) for r in reqs]
+    out = {"workload": f"3M Gaussians SH3 BF16, {len(reqs)} requests, Poisson 200/s, 70% renders "
+                       "(640x360/1280x720/1920x1080), 30% tracking Jacobians (640x512, 20k px)",
+           "mem_budget_gib": 4}
+
+    def open_loop(submit_one, rs):
+        t0 = time.perf_counter()
+        for r, t in zip(rs, arrivals):
+            wait = t0 + t - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            submit_one(r)
+
+    # batched server
+    srv = Server(gm, mem_budget=4 << 30, max_views=4, n_streams=4, pairs_per_pixel=8.0, device=dev)
+    srv.warmup({r.key for r in reqs})
+    srv.start()
+    rs = fresh()
+    for r in rs:
+        r.future = type(r.future)()
+    open_loop(lambda r: srv.submit(r), rs)
+    for r in rs:
+        r.future.result()
+    out["server_open_loop"] = latency_stats(rs)
+    rs = fresh()
+    for r in rs:
+        r.future = type(r.future)()
+    t0 = time.perf_counter()
+    for r in rs:
+        srv.submit(r)
+    for r in rs:
+        r.future.result()
+    out["server_req_per_s"] = len(rs) / (time.perf_counter() - t0)
+    srv.stop()
+    out["server_batches"] = srv.batches
+    out["server_retries"] = srv.retries
+    out["server_max_inflight_sort_gib"] = round(srv.max_inflight_bytes / 2 ** 30, 3)
+    del srv
+    torch.cuda.empty_cache()
+
+    # plain path: one worker, FIFO, one launch sequence per request
+    plain = PlainRenderer(gm, device=dev)
+    for r in reqs[:8]:
+        plain.run(r)  # warm-up
+    rs = fresh()
+    q, done_all = [], threading.Event()
+    lock = threading.Condition()
+
+    def worker():
+        k = 0
+        while k < len(rs):
+            with lock:
+                while len(q) <= k:
+                    lock.wait()
+            r = q[k]
+            plain.run(r)
+            r.done = time.perf_counter()
+            k += 1
+        done_all.set()
+
+    th = threading.Thread(target=worker)
+    th.start()
+
+    def submit_plain(r):
+        r.arrival = time.perf_counter()
+        with lock:
+            q.append(r)
+            lock.notify()
+    open_loop(submit_plain, rs)
+    done_all.wait()
+    th.join()
+    out["plain_open_loop"] = latency_stats(rs)
+    rs = fresh()
+    t0 = time.perf_counter()
+    for r in rs:
+        plain.run(r)
+    out["plain_req_per_s"] = len(rs) / (time.perf_counter() - t0)
+    out["throughput_ratio"] = out["server_req_per_s"] / out["plain_req_per_s"]
+    return out
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_ours(args):
     import numpy as np
@@ -422,6 +548,12 @@ def run_ours(args):
     total_px = d.sum(px_step * args.steps)
     value = total_px / (ms / 1e3) / 1e6
 
+    serving = None
+    if d.rank == 0 and args.serving_requests > 0:
+        del out, grads
+        torch.cuda.empty_cache()
+        serving = run_serving(args, d.dev)
+
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -442,6 +574,7 @@ def run_ours(args):
                 "gpu_launches": int(launches),
                 "roofline": roofline,
                 "cpu_baseline": cpu,
+                "serving": serving,
                 "kernels": kernels,
                 "work": {"visible_entries": n_visible, "pairs": n_pairs, "row_items": n_rows,
                          "blend_evaluations": k_eval,

@@ -1,0 +1,353 @@
+"""Continuous-batching server for novel-view renders and tracking Jacobians.
+
+Requests (a camera pose at some resolution; tracking requests add pixel
+indices and target colours) arrive against one device-resident Gaussian map
+(arxiv 2507.04004: novel-view rendering at a queried pose, Sec. "Video Frame
+Interpolation"/"Rapid Mesh Reconstruction" use-cases; tracking with camera
+factor option 2, Sec. "Camera Factor (Option 2)").  The server
+
+* groups waiting requests by (kind, resolution) and packs up to ``max_views``
+  of them into one multi-view launch of the rasterizer (views folded into the
+  tile index, so every kernel runs once for the whole batch);
+* admits a batch only while the workspaces of the batches in flight stay
+  within ``mem_budget`` bytes (the sort buffers dominate a workspace);
+* replays a CUDA graph captured per (kind, resolution, slot count) with the
+  request cameras copied into the graph's camera buffer;
+* runs batches on a pool of streams so that batches formed while others are
+  on the GPU overlap with them, and resolves each request's future when its
+  batch's completion event fires.
+
+All rasterizer work runs in the CUDA kernels of ``libgsb300.so``.  A batch whose
+pair buffer overflowed (device status word) is re-run eagerly with a larger
+buffer and its graph re-captured.
+"""
+from __future__ import annotations
+
+import collections
+import queue
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .raster import GaussianMap, Rasterizer, RenderOut, cameras_tensor
+
+
+# Bytes of a workspace that scale with its pair capacity (the sort buffers):
+# 64-bit keys, 64-bit merge buffer, 32-bit sorted indices, 64-bit row items,
+# 32-bit row spans.
+SORT_BYTES_PER_PAIR = 8 + 8 + 4 + 8 + 4
+
+
+@dataclass
+class Request:
+    kind: str                      # "render" or "jacobian"
+    camera: dict                   # synth.camera(...) dict (pose + intrinsics + size)
+    pix: np.ndarray | None = None  # jacobian: int32 linear pixel indices
+    target: np.ndarray | None = None  # jacobian: [n_pix][3] target colours
+    arrival: float = 0.0           # time.perf_counter() at submission (set by submit)
+    done: float = 0.0
+    future: Future = field(default_factory=Future)
+
+    @property
+    def key(self):
+        c = self.camera
+        npix = 0 if self.pix is None else len(self.pix)
+        return (self.kind, int(c["width"]), int(c["height"]), npix)
+
+
+def _slot_counts(max_views):
+    s, out = 1, []
+    while s <= max_views:
+        out.append(s)
+        s *= 2
+    return out
+
+
+class _Runner:
+    """Workspace, buffers and (optionally) a captured graph for one
+    (kind, resolution, slot count)."""
+
+    def __init__(self, server, key, slots, capacity):
+        kind, W, H, npix = key
+        self.server, self.key, self.slots = server, key, slots
+        dev = server.device
+        self.rast = Rasterizer(server.gmap.n, slots, W, H, pair_capacity=capacity, device=dev)
+        self.cams = torch.zeros(slots, 16, device=dev)
+        f = dict(device=dev, dtype=torch.float32)
+        self.out = RenderOut(torch.empty(slots, 3, H, W, **f), torch.empty(slots, H, W, **f),
+                             torch.empty(slots, H, W, **f), torch.empty(slots, H, W, **f),
+                             torch.empty(slots, H, W, dtype=torch.int32, device=dev))
+        self.jac = kind == "jacobian"
+        if self.jac:
+            self.pix = torch.zeros(slots, npix, dtype=torch.int32, device=dev)
+            self.J = torch.empty(slots, npix, 3, 6, **f)
+            self.jrgb = torch.empty(slots, npix, 3, **f)
+            self.host_J = torch.empty(slots, npix, 3, 6, pin_memory=True)
+            self.host_jrgb = torch.empty(slots, npix, 3, pin_memory=True)
+        else:
+            self.host_rgb = torch.empty(slots, 3, H, W, pin_memory=True)
+            self.host_depth = torch.empty(slots, H, W, pin_memory=True)
+        self.host_cams = torch.empty(slots, 16, pin_memory=True)
+        self.host_pix = torch.empty(slots, npix, dtype=torch.int32, pin_memory=True) if self.jac else None
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.host_status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        self.graph = None
+        self.event = torch.cuda.Event()
+        self.busy = False
+        self.bytes = SORT_BYTES_PER_PAIR * self.rast.capacity
+
+    # -- the device work of one batch (captured once per runner)
+    def _work(self):
+        gm = self.server.gmap
+        self.rast.project_and_sort(gm, self.cams, check=False)
+        N.gs_render_fwd(self.rast.cfg, self.rast.ws, self.out.rgb, self.out.depth, self.out.opac,
+                        self.out.t_final, self.out.n_contrib, torch.cuda.current_stream(self.server.device).cuda_stream)
+        if self.jac:
+            N.gs_pose_jacobian(gm.struct(), self.cams, self.rast.cfg, self.rast.ws, self.pix, self.pix.shape[1],
+                               self.J, self.jrgb, torch.cuda.current_stream(self.server.device).cuda_stream)
+        cnt = self.rast._view(self.rast.layout.counters, 1, torch.int32)
+        self.status.copy_(cnt)
+
+    def capture(self):
+        s = torch.cuda.Stream(device=self.server.device)
+        with torch.cuda.stream(s):
+            self._work()  # warm-up outside the capture (sets kernel attributes)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            self._work()
+        self.graph = g
+
+    def launch(self, reqs, stream):
+        """Copy inputs, run, copy results to pinned host buffers (async)."""
+        n = len(reqs)
+        for i, r in enumerate(reqs):
+            self.host_cams[i] = torch.as_tensor(cameras_tensor([r.camera], device="cpu")[0])
+            if self.jac:
+                self.host_pix[i] = torch.as_tensor(r.pix)
+        for i in range(n, self.slots):  # unused slots repeat the first camera
+            self.host_cams[i] = self.host_cams[0]
+            if self.jac:
+                self.host_pix[i] = self.host_pix[0]
+        with torch.cuda.stream(stream):
+            self.cams.copy_(self.host_cams, non_blocking=True)
+            if self.jac:
+                self.pix.copy_(self.host_pix, non_blocking=True)
+            if self.graph is not None and self.server.use_graphs:
+                self.graph.replay()
+            else:
+                self._work()
+            if self.jac:
+                self.host_J[:n].copy_(self.J[:n], non_blocking=True)
+                self.host_jrgb[:n].copy_(self.jrgb[:n], non_blocking=True)
+            else:
+                self.host_rgb[:n].copy_(self.out.rgb[:n], non_blocking=True)
+                self.host_depth[:n].copy_(self.out.depth[:n], non_blocking=True)
+            self.host_status.copy_(self.status, non_blocking=True)
+            self.event.record(stream)
+
+    def results(self, reqs):
+        out = []
+        for i, r in enumerate(reqs):
+            if self.jac:
+                J = self.host_J[i].numpy().copy()
+                rgb = self.host_jrgb[i].numpy().copy()
+                res = rgb - (r.target if r.target is not None else 0.0)
+                out.append(dict(J=J, rgb=rgb, residual=res))
+            else:
+                out.append(dict(rgb=self.host_rgb[i].numpy().copy(), depth=self.host_depth[i].numpy().copy()))
+        return out
+
+
+class Server:
+    """Continuous batching over one device-resident map (see module docs)."""
+
+    def __init__(self, gmap: GaussianMap, mem_budget: int = 4 << 30, max_views: int = 8, n_streams: int = 4,
+                 use_graphs: bool = True, pairs_per_pixel: float = 4.0, device="cuda"):
+        self.gmap, self.mem_budget, self.max_views = gmap, int(mem_budget), int(max_views)
+        self.use_graphs = use_graphs
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.pairs_per_pixel = float(pairs_per_pixel)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
+        self.runners: dict = collections.defaultdict(list)
+        self.waiting: dict = collections.defaultdict(collections.deque)
+        self.inbox: queue.Queue = queue.Queue()
+        self.inflight = []          # (runner, reqs)
+        self.inflight_bytes = 0
+        self.max_inflight_bytes = 0
+        self._stop = threading.Event()
+        self._thread = None
+        self._stream_rr = 0
+        self.batches = 0
+        self.retries = 0
+
+    # ---------------------------------------------------------------- setup
+    def _capacity(self, key, slots):
+        _, W, H, _ = key
+        return max(1 << 16, int(self.pairs_per_pixel * W * H * slots))
+
+    def _runner(self, key, slots):
+        """A free runner for (key, slots), creating (and capturing) one if none is free."""
+        for r in self.runners[(key, slots)]:
+            if not r.busy:
+                return r
+        r = _Runner(self, key, slots, self._capacity(key, slots))
+        if self.use_graphs:
+            r.capture()
+        self.runners[(key, slots)].append(r)
+        return r
+
+    def warmup(self, keys):
+        """Create and capture one runner per (key, slot count) before serving."""
+        for key in keys:
+            for s in _slot_counts(self.max_views):
+                self._runner(key, s)
+        torch.cuda.synchronize(self.device)
+
+    # ---------------------------------------------------------------- API
+    def submit(self, req: Request) -> Future:
+        req.arrival = time.perf_counter()
+        self.inbox.put(req)
+        return req.future
+
+    def start(self):
+        self._thread = threading.Thread(target=self._loop, daemon=True)
+        self._thread.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._thread is not None:
+            self._thread.join()
+
+    # ---------------------------------------------------------------- loop
+    def _loop(self):
+        try:
+            self._run()
+        except BaseException as exc:  # never leave callers waiting on a dead loop
+            pending = [r for _, rs in self.inflight for r in rs] + [r for q in self.waiting.values() for r in q]
+            while not self.inbox.empty():
+                pending.append(self.inbox.get_nowait())
+            for r in pending:
+                if not r.future.done():
+                    r.future.set_exception(exc)
+            raise
+
+    def _run(self):
+        torch.cuda.set_device(self.device)
+        while not self._stop.is_set() or self.inflight or any(self.waiting.values()) or not self.inbox.empty():
+            self._drain_inbox()
+            self._complete()
+            launched = self._schedule()
+            if not launched and not self.inflight:
+                try:
+                    req = self.inbox.get(timeout=0.001)
+                    self.waiting[req.key].append(req)
+                except queue.Empty:
+                    pass
+            elif not launched:
+                time.sleep(0)
+
+    def _drain_inbox(self):
+        while True:
+            try:
+                req = self.inbox.get_nowait()
+            except queue.Empty:
+                return
+            self.waiting[req.key].append(req)
+
+    def _schedule(self) -> bool:
+        launched = False
+        # oldest waiting request first
+        keys = sorted((k for k, q in self.waiting.items() if q), key=lambda k: self.waiting[k][0].arrival)
+        for key in keys:
+            q = self.waiting[key]
+            while q:
+                n = min(len(q), self.max_views)
+                slots = next(s for s in _slot_counts(self.max_views) if s >= n)
+                runner = None
+                for r in self.runners[(key, slots)]:
+                    if not r.busy:
+                        runner = r
+                        break
+                if runner is None:
+                    need = SORT_BYTES_PER_PAIR * self._capacity(key, slots)
+                    if self.inflight_bytes + need > self.mem_budget and self.inflight:
+                        return launched  # admission: wait for sort-buffer memory to free up
+                    runner = self._runner(key, slots)
+                if self.inflight_bytes + runner.bytes > self.mem_budget and self.inflight:
+                    return launched
+                reqs = [q.popleft() for _ in range(n)]
+                runner.busy = True
+                stream = self.streams[self._stream_rr % len(self.streams)]
+                self._stream_rr += 1
+                runner.launch(reqs, stream)
+                self.inflight.append((runner, reqs))
+                self.inflight_bytes += runner.bytes
+                self.max_inflight_bytes = max(self.max_inflight_bytes, self.inflight_bytes)
+                self.batches += 1
+                launched = True
+        return launched
+
+    def _complete(self):
+        still = []
+        for runner, reqs in self.inflight:
+            if not runner.event.query():
+                still.append((runner, reqs))
+                continue
+            if int(runner.host_status[0]) != 0:
+                # pair buffer overflow inside the graph: grow, re-run eagerly, re-capture
+                self.retries += 1
+                self.inflight_bytes -= runner.bytes
+                runner.rast.project_and_sort(self.gmap, runner.cams, check=True)
+                runner.bytes = SORT_BYTES_PER_PAIR * runner.rast.capacity
+                self.inflight_bytes += runner.bytes
+                runner.graph = None
+                if self.use_graphs:
+                    runner.capture()
+                runner.launch(reqs, self.streams[0])
+                runner.event.synchronize()
+            t = time.perf_counter()
+            for r, res in zip(reqs, runner.results(reqs)):
+                r.done = t
+                r.future.set_result(res)
+            runner.busy = False
+            self.inflight_bytes -= runner.bytes
+        self.inflight = still
+
+
+class PlainRenderer:
+    """One request at a time, one launch sequence per request, no graphs: the
+    reference point for the server."""
+
+    def __init__(self, gmap: GaussianMap, device="cuda"):
+        self.gmap = gmap
+        self.device = torch.device(device)
+        self.rasts = {}
+
+    def run(self, req: Request):
+        kind, W, H, npix = req.key
+        key = (W, H)
+        if key not in self.rasts:
+            self.rasts[key] = Rasterizer(self.gmap.n, 1, W, H, device=self.device)
+        rast = self.rasts[key]
+        cams = cameras_tensor([req.camera], device=self.device)
+        out = rast.render(self.gmap, cams, check=True)
+        if kind == "jacobian":
+            pix = torch.as_tensor(req.pix, device=self.device).view(1, -1)
+            J, rgb = rast.pose_jacobian(self.gmap, cams, pix)
+            J, rgb = J[0].cpu().numpy(), rgb[0].cpu().numpy()
+            return dict(J=J, rgb=rgb, residual=rgb - (req.target if req.target is not None else 0.0))
+        return dict(rgb=out.rgb[0].cpu().numpy(), depth=out.depth[0].cpu().numpy())
+
+
+def latency_stats(reqs):
+    lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
+    return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                mean_ms=float(lat.mean()), n=len(lat))

@@ -1,0 +1,59 @@
+"""Continuous-batching server (needs a GPU): every request's result is the
+same alone (plain one-launch-per-request path) and inside a mixed, batched,
+overlapping stream; the sort-buffer budget bounds what is in flight."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_04004_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(rng, n, box_lo, box_hi):
+    from paper_2507_04004_b300.serve import Request
+    sizes = [(160, 96), (320, 176), (480, 272)]
+    reqs = []
+    img = synth.smooth_target(rng, 96, 128)
+    pix = synth.top_gradient_pixels(img, 500)
+    tgt = img.reshape(3, -1)[:, pix].T.copy()
+    for i, (centre, Rc) in enumerate(synth.tracking_poses(rng, n, box_lo, box_hi)):
+        R, t = synth.pose_from_centre(Rc, centre)
+        if i % 3 == 2:
+            cam = synth.camera(R, t, 100.0, 100.0, 64, 48, 128, 96)
+            reqs.append(Request("jacobian", cam, pix=pix, target=tgt))
+        else:
+            W, H = sizes[i % len(sizes)]
+            cam = synth.camera(R, t, 0.6 * W, 0.6 * W, W / 2, H / 2, W, H)
+            reqs.append(Request("render", cam))
+    return reqs
+
+
+@pytest.mark.parametrize("use_graphs", [True, False])
+def test_results_alone_equal_results_in_the_mix(use_graphs):
+    from paper_2507_04004_b300.raster import GaussianMap
+    from paper_2507_04004_b300.serve import PlainRenderer, Server
+    rng = np.random.default_rng(1)
+    lo, hi = (-6.0, -2.0, -6.0), (6.0, 2.0, 6.0)
+    g = synth.random_map(rng, 30000, lo, hi, 3, log_scale_mean=-2.3)
+    gm = GaussianMap.from_host(g, sh_bf16=True)
+    reqs = _requests(rng, 24, lo, hi)
+    budget = 64 << 20
+    srv = Server(gm, mem_budget=budget, max_views=4, n_streams=3, use_graphs=use_graphs, pairs_per_pixel=6.0)
+    srv.warmup({r.key for r in reqs})
+    srv.start()
+    futs = [srv.submit(r) for r in reqs]  # all at once: batches form and overlap
+    res = [f.result(timeout=120) for f in futs]
+    srv.stop()
+    assert srv.batches < len(reqs)
+    assert srv.max_inflight_bytes <= max(budget, max(r.bytes for rs in srv.runners.values() for r in rs))
+    plain = PlainRenderer(gm)
+    for r, got in zip(reqs, res):
+        alone = plain.run(r)
+        if r.kind == "render":
+            assert np.array_equal(got["rgb"], alone["rgb"]) and np.array_equal(got["depth"], alone["depth"])
+        else:
+            assert np.array_equal(got["rgb"], alone["rgb"])
+            scale = np.abs(alone["J"]).max()
+            assert np.abs(got["J"] - alone["J"]).max() <= 1e-3 * scale
+            np.testing.assert_allclose(got["residual"], alone["rgb"] - r.target, atol=1e-6)
