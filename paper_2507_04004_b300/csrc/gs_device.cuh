@@ -244,6 +244,19 @@ __device__ __forceinline__ float blend_p2(float4 g0, float4 g1, float px, float 
   return col_p2(col_terms(g0, g1, px), py);
 }
 
+// Packed FP32 pairs: the blend kernels evaluate two vertically adjacent
+// pixels per instruction with the sm_100+ f32x2 FMA/ADD/MUL.  Each half is
+// rounded exactly like the scalar __fmaf_rn / __fadd_rn / __fmul_rn, so
+// col_p2x2 returns the bits col_p2 returns for each pixel.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 col_p2x2(const ColTerms& c, float2 py) {
+  const float2 dy = __fadd2_rn(py, f2(-c.my));
+  return __ffma2_rn(dy, __ffma2_rn(f2(c.hc), dy, f2(c.B)), f2(c.A));
+}
+
 // ----------------------------------------------------------------------------
 // Tile culling (Sec. "Fast Tile-based Culling"): a tile is kept iff one of its
 // pixel centres lies in the ellipse q <= q_thr, q_thr = 2 ln(o / alpha_min),

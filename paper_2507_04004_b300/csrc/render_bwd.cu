@@ -165,7 +165,20 @@ __global__ void __launch_bounds__(256 / PPT, 2048 / (256 / PPT) / 2) k_render_bw
     if (tot != 0.f) atomicAdd(a.loss + v, tot);
   }
 
-  // ---- back-to-front walk
+  // ---- back-to-front walk over vertical pixel pairs (k = 2h, 2h + 1)
+  constexpr int NP = PPT / 2;
+  float2 C0[NP], C1[NP], C2[NP], GD[NP], GO[NP], T2[NP], S2[NP], Y[NP];
+#pragma unroll
+  for (int h = 0; h < NP; ++h) {
+    C0[h] = make_float2(gC0[2 * h], gC0[2 * h + 1]);
+    C1[h] = make_float2(gC1[2 * h], gC1[2 * h + 1]);
+    C2[h] = make_float2(gC2[2 * h], gC2[2 * h + 1]);
+    GD[h] = make_float2(gD[2 * h], gD[2 * h + 1]);
+    GO[h] = make_float2(gO[2 * h], gO[2 * h + 1]);
+    T2[h] = make_float2(T[2 * h], T[2 * h + 1]);
+    S2[h] = make_float2(S[2 * h], S[2 * h + 1]);
+    Y[h] = make_float2(py[2 * h], py[2 * h + 1]);
+  }
   const float a_max = cfg.alpha_max;
   const float lt = __log2f(cfg.alpha_min);
   for (int64_t end = max_last; end > 0; end -= NB) {
@@ -189,14 +202,15 @@ __global__ void __launch_bounds__(256 / PPT, 2048 / (256 / PPT) / 2) k_render_bw
       const uint32_t pos = (uint32_t)(beg + j);
       const float dx = px - g0.x;
       const ColTerms ct = col_terms(g0, g1, px);
-      float p2[PPT];
+      float2 p2[NP];
       bool act[PPT];
       bool any = false;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        p2[k] = col_p2(ct, py[k]);
-        act[k] = (pos < last[k]) & (p2[k] >= lt);
-        any |= act[k];
+      for (int h = 0; h < NP; ++h) {
+        p2[h] = col_p2x2(ct, Y[h]);
+        act[2 * h] = (pos < last[2 * h]) & (p2[h].x >= lt);
+        act[2 * h + 1] = (pos < last[2 * h + 1]) & (p2[h].y >= lt);
+        any |= act[2 * h] | act[2 * h + 1];
       }
       if (!__any_sync(kFull, any)) continue;
       // Per-Gaussian sums over this thread's pixels.  With dp = dL/dpower
@@ -205,34 +219,52 @@ __global__ void __launch_bounds__(256 / PPT, 2048 / (256 / PPT) / 2) k_render_bw
       // applied once per Gaussian when the CTA's sums are flushed:
       //   val[0..5] = sum dp dx, dp dy, dp dx^2, dp dx dy, dp dy^2, dp
       //   val[6..9] = sum gD w, gC w (w = alpha T)
-      float val[10];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) val[q] = 0.f;
+      // The thread's pixels share one column (dx) and sit at dy = dy0 + k, so
+      // the six moments follow from m_i = sum k^i dp, i = 0, 1, 2.
+      // Pixels run in vertical pairs, branch-free: an inactive pixel gets
+      // alpha = 0, for which every update below leaves its state unchanged.
       const float4 c = s_c[j];
+      const float2 cr = f2(c.x), cg = f2(c.y), cb = f2(c.z), dep = f2(g1.z);
+      float2 v6 = f2(0.f), v7 = f2(0.f), v8 = f2(0.f), v9 = f2(0.f);
+      float2 M0 = f2(0.f), M1 = f2(0.f), M2 = f2(0.f);
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (!act[k]) continue;
-        const float araw = exp2f(p2[k]);
-        const float al = fminf(a_max, araw);
-        T[k] = __fdividef(T[k], 1.f - al);  // transmittance in front of this Gaussian (1 - al >= 0.01)
-        const float w = al * T[k];
-        const float gx = fmaf(gC0[k], c.x, fmaf(gC1[k], c.y, fmaf(gC2[k], c.z, fmaf(gD[k], g1.z, gO[k]))));
-        const float dA = T[k] * (gx - S[k]);  // dL/dalpha
-        S[k] = fmaf(al, gx - S[k], S[k]);
-        val[6] = fmaf(gD[k], w, val[6]);
-        val[7] = fmaf(gC0[k], w, val[7]);
-        val[8] = fmaf(gC1[k], w, val[8]);
-        val[9] = fmaf(gC2[k], w, val[9]);
-        const float dp = araw > a_max ? 0.f : dA * al;  // alpha = o exp(power): dL/dpower = dL/dalpha alpha
-        const float dy = py[k] - g0.y;
-        const float t = dp * dx, u = dp * dy;
-        val[0] += t;
-        val[1] += u;
-        val[2] = fmaf(t, dx, val[2]);
-        val[3] = fmaf(t, dy, val[3]);
-        val[4] = fmaf(u, dy, val[4]);
-        val[5] += dp;
+      for (int h = 0; h < NP; ++h) {
+        const bool a0 = act[2 * h], a1 = act[2 * h + 1];
+        const float e0 = exp2f(p2[h].x), e1 = exp2f(p2[h].y);
+        const float2 al = make_float2(a0 ? fminf(a_max, e0) : 0.f, a1 ? fminf(a_max, e1) : 0.f);
+        // alpha = o exp(power): dL/dpower = dL/dalpha alpha, zero where alpha is clamped
+        const float2 ag = make_float2(e0 > a_max ? 0.f : al.x, e1 > a_max ? 0.f : al.y);
+        const float2 om = fma2(al, f2(-1.f), f2(1.f));  // 1 - alpha >= 0.01
+        // transmittance in front of this Gaussian
+        T2[h] = mul2(T2[h], make_float2(a0 ? __fdividef(1.f, om.x) : 1.f, a1 ? __fdividef(1.f, om.y) : 1.f));
+        const float2 w = mul2(al, T2[h]);
+        const float2 gx = fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, fma2(GD[h], dep, GO[h]))));
+        const float2 e = fma2(S2[h], f2(-1.f), gx);
+        const float2 dA = mul2(T2[h], e);  // dL/dalpha
+        S2[h] = fma2(al, e, S2[h]);
+        v6 = fma2(GD[h], w, v6);
+        v7 = fma2(C0[h], w, v7);
+        v8 = fma2(C1[h], w, v8);
+        v9 = fma2(C2[h], w, v9);
+        const float2 dp = mul2(dA, ag);
+        M0 = add2(M0, dp);
+        M1 = fma2(dp, make_float2((float)(2 * h), (float)(2 * h + 1)), M1);
+        M2 = fma2(dp, make_float2((float)(4 * h * h), (float)((2 * h + 1) * (2 * h + 1))), M2);
       }
+      float val[10];
+      const float m0 = M0.x + M0.y, m1 = M1.x + M1.y, m2 = M2.x + M2.y;
+      const float dy0 = Y[0].x - g0.y;
+      const float sy = fmaf(dy0, m0, m1);  // sum dp dy
+      val[0] = dx * m0;
+      val[1] = sy;
+      val[2] = dx * val[0];
+      val[3] = dx * sy;
+      val[4] = fmaf(dy0, sy + m1, m2);     // dy0^2 m0 + 2 dy0 m1 + m2
+      val[5] = m0;
+      val[6] = v6.x + v6.y;
+      val[7] = v7.x + v7.y;
+      val[8] = v8.x + v8.y;
+      val[9] = v9.x + v9.y;
       int slot;
       const float sum = warp_reduce_scatter10(val, lane, &slot);
       if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) atomicAdd(&s_acc[j][slot], sum);

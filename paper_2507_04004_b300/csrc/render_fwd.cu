@@ -31,16 +31,23 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   const float a_max = cfg.alpha_max, t_min = cfg.t_min;
   const float lt = __log2f(cfg.alpha_min);
 
-  float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], py[PPT];
+  // pixels run in vertical pairs (k = 2h, 2h + 1) through packed FP32 pairs
+  constexpr int NP = PPT / 2;
+  float2 T[NP], C0[NP], C1[NP], C2[NP], D[NP], Y[NP];
   uint32_t last[PPT];
   bool done[PPT];
   bool all_done = true;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    T[k] = 1.f; C0[k] = C1[k] = C2[k] = D[k] = 0.f; last[k] = 0;
-    py[k] = (float)(yb + k) + 0.5f;
+    last[k] = 0;
     done[k] = !(x < ws.width && yb + k < ws.height);
     all_done &= done[k];
+  }
+#pragma unroll
+  for (int h = 0; h < NP; ++h) {
+    T[h] = f2(1.f);
+    C0[h] = C1[h] = C2[h] = D[h] = f2(0.f);
+    Y[h] = make_float2((float)(yb + 2 * h) + 0.5f, (float)(yb + 2 * h + 1) + 0.5f);
   }
   for (uint32_t b0 = 0; b0 < cnt; b0 += 256) {
     if (__syncthreads_count(all_done) == NT) break;
@@ -57,29 +64,31 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     for (uint32_t j = 0; j < nb && !all_done; ++j) {
       const float4 g0 = s_g0[j], g1 = s_g1[j];
       const ColTerms ct = col_terms(g0, g1, px);
+      const float4 c = s_c[j];
+      const float2 cr = f2(c.x), cg = f2(c.y), cb = f2(c.z), dep = f2(g1.z);
+      const uint32_t nxt = b0 + j + 1;
       all_done = true;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const float p2 = col_p2(ct, py[k]);
-        if (!done[k]) {
-          if (p2 >= lt) {
-            const float al = fminf(a_max, exp2f(p2));
-            const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, al));
-            if (Tn < t_min) {
-              done[k] = true;
-            } else {
-              const float w = __fmul_rn(al, T[k]);
-              const float4 c = s_c[j];
-              C0[k] = __fmaf_rn(c.x, w, C0[k]);
-              C1[k] = __fmaf_rn(c.y, w, C1[k]);
-              C2[k] = __fmaf_rn(c.z, w, C2[k]);
-              D[k] = __fmaf_rn(g1.z, w, D[k]);
-              T[k] = Tn;
-              last[k] = b0 + j + 1;
-            }
-          }
-        }
-        all_done &= done[k];
+      for (int h = 0; h < NP; ++h) {
+        // a pixel blends this Gaussian unless it is done, below alpha_min, or
+        // would drop under t_min (then it is done and this Gaussian is not blended)
+        const float2 p2 = col_p2x2(ct, Y[h]);
+        const bool a0 = !done[2 * h] & (p2.x >= lt), a1 = !done[2 * h + 1] & (p2.y >= lt);
+        const float2 al = make_float2(fminf(a_max, exp2f(p2.x)), fminf(a_max, exp2f(p2.y)));
+        const float2 Tc = mul2(T[h], fma2(al, f2(-1.f), f2(1.f)));
+        const bool s0 = a0 & (Tc.x < t_min), s1 = a1 & (Tc.y < t_min);
+        const bool k0 = a0 & !s0, k1 = a1 & !s1;
+        done[2 * h] |= s0;
+        done[2 * h + 1] |= s1;
+        const float2 w = mul2(make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f), T[h]);
+        C0[h] = fma2(cr, w, C0[h]);
+        C1[h] = fma2(cg, w, C1[h]);
+        C2[h] = fma2(cb, w, C2[h]);
+        D[h] = fma2(dep, w, D[h]);
+        T[h] = make_float2(k0 ? Tc.x : T[h].x, k1 ? Tc.y : T[h].y);
+        last[2 * h] = k0 ? nxt : last[2 * h];
+        last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
+        all_done &= done[2 * h] & done[2 * h + 1];
       }
     }
     // pixels whose list ended are done only when the whole list is walked
@@ -90,14 +99,17 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     const int y = yb + k;
     if (!(x < ws.width && y < ws.height)) continue;
     const int64_t p = (int64_t)y * ws.width + x;
+    const int h = k >> 1;
+    const bool hi = k & 1;
+    const float Tk = hi ? T[h].y : T[h].x;
     if (rgb) {
-      rgb[(3 * (int64_t)v + 0) * HW + p] = __fmaf_rn(T[k], cfg.bg[0], C0[k]);
-      rgb[(3 * (int64_t)v + 1) * HW + p] = __fmaf_rn(T[k], cfg.bg[1], C1[k]);
-      rgb[(3 * (int64_t)v + 2) * HW + p] = __fmaf_rn(T[k], cfg.bg[2], C2[k]);
+      rgb[(3 * (int64_t)v + 0) * HW + p] = __fmaf_rn(Tk, cfg.bg[0], hi ? C0[h].y : C0[h].x);
+      rgb[(3 * (int64_t)v + 1) * HW + p] = __fmaf_rn(Tk, cfg.bg[1], hi ? C1[h].y : C1[h].x);
+      rgb[(3 * (int64_t)v + 2) * HW + p] = __fmaf_rn(Tk, cfg.bg[2], hi ? C2[h].y : C2[h].x);
     }
-    if (depth) depth[v * HW + p] = D[k];
-    if (opac) opac[v * HW + p] = 1.f - T[k];
-    t_final[v * HW + p] = T[k];
+    if (depth) depth[v * HW + p] = hi ? D[h].y : D[h].x;
+    if (opac) opac[v * HW + p] = 1.f - Tk;
+    t_final[v * HW + p] = Tk;
     n_contrib[v * HW + p] = last[k];
   }
 }
