@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
-    p.add_argument("--serving-requests", type=int, default=400,
+    p.add_argument("--serving-requests", type=int, default=2000,
                    help="requests in the serving measurement (0 skips it); the full serving workload has 10,000")
     return p.parse_args()
 
@@ -296,11 +296,12 @@ def run_e2e(args, d, rast, gm, w, px_step):
             "d2h_bytes_per_step": ms_step.d2h_bytes}
 
 
-def serving_workload(n_requests: int, seed: int = 2507_04004 + 5):
+def serving_workload(n_requests: int, seed: int = 2507_04004 + 5, n_calib: int = 64):
     """3M-Gaussian map (SH 3, BF16), requests: 70 % renders at 640x360,
     1280x720 or 1920x1080 (focal 0.52 W) and 30 % tracking-Jacobian requests at
     640x512 with the 20k highest-gradient pixels, random poses inside the map,
-    Poisson arrivals at 200 requests/s."""
+    Poisson arrivals at 200 requests/s; plus ``n_calib`` further requests from
+    the same distribution for sizing the server's buffers (not measured)."""
     import numpy as np
 
     from paper_2507_04004_b300 import synth
@@ -315,7 +316,7 @@ def serving_workload(n_requests: int, seed: int = 2507_04004 + 5):
         pool.append((pix, img.reshape(3, -1)[:, pix].T.copy()))
     sizes = [(640, 360), (1280, 720), (1920, 1080)]
     reqs = []
-    for i, (centre, Rc) in enumerate(synth.tracking_poses(rng, n_requests, lo, hi)):
+    for i, (centre, Rc) in enumerate(synth.tracking_poses(rng, n_requests + n_calib, lo, hi)):
         R, t = synth.pose_from_centre(Rc, centre)
         if rng.random() < 0.3:
             pix, tgt = pool[i % len(pool)]
@@ -324,7 +325,7 @@ def serving_workload(n_requests: int, seed: int = 2507_04004 + 5):
             W, H = sizes[int(rng.integers(0, 3))]
             reqs.append(Request("render", synth.camera(R, t, 0.52 * W, 0.52 * W, W / 2, H / 2, W, H)))
     gaps = rng.exponential(1.0 / 200.0, n_requests)
-    return g, reqs, np.cumsum(gaps)
+    return g, reqs[:n_requests], np.cumsum(gaps), reqs[n_requests:]
 
 
 def run_serving(args, dev):
@@ -337,9 +338,18 @@ def run_serving(args, dev):
 
     from paper_2507_04004_b300.raster import GaussianMap
     from paper_2507_04004_b300.serve import PlainRenderer, Server, latency_stats
-    g, reqs, arrivals = serving_workload(args.serving_requests)
+    g, reqs, arrivals, calib = serving_workload(args.serving_requests)
     gm = GaussianMap.from_host(g, device=dev, sh_bf16=True)
-    fresh = lambda: [copy.copy(r) for r in reqs]
+    def drop(req, res):  # the consumer reads nothing back: results are released at once
+        pass
+
+    def fresh():
+        out = []
+        for r in reqs:
+            c = copy.copy(r)
+            c.on_result = drop
+            out.append(c)
+        return out
     out = {"workload": f"3M Gaussians SH3 BF16, {len(reqs)} requests, Poisson 200/s, 70% renders "
                        "(640x360/1280x720/1920x1080), 30% tracking Jacobians (640x512, 20k px)",
            "mem_budget_gib": 4}
@@ -354,6 +364,7 @@ def run_serving(args, dev):
 
     # batched server
     srv = Server(gm, mem_budget=4 << 30, max_views=4, n_streams=4, pairs_per_pixel=8.0, device=dev)
+    srv.calibrate(calib)
     srv.warmup({r.key for r in reqs})
     srv.start()
     rs = fresh()
@@ -375,6 +386,9 @@ def run_serving(args, dev):
     srv.stop()
     out["server_batches"] = srv.batches
     out["server_retries"] = srv.retries
+    out["server_runners_added"] = srv.runners_added
+    out["server_grows"] = srv.grows
+    out["server_pairs_per_view_max"] = {f"{k[0]} {k[1]}x{k[2]}": v for k, v in srv.pairs_per_view.items()}
     out["server_max_inflight_sort_gib"] = round(srv.max_inflight_bytes / 2 ** 30, 3)
     del srv
     torch.cuda.empty_cache()

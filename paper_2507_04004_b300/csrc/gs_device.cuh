@@ -19,7 +19,7 @@ constexpr int kTilePixels = kTile * kTile;
 constexpr unsigned kFull = 0xffffffffu;
 // pixels per thread in the blend kernels (a tile is 256 / PPT threads)
 constexpr int kFwdPPT = 4;
-constexpr int kBwdPPT = 4;
+constexpr int kBwdPPT = 8;
 constexpr int kBwdBatch = 128;  // Gaussians staged in shared memory per batch by the backward blend
 
 // Device view of the workspace parts (pointers resolved from gs_layout).

@@ -71,7 +71,7 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int la
 }
 
 template <bool FUSED, int PPT>
-__global__ void __launch_bounds__(256 / PPT, 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block

@@ -50,8 +50,12 @@ class Request:
     pix: np.ndarray | None = None  # jacobian: int32 linear pixel indices
     target: np.ndarray | None = None  # jacobian: [n_pix][3] target colours
     arrival: float = 0.0           # time.perf_counter() at submission (set by submit)
+    launched: float = 0.0          # when its batch was launched
     done: float = 0.0
     future: Future = field(default_factory=Future)
+    # streaming consumers: called with (request, result) on the scheduler
+    # thread instead of storing the result in the future (resolved with None)
+    on_result: object = None
 
     @property
     def key(self):
@@ -87,18 +91,14 @@ class _Runner:
             self.pix = torch.zeros(slots, npix, dtype=torch.int32, device=dev)
             self.J = torch.empty(slots, npix, 3, 6, **f)
             self.jrgb = torch.empty(slots, npix, 3, **f)
-            self.host_J = torch.empty(slots, npix, 3, 6, pin_memory=True)
-            self.host_jrgb = torch.empty(slots, npix, 3, pin_memory=True)
-        else:
-            self.host_rgb = torch.empty(slots, 3, H, W, pin_memory=True)
-            self.host_depth = torch.empty(slots, H, W, pin_memory=True)
         self.host_cams = torch.empty(slots, 16, pin_memory=True)
         self.host_pix = torch.empty(slots, npix, dtype=torch.int32, pin_memory=True) if self.jac else None
-        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.host_status = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        self.status = torch.zeros(2, dtype=torch.int32, device=dev)  # (status, pairs needed)
+        self.host_status = torch.zeros(2, dtype=torch.int32, pin_memory=True)
         self.graph = None
         self.event = torch.cuda.Event()
         self.busy = False
+        self.outputs = None
         self.bytes = SORT_BYTES_PER_PAIR * self.rast.capacity
 
     # -- the device work of one batch (captured once per runner)
@@ -110,21 +110,38 @@ class _Runner:
         if self.jac:
             N.gs_pose_jacobian(gm.struct(), self.cams, self.rast.cfg, self.rast.ws, self.pix, self.pix.shape[1],
                                self.J, self.jrgb, torch.cuda.current_stream(self.server.device).cuda_stream)
-        cnt = self.rast._view(self.rast.layout.counters, 1, torch.int32)
+        cnt = self.rast._view(self.rast.layout.counters, 2, torch.int32)
         self.status.copy_(cnt)
 
-    def capture(self):
+    def grow(self, pairs: int):
+        """Re-allocate the workspace for ``pairs`` pairs and drop the graph."""
+        self.rast.capacity = int(pairs)
+        self.rast._alloc()
+        self.bytes = SORT_BYTES_PER_PAIR * self.rast.capacity
+        self.graph = None
+
+    def capture(self, warm: bool = True):
         s = torch.cuda.Stream(device=self.server.device)
-        with torch.cuda.stream(s):
-            self._work()  # warm-up outside the capture (sets kernel attributes)
-        s.synchronize()
+        if warm:
+            with torch.cuda.stream(s):
+                self._work()  # first run outside the capture (sets kernel attributes)
+            s.synchronize()
+        # capture_begin/end directly: the torch.cuda.graph context manager
+        # synchronises the device and empties the allocator cache on entry,
+        # which would stall every batch in flight
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
-            self._work()
+        with torch.cuda.stream(s):
+            g.capture_begin(capture_error_mode="thread_local")
+            try:
+                self._work()
+            finally:
+                g.capture_end()
         self.graph = g
 
     def launch(self, reqs, stream):
-        """Copy inputs, run, copy results to pinned host buffers (async)."""
+        """Copy inputs, run, copy each request's results into its own pinned
+        host tensors (async; the tensors come from torch's pinned-memory cache
+        and are handed to the caller without a further copy)."""
         n = len(reqs)
         for i, r in enumerate(reqs):
             self.host_cams[i] = torch.as_tensor(cameras_tensor([r.camera], device="cpu")[0])
@@ -142,25 +159,33 @@ class _Runner:
                 self.graph.replay()
             else:
                 self._work()
-            if self.jac:
-                self.host_J[:n].copy_(self.J[:n], non_blocking=True)
-                self.host_jrgb[:n].copy_(self.jrgb[:n], non_blocking=True)
-            else:
-                self.host_rgb[:n].copy_(self.out.rgb[:n], non_blocking=True)
-                self.host_depth[:n].copy_(self.out.depth[:n], non_blocking=True)
+            self.outputs = []
+            for i in range(n):
+                if self.jac:
+                    J = torch.empty(self.J.shape[1:], pin_memory=True)
+                    rgb = torch.empty(self.jrgb.shape[1:], pin_memory=True)
+                    J.copy_(self.J[i], non_blocking=True)
+                    rgb.copy_(self.jrgb[i], non_blocking=True)
+                    self.outputs.append((J, rgb))
+                else:
+                    rgb = torch.empty(self.out.rgb.shape[1:], pin_memory=True)
+                    dep = torch.empty(self.out.depth.shape[1:], pin_memory=True)
+                    rgb.copy_(self.out.rgb[i], non_blocking=True)
+                    dep.copy_(self.out.depth[i], non_blocking=True)
+                    self.outputs.append((rgb, dep))
             self.host_status.copy_(self.status, non_blocking=True)
             self.event.record(stream)
 
     def results(self, reqs):
         out = []
-        for i, r in enumerate(reqs):
+        for r, (a, b) in zip(reqs, self.outputs):
             if self.jac:
-                J = self.host_J[i].numpy().copy()
-                rgb = self.host_jrgb[i].numpy().copy()
+                J, rgb = a.numpy(), b.numpy()
                 res = rgb - (r.target if r.target is not None else 0.0)
                 out.append(dict(J=J, rgb=rgb, residual=res))
             else:
-                out.append(dict(rgb=self.host_rgb[i].numpy().copy(), depth=self.host_depth[i].numpy().copy()))
+                out.append(dict(rgb=a.numpy(), depth=b.numpy()))
+        self.outputs = None
         return out
 
 
@@ -187,11 +212,42 @@ class Server:
         self._stream_rr = 0
         self.batches = 0
         self.retries = 0
+        self.pairs_per_view: dict = {}  # key -> largest pair count one view needed so far
+        self.pairs_sum: dict = collections.defaultdict(float)  # key -> (sum of per-view pair counts, views)
+        self.pairs_views: dict = collections.defaultdict(int)
+        self.runners_added = 0  # runners created while serving (all others came from warmup)
+        self.grows = 0          # workspaces re-allocated for a larger pair demand
 
     # ---------------------------------------------------------------- setup
-    def _capacity(self, key, slots):
+    def _capacity(self, key, slots, headroom: float = 1.25):
+        """Pair capacity of a runner: ``headroom`` x the largest per-view demand
+        seen, and for several slots at least 1.5 x slots x the mean demand
+        (several views rarely all need the maximum; an overflow re-runs)."""
         _, W, H, _ = key
-        return max(1 << 16, int(self.pairs_per_pixel * W * H * slots))
+        if key not in self.pairs_per_view:
+            return max(1 << 16, int(self.pairs_per_pixel * W * H * slots))
+        mean = self.pairs_sum[key] / max(1, self.pairs_views[key])
+        cap = max(headroom * self.pairs_per_view[key], 1.5 * slots * mean)
+        return max(1 << 16, int(cap))
+
+    def _observe(self, key, per_view_pairs: int, views: int = 1):
+        self.pairs_per_view[key] = max(self.pairs_per_view.get(key, 0), int(per_view_pairs))
+        self.pairs_sum[key] += float(per_view_pairs) * views
+        self.pairs_views[key] += views
+
+    def calibrate(self, requests):
+        """Measure the pair demand of sample requests (one eager, checked
+        render each) so that runners are sized before serving starts."""
+        rasts = {}
+        for r in requests:
+            kind, W, H, _ = r.key
+            rast = rasts.get((W, H))
+            if rast is None:
+                rast = rasts[(W, H)] = Rasterizer(self.gmap.n, 1, W, H, pair_capacity=1 << 22, device=self.device)
+            rast.project_and_sort(self.gmap, cameras_tensor([r.camera], device=self.device), check=True)
+            self._observe(r.key, rast.status()[1])
+        del rasts
+        torch.cuda.synchronize(self.device)
 
     def _runner(self, key, slots):
         """A free runner for (key, slots), creating (and capturing) one if none is free."""
@@ -202,13 +258,23 @@ class Server:
         if self.use_graphs:
             r.capture()
         self.runners[(key, slots)].append(r)
+        if self._thread is not None:
+            self.runners_added += 1
         return r
 
-    def warmup(self, keys):
-        """Create and capture one runner per (key, slot count) before serving."""
+    def warmup(self, keys, copies: int = 2):
+        """Create and capture runners per (key, slot count) before serving
+        (``copies`` of each, one more for single-request batches, which
+        overlap most), so that overlapping batches rarely need a new one."""
         for key in keys:
             for s in _slot_counts(self.max_views):
-                self._runner(key, s)
+                made = []
+                for _ in range(copies + (s == 1)):
+                    r = self._runner(key, s)
+                    r.busy = True  # so that the next call makes another
+                    made.append(r)
+                for r in made:
+                    r.busy = False
         torch.cuda.synchronize(self.device)
 
     # ---------------------------------------------------------------- API
@@ -252,7 +318,7 @@ class Server:
                 except queue.Empty:
                     pass
             elif not launched:
-                time.sleep(0)
+                time.sleep(5e-5)  # batches in flight: poll their events without holding a core
 
     def _drain_inbox(self):
         while True:
@@ -281,13 +347,26 @@ class Server:
                     if self.inflight_bytes + need > self.mem_budget and self.inflight:
                         return launched  # admission: wait for sort-buffer memory to free up
                     runner = self._runner(key, slots)
+                if runner.rast.capacity < self._capacity(key, slots):
+                    # the pair demand seen for this key outgrew the runner: grow it
+                    # before use, with room for further growth of the estimate
+                    runner.grow(self._capacity(key, slots, headroom=1.6))
+                    self.grows += 1
+                    if self.use_graphs:
+                        runner.capture(warm=False)
                 if self.inflight_bytes + runner.bytes > self.mem_budget and self.inflight:
                     return launched
                 reqs = [q.popleft() for _ in range(n)]
+                t_launch = time.perf_counter()
+                for r in reqs:
+                    r.launched = t_launch
                 runner.busy = True
                 stream = self.streams[self._stream_rr % len(self.streams)]
                 self._stream_rr += 1
+                if self.use_graphs and runner.graph is None:
+                    runner.capture(warm=False)
                 runner.launch(reqs, stream)
+                runner.bytes_launched = runner.bytes
                 self.inflight.append((runner, reqs))
                 self.inflight_bytes += runner.bytes
                 self.max_inflight_bytes = max(self.max_inflight_bytes, self.inflight_bytes)
@@ -301,24 +380,28 @@ class Server:
             if not runner.event.query():
                 still.append((runner, reqs))
                 continue
+            key = reqs[0].key
+            needed = int(runner.host_status[1])
+            self._observe(key, -(-needed // runner.slots), len(reqs))
             if int(runner.host_status[0]) != 0:
-                # pair buffer overflow inside the graph: grow, re-run eagerly, re-capture
+                # pair buffer overflow: grow the runner (re-captured before its
+                # next launch) and put the requests back at the head of their queue
                 self.retries += 1
-                self.inflight_bytes -= runner.bytes
-                runner.rast.project_and_sort(self.gmap, runner.cams, check=True)
-                runner.bytes = SORT_BYTES_PER_PAIR * runner.rast.capacity
-                self.inflight_bytes += runner.bytes
-                runner.graph = None
-                if self.use_graphs:
-                    runner.capture()
-                runner.launch(reqs, self.streams[0])
-                runner.event.synchronize()
+                runner.grow(int(1.25 * needed) + 1024)
+                runner.outputs = None
+                runner.busy = False
+                self.inflight_bytes -= runner.bytes_launched
+                self.waiting[key].extendleft(reversed(reqs))
+                continue
             t = time.perf_counter()
             for r, res in zip(reqs, runner.results(reqs)):
                 r.done = t
+                if r.on_result is not None:
+                    r.on_result(r, res)
+                    res = None
                 r.future.set_result(res)
             runner.busy = False
-            self.inflight_bytes -= runner.bytes
+            self.inflight_bytes -= runner.bytes_launched
         self.inflight = still
 
 
@@ -348,6 +431,12 @@ class PlainRenderer:
 
 
 def latency_stats(reqs):
+    """p50/p99/mean of arrival -> result latency; for server requests also the
+    queueing part (arrival -> batch launch)."""
     lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
-    return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                mean_ms=float(lat.mean()), n=len(lat))
+    out = dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+               mean_ms=float(lat.mean()), n=len(lat))
+    if all(r.launched for r in reqs):
+        wait = np.array([r.launched - r.arrival for r in reqs]) * 1e3
+        out.update(queue_p50_ms=float(np.percentile(wait, 50)), queue_p99_ms=float(np.percentile(wait, 99)))
+    return out

@@ -40,6 +40,7 @@ def test_results_alone_equal_results_in_the_mix(use_graphs):
     reqs = _requests(rng, 24, lo, hi)
     budget = 64 << 20
     srv = Server(gm, mem_budget=budget, max_views=4, n_streams=3, use_graphs=use_graphs, pairs_per_pixel=6.0)
+    srv.calibrate(reqs[:3])
     srv.warmup({r.key for r in reqs})
     srv.start()
     futs = [srv.submit(r) for r in reqs]  # all at once: batches form and overlap
