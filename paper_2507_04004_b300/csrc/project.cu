@@ -310,9 +310,16 @@ __global__ void __launch_bounds__(256) k_rows_emit(Ws ws) {
       }
     }
     __syncthreads();
+    // reserve this CTA's range in each tile bin; s_cnt then counts down as the
+    // CTA fills it, so an index below zero (never expected: both loops take
+    // the same decisions) is caught without a global load per pair
     for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
-      s_base[i] = s_cnt[i] ? atomicAdd(ws.tile_cursor + win0 + i, s_cnt[i]) : 0u;
-      s_cnt[i] = 0;
+      if (s_cnt[i] == 0) continue;
+      s_base[i] = atomicAdd(ws.tile_cursor + win0 + i, s_cnt[i]);
+      if (s_base[i] + s_cnt[i] > ws.tile_start[win0 + i] + ws.tile_count[win0 + i]) {
+        atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+        s_cnt[i] = 0;
+      }
     }
     __syncthreads();
   }
@@ -331,9 +338,15 @@ __global__ void __launch_bounds__(256) k_rows_emit(Ws ws) {
     for (int tx = sp.lo; tx <= sp.hi; ++tx) {
       if (sp.gap && !tile_kept(el, tx, ty, ws.width, ws.height)) continue;
       const int64_t t = row0 + tx;
-      const uint32_t pos = smem ? s_base[t - win0] + atomicAdd(s_cnt + (t - win0), 1u) : atomicAdd(ws.tile_cursor + t, 1u);
-      if (pos < ws.tile_start[t] + ws.tile_count[t]) ws.keys[pos] = key;
-      else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+      if (smem) {
+        const int local = (int)atomicSub(s_cnt + (t - win0), 1u) - 1;
+        if (local >= 0) ws.keys[s_base[t - win0] + local] = key;
+        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+      } else {
+        const uint32_t pos = atomicAdd(ws.tile_cursor + t, 1u);
+        if (pos < ws.tile_start[t] + ws.tile_count[t]) ws.keys[pos] = key;
+        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+      }
     }
   }
 }

@@ -13,6 +13,8 @@
 //   - the chain through the projection (Sec. "3D Gaussian Splatting
 //     Representation") to mean, log-scale, quaternion, opacity logit and SH,
 //     and the per-view pose derivative under T Exp(xi) (Eq. 3dgs_jacobi).
+#include <type_traits>
+
 #include "gs_internal.h"
 
 namespace gsb {
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
   }
   const float a_max = cfg.alpha_max;
   const float lt = __log2f(cfg.alpha_min);
+  const float clamp_from = __log2f(cfg.alpha_max) - 1e-4f;
   for (int64_t end = max_last; end > 0; end -= NB) {
     const int64_t beg = end > NB ? end - NB : 0;
     const int nb = (int)(end - beg);
@@ -227,13 +230,20 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
       const float2 cr = f2(c.x), cg = f2(c.y), cb = f2(c.z), dep = f2(g1.z);
       float2 v6 = f2(0.f), v7 = f2(0.f), v8 = f2(0.f), v9 = f2(0.f);
       float2 M0 = f2(0.f), M1 = f2(0.f), M2 = f2(0.f);
+      auto walk = [&](auto clamp) {
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
         const bool a0 = act[2 * h], a1 = act[2 * h + 1];
         const float e0 = exp2f(p2[h].x), e1 = exp2f(p2[h].y);
-        const float2 al = make_float2(a0 ? fminf(a_max, e0) : 0.f, a1 ? fminf(a_max, e1) : 0.f);
-        // alpha = o exp(power): dL/dpower = dL/dalpha alpha, zero where alpha is clamped
-        const float2 ag = make_float2(e0 > a_max ? 0.f : al.x, e1 > a_max ? 0.f : al.y);
+        float2 al, ag;
+        if (decltype(clamp)::value) {
+          al = make_float2(a0 ? fminf(a_max, e0) : 0.f, a1 ? fminf(a_max, e1) : 0.f);
+          // alpha = o exp(power): dL/dpower = dL/dalpha alpha, zero where alpha is clamped
+          ag = make_float2(e0 > a_max ? 0.f : al.x, e1 > a_max ? 0.f : al.y);
+        } else {
+          al = make_float2(a0 ? e0 : 0.f, a1 ? e1 : 0.f);
+          ag = al;
+        }
         const float2 om = fma2(al, f2(-1.f), f2(1.f));  // 1 - alpha >= 0.01
         // transmittance in front of this Gaussian
         T2[h] = mul2(T2[h], make_float2(a0 ? __fdividef(1.f, om.x) : 1.f, a1 ? __fdividef(1.f, om.y) : 1.f));
@@ -251,6 +261,12 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
         M1 = fma2(dp, make_float2((float)(2 * h), (float)(2 * h + 1)), M1);
         M2 = fma2(dp, make_float2((float)(4 * h * h), (float)((2 * h + 1) * (2 * h + 1))), M2);
       }
+      };
+      // the clamp of alpha can act only where the opacity nearly reaches
+      // alpha_max (per Gaussian, warp-uniform, with a margin for the rounding
+      // of p2): other Gaussians take the path without it
+      if (g1.y > clamp_from) walk(std::true_type{});
+      else walk(std::false_type{});
       float val[10];
       const float m0 = M0.x + M0.y, m1 = M1.x + M1.y, m2 = M2.x + M2.y;
       const float dy0 = Y[0].x - g0.y;

@@ -193,13 +193,14 @@ class Server:
     """Continuous batching over one device-resident map (see module docs)."""
 
     def __init__(self, gmap: GaussianMap, mem_budget: int = 4 << 30, max_views: int = 8, n_streams: int = 4,
-                 use_graphs: bool = True, pairs_per_pixel: float = 4.0, device="cuda"):
+                 use_graphs: bool = True, pairs_per_pixel: float = 4.0, device="cuda", max_bypass: float = 0.02):
         self.gmap, self.mem_budget, self.max_views = gmap, int(mem_budget), int(max_views)
         self.use_graphs = use_graphs
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.pairs_per_pixel = float(pairs_per_pixel)
+        self.max_bypass = float(max_bypass)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
         self.runners: dict = collections.defaultdict(list)
         self.waiting: dict = collections.defaultdict(collections.deque)
@@ -221,13 +222,14 @@ class Server:
     # ---------------------------------------------------------------- setup
     def _capacity(self, key, slots, headroom: float = 1.25):
         """Pair capacity of a runner: ``headroom`` x the largest per-view demand
-        seen, and for several slots at least 1.5 x slots x the mean demand
-        (several views rarely all need the maximum; an overflow re-runs)."""
+        seen, and for several slots at least ``headroom`` x 1.25 x slots x the
+        mean demand (several views rarely all need the maximum; an overflow
+        re-runs)."""
         _, W, H, _ = key
         if key not in self.pairs_per_view:
             return max(1 << 16, int(self.pairs_per_pixel * W * H * slots))
         mean = self.pairs_sum[key] / max(1, self.pairs_views[key])
-        cap = max(headroom * self.pairs_per_view[key], 1.5 * slots * mean)
+        cap = headroom * max(self.pairs_per_view[key], 1.25 * slots * mean)
         return max(1 << 16, int(cap))
 
     def _observe(self, key, per_view_pairs: int, views: int = 1):
@@ -254,22 +256,23 @@ class Server:
         for r in self.runners[(key, slots)]:
             if not r.busy:
                 return r
-        r = _Runner(self, key, slots, self._capacity(key, slots))
+        r = _Runner(self, key, slots, self._capacity(key, slots, headroom=1.6))
         if self.use_graphs:
-            r.capture()
+            # a first eager run only matters before any kernel has been launched
+            r.capture(warm=self._thread is None)
         self.runners[(key, slots)].append(r)
         if self._thread is not None:
             self.runners_added += 1
         return r
 
-    def warmup(self, keys, copies: int = 2):
+    def warmup(self, keys, copies: int = 3):
         """Create and capture runners per (key, slot count) before serving
-        (``copies`` of each, one more for single-request batches, which
+        (``copies`` of each, two more for single-request batches, which
         overlap most), so that overlapping batches rarely need a new one."""
         for key in keys:
             for s in _slot_counts(self.max_views):
                 made = []
-                for _ in range(copies + (s == 1)):
+                for _ in range(copies + 2 * (s == 1)):
                     r = self._runner(key, s)
                     r.busy = True  # so that the next call makes another
                     made.append(r)
@@ -328,34 +331,54 @@ class Server:
                 return
             self.waiting[req.key].append(req)
 
+    def _free_runner(self, key, slots):
+        for r in self.runners[(key, slots)]:
+            if not r.busy:
+                return r
+        return None
+
+    def _admit(self, key, n):
+        """(runner, requests to take) for up to ``n`` waiting requests of
+        ``key``: the smallest slot count that holds all of them if its sort
+        buffers fit in the free budget, else the largest smaller one that fits;
+        anything runs when nothing else is in flight."""
+        free = self.mem_budget - self.inflight_bytes
+        counts = _slot_counts(self.max_views)
+        order = [s for s in counts if s >= n][:1] + [s for s in reversed(counts) if s < n]
+        for slots in order:
+            runner = self._free_runner(key, slots)
+            target = self._capacity(key, slots, headroom=1.6)
+            need = SORT_BYTES_PER_PAIR * (target if runner is None or
+                                          runner.rast.capacity < self._capacity(key, slots, headroom=1.0)
+                                          else runner.rast.capacity)
+            if need > free and self.inflight:
+                continue
+            if runner is None:
+                runner = self._runner(key, slots)
+            elif runner.rast.capacity < self._capacity(key, slots, headroom=1.0):
+                # the pair demand seen for this key outgrew the runner: grow it
+                # before use, with room for further growth of the estimate
+                runner.grow(target)
+                self.grows += 1
+            return runner, min(n, slots)
+        return None
+
     def _schedule(self) -> bool:
         launched = False
-        # oldest waiting request first
+        now = time.perf_counter()
+        # oldest waiting request first; a key whose batch does not fit the free
+        # budget lets later keys use it until its oldest request has waited
+        # max_bypass seconds, then everything waits for it
         keys = sorted((k for k, q in self.waiting.items() if q), key=lambda k: self.waiting[k][0].arrival)
         for key in keys:
             q = self.waiting[key]
             while q:
-                n = min(len(q), self.max_views)
-                slots = next(s for s in _slot_counts(self.max_views) if s >= n)
-                runner = None
-                for r in self.runners[(key, slots)]:
-                    if not r.busy:
-                        runner = r
-                        break
-                if runner is None:
-                    need = SORT_BYTES_PER_PAIR * self._capacity(key, slots)
-                    if self.inflight_bytes + need > self.mem_budget and self.inflight:
-                        return launched  # admission: wait for sort-buffer memory to free up
-                    runner = self._runner(key, slots)
-                if runner.rast.capacity < self._capacity(key, slots):
-                    # the pair demand seen for this key outgrew the runner: grow it
-                    # before use, with room for further growth of the estimate
-                    runner.grow(self._capacity(key, slots, headroom=1.6))
-                    self.grows += 1
-                    if self.use_graphs:
-                        runner.capture(warm=False)
-                if self.inflight_bytes + runner.bytes > self.mem_budget and self.inflight:
-                    return launched
+                pick = self._admit(key, min(len(q), self.max_views))
+                if pick is None:
+                    if now - q[0].arrival > self.max_bypass:
+                        return launched
+                    break
+                runner, n = pick
                 reqs = [q.popleft() for _ in range(n)]
                 t_launch = time.perf_counter()
                 for r in reqs:

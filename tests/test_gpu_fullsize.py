@@ -100,6 +100,53 @@ def test_mapping_benchmark_workload_sampled(oracle):
     assert np.abs(g["pose"][1]).max() == 0 and np.abs(g["pose"][2]).max() == 0
 
 
+RECTS_720 = [(0, 0, 40, 32), (616, 340, 48, 40), (1250, 692, 30, 28)]  # corner, centre, ragged edge
+
+
+def test_mapping_500k_4x720p_sampled(oracle):
+    """The 500k-Gaussian mapping step (SH 3, 4 keyframes of 1280x720, fx = 700,
+    LiDAR depth, 0.8 L1 colour + 0.2 L1 depth): images and gradients against
+    the oracle on sampled rectangles, and the fused loss backward against the
+    external-adjoint backward fed with the loss's own pixel adjoints."""
+    w = synth.mapping()
+    m = host_map(w.gmap)
+    rast, gm, ct, out = _render(w)
+    assert rast.status()[0] == 0
+    for v in (0, 3):
+        for rect in RECTS_720:
+            e_rgb, e_o, e_d, dscale, okf = _image_errors(oracle, m, w.cams[v], out, v, rect)
+            assert okf > 0.9
+            assert e_rgb.max() <= IMG_TOL and e_o.max() <= IMG_TOL and e_d.max() <= IMG_TOL * dscale, (v, rect)
+    H, W = 720, 1280
+    er, ed, eo = _rect_adjoints(4, H, W, (0, 3), RECTS_720, 29)
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    g = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
+    o = _oracle_rect_grads(oracle, m, w.cams, (0, 3), RECTS_720, er, ed, eo)
+    assert_grads_close(g, o, GRAD_KEYS)
+    for v in (0, 3):
+        assert rel_err(g["pose"][v], o["pose"][v]) <= GRAD_TOL, v
+
+    # fused loss == external adjoints of the same loss (a property at any size)
+    tr, td = t(w.tgt_rgb), t(w.tgt_depth)
+    gf = rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth)
+    r = out.rgb - tr
+    dC = w.w_rgb * torch.sign(r) / (3.0 * H * W)
+    nd = (td > 0).flatten(1).sum(1).to(torch.float32).view(4, 1, 1)
+    valid = (td > 0) & (out.opac > 0)
+    O = torch.where(valid, out.opac, torch.ones_like(out.opac))
+    sg = torch.where(valid, torch.sign(out.depth / O - td), torch.zeros_like(td))
+    dD = w.w_depth * sg / (O * nd)
+    dO = -w.w_depth * sg * out.depth / (O * O * nd)
+    ge = rast.backward(gm, ct, out, dl_drgb=dC.contiguous(), dl_ddepth=dD.contiguous(), dl_dopac=dO.contiguous())
+    gf, ge = grads_to_numpy(gf), grads_to_numpy(ge)
+    for k in GRAD_KEYS + ("pose",):
+        assert rel_err(gf[k], ge[k]) <= GRAD_TOL, k
+    loss = (w.w_rgb * r.abs().flatten(1).mean(1)
+            + w.w_depth * (torch.where(valid, (out.depth / O - td).abs(), torch.zeros_like(td)).flatten(1).sum(1)
+                           / nd.view(4)))
+    np.testing.assert_allclose(gf["loss"], loss.cpu().numpy(), rtol=1e-4)
+
+
 @pytest.mark.parametrize("sh_bf16", [True, False])
 def test_precision_2m_gaussians_8_views_sampled(oracle, sh_bf16, capsys):
     yaw = math.radians(20.0)

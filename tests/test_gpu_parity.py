@@ -131,6 +131,22 @@ def test_long_tiles_and_merge_path(oracle):
     _check_images(o_r, out, 0, "long tiles")
 
 
+@pytest.mark.parametrize("n,lo,hi", [(900, 65, 768), (2600, 769, 2048)])
+def test_bin_size_classes(oracle, n, lo, hi):
+    """Bins sorted by one warp (65..768 keys) and by one CTA (769..2,048
+    keys): tile lists bit-exact against the oracle."""
+    rng = np.random.default_rng(6)
+    g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
+    cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 40.0, 24.0, 20.0, 48, 40)
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, [cam])
+    _, count, _ = rast.tile_lists()
+    c = count.cpu().numpy()
+    assert ((c >= lo) & (c <= hi)).any(), c
+    compare_tiles(oracle, m, cam, rast, 0)
+    _check_images(oracle.render(m, cam), out, 0, f"bins of {lo}..{hi} keys")
+
+
 def test_capacity_overflow_reports_and_retries(oracle):
     w = synth.tiny()
     m = host_map(w.gmap)
@@ -197,6 +213,38 @@ def test_tiny_fused_loss_gradients(oracle):
     assert g["loss"][0] == pytest.approx(o["loss"][0], rel=1e-4)
     assert_grads_close(g, o, GRAD_KEYS)
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
+
+
+def test_alpha_clamp_path(oracle):
+    """A fifth of the Gaussians with opacity 0.9975, so that alpha is clamped
+    at alpha_max near their centres (the blend kernels take a separate path
+    for Gaussians whose opacity comes near the clamp): images, last
+    contributors, fused-loss gradients and Jacobian rows against the oracle."""
+    w = synth.tiny()
+    rng = np.random.default_rng(11)
+    lo = w.gmap.logit_opacity.copy()
+    hot = rng.random(lo.shape[0]) < 0.2
+    lo[hot] = logit(0.9975)
+    w.gmap.logit_opacity[:] = lo.astype(np.float32)
+    m = host_map(w.gmap)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    o_r = oracle.render(m, w.cams[0])
+    _check_images(o_r, out, 0, "clamped alpha")
+    _check_last_contributor(rast, out, o_r, 0)
+    tgt_d = _tiny_depth_target(oracle, w, m)
+    tr = torch.as_tensor(w.tgt_rgb, device="cuda")
+    td = torch.as_tensor(tgt_d, device="cuda")
+    g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth))
+    o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=tgt_d, w_rgb=w.w_rgb, w_depth=w.w_depth)
+    assert_grads_close(g, o, GRAD_KEYS)
+    assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
+    pix = np.sort(rng.choice(96 * 128, 400, replace=False)).astype(np.int32)[None]
+    J, rgb = rast.pose_jacobian(gm, ct, torch.as_tensor(pix, device="cuda"))
+    Jo, rgbo = oracle.pose_jacobian(m, w.cams[0], pix[0])
+    ok = o_r["flags"].reshape(-1)[pix[0]] == 0
+    np.testing.assert_allclose(rgb.cpu().numpy()[0][ok], rgbo[ok], atol=IMG_TOL)
+    Jg = J.cpu().numpy()[0]
+    assert np.abs(Jg[ok] - Jo[ok]).max() <= GRAD_TOL * np.abs(Jo[ok]).max()
 
 
 @pytest.mark.parametrize("sh_bf16", [False, True])
@@ -283,11 +331,11 @@ def test_pose_jacobian_rows_match_oracle(oracle):
         assert err <= GRAD_TOL, f"view {v}: J relative error {err:.3e}"
 
 
-@pytest.mark.parametrize("n", [40, 600])
+@pytest.mark.parametrize("n", [40, 600, 1200])
 def test_equal_depth_keys_sort_by_index(oracle, n):
     """Many Gaussians at exactly the same depth (identity pose, equal z): the
-    per-tile order must fall back to the Gaussian index, both for short bins
-    (warp sort) and for radix-sorted bins."""
+    per-tile order must fall back to the Gaussian index for short bins (warp
+    bitonic), warp radix-sorted bins and CTA radix-sorted bins."""
     rng = np.random.default_rng(n)
     means = np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), np.full(n, 5.0)], 1)
     m = one_gaussian_map(means, np.full(n, math.log(0.08)), rng.normal(0, 1, n), rng.random((n, 3)))
