@@ -5,14 +5,12 @@
 // is read once per kPPT pixels.  The tile's depth-sorted Gaussians are staged
 // 256 at a time and the CTA stops as soon as every pixel's transmittance is
 // exhausted.
-#include <type_traits>
-
 #include "gs_internal.h"
 
 namespace gsb {
 
 template <int PPT>
-__global__ void __launch_bounds__(256 / PPT, 4096 / (256 / PPT) / 4) k_render_fwd(gs_config cfg, Ws ws, float* __restrict__ rgb,
+__global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, float* __restrict__ rgb,
                                                           float* __restrict__ depth, float* __restrict__ opac,
                                                           float* __restrict__ t_final,
                                                           uint32_t* __restrict__ n_contrib) {
@@ -32,7 +30,6 @@ __global__ void __launch_bounds__(256 / PPT, 4096 / (256 / PPT) / 4) k_render_fw
   const float4* rec = ws.records + 3 * (int64_t)v * ws.n;
   const float a_max = cfg.alpha_max, t_min = cfg.t_min;
   const float lt = __log2f(cfg.alpha_min);
-  const float clamp_from = __log2f(cfg.alpha_max) - 1e-4f;
 
   // pixels run in vertical pairs (k = 2h, 2h + 1) through packed FP32 pairs
   constexpr int NP = PPT / 2;
@@ -71,38 +68,28 @@ __global__ void __launch_bounds__(256 / PPT, 4096 / (256 / PPT) / 4) k_render_fw
       const float2 cr = f2(c.x), cg = f2(c.y), cb = f2(c.z), dep = f2(g1.z);
       const uint32_t nxt = b0 + j + 1;
       all_done = true;
-      auto blend = [&](auto clamp) {
 #pragma unroll
-        for (int h = 0; h < NP; ++h) {
-          // a pixel blends this Gaussian unless it is done, below alpha_min, or
-          // would drop under t_min (then it is done and this Gaussian is not blended)
-          const float2 p2 = col_p2x2(ct, Y[h]);
-          const bool a0 = !done[2 * h] & (p2.x >= lt), a1 = !done[2 * h + 1] & (p2.y >= lt);
-          float2 al = make_float2(exp2f(p2.x), exp2f(p2.y));
-          if (decltype(clamp)::value) al = make_float2(fminf(a_max, al.x), fminf(a_max, al.y));
-          const float2 Tc = mul2(T[h], fma2(al, f2(-1.f), f2(1.f)));
-          const bool s0 = a0 & (Tc.x < t_min), s1 = a1 & (Tc.y < t_min);
-          const bool k0 = a0 & !s0, k1 = a1 & !s1;
-          done[2 * h] |= s0;
-          done[2 * h + 1] |= s1;
-          // alpha of a blended pixel, 0 otherwise (then T and the sums stay as they are)
-          const float2 ak = make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f);
-          const float2 w = mul2(ak, T[h]);
-          C0[h] = fma2(cr, w, C0[h]);
-          C1[h] = fma2(cg, w, C1[h]);
-          C2[h] = fma2(cb, w, C2[h]);
-          D[h] = fma2(dep, w, D[h]);
-          T[h] = mul2(T[h], fma2(ak, f2(-1.f), f2(1.f)));
-          last[2 * h] = k0 ? nxt : last[2 * h];
-          last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
-          all_done &= done[2 * h] & done[2 * h + 1];
-        }
-      };
-      // alpha reaches alpha_max only where the opacity nearly does (a
-      // per-Gaussian, warp-uniform test with a margin for the rounding of
-      // p2); every other Gaussian takes the path without the clamp
-      if (g1.y > clamp_from) blend(std::true_type{});
-      else blend(std::false_type{});
+      for (int h = 0; h < NP; ++h) {
+        // a pixel blends this Gaussian unless it is done, below alpha_min, or
+        // would drop under t_min (then it is done and this Gaussian is not blended)
+        const float2 p2 = col_p2x2(ct, Y[h]);
+        const bool a0 = !done[2 * h] & (p2.x >= lt), a1 = !done[2 * h + 1] & (p2.y >= lt);
+        const float2 al = make_float2(fminf(a_max, exp2f(p2.x)), fminf(a_max, exp2f(p2.y)));
+        const float2 Tc = mul2(T[h], fma2(al, f2(-1.f), f2(1.f)));
+        const bool s0 = a0 & (Tc.x < t_min), s1 = a1 & (Tc.y < t_min);
+        const bool k0 = a0 & !s0, k1 = a1 & !s1;
+        done[2 * h] |= s0;
+        done[2 * h + 1] |= s1;
+        const float2 w = mul2(make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f), T[h]);
+        C0[h] = fma2(cr, w, C0[h]);
+        C1[h] = fma2(cg, w, C1[h]);
+        C2[h] = fma2(cb, w, C2[h]);
+        D[h] = fma2(dep, w, D[h]);
+        T[h] = make_float2(k0 ? Tc.x : T[h].x, k1 ? Tc.y : T[h].y);
+        last[2 * h] = k0 ? nxt : last[2 * h];
+        last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
+        all_done &= done[2 * h] & done[2 * h + 1];
+      }
     }
     // pixels whose list ended are done only when the whole list is walked
   }
