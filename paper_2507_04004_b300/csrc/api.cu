@@ -29,6 +29,7 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   L->rects = take((size_t)E * sizeof(uint2));
   L->adjoints = take((size_t)E * 3 * sizeof(float4));
   L->visible = take((size_t)E * sizeof(uint32_t));
+  L->gauss_list = take((size_t)n * sizeof(uint32_t));
   L->tile_count = take((size_t)(V * T) * sizeof(uint32_t));
   L->tile_start = take((size_t)(V * T) * sizeof(uint32_t));
   L->tile_cursor = take((size_t)(V * T) * sizeof(uint32_t));
@@ -55,6 +56,7 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.rects = reinterpret_cast<uint2*>(b + L.rects);
   ws.adjoints = reinterpret_cast<float4*>(b + L.adjoints);
   ws.visible = reinterpret_cast<uint32_t*>(b + L.visible);
+  ws.gauss_list = reinterpret_cast<uint32_t*>(b + L.gauss_list);
   ws.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
   ws.tile_start = reinterpret_cast<uint32_t*>(b + L.tile_start);
   ws.tile_cursor = reinterpret_cast<uint32_t*>(b + L.tile_cursor);

@@ -29,6 +29,7 @@ struct Ws {
   uint2* rects;           // [V*N]
   float4* adjoints;       // [V*N][3]
   uint32_t* visible;      // [V*N]
+  uint32_t* gauss_list;   // [N] Gaussians visible in at least one view
   uint32_t* tile_count;   // [V*T]
   uint32_t* tile_start;   // [V*T]
   uint32_t* tile_cursor;  // [V*T]
@@ -47,7 +48,7 @@ struct Ws {
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
 
-enum CounterSlot { kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4 };
+enum CounterSlot { kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4, kGaussCount = 5 };
 
 struct Cam {
   float R[9], t[3], fx, fy, cx, cy;

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
     for (int k = 0; k < 3; ++k) sc[k] = expf(ls[k]);
     const float o = 1.f / (1.f + expf(-logit));
     const float q_thr = 2.f * logf(o / cfg.alpha_min);
+    bool seen = false;  // a non-empty box in some view
     for (int v = 0; v < ws.views; ++v) {
       const int64_t e = (int64_t)v * n + g;
       const Cam cam = load_cam(cams, v);
@@ -178,6 +179,17 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         slot = __shfl_sync(kFull, slot, leader);
         if (ok) ws.visible[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
       }
+      seen |= ok;
+    }
+    // Gaussians seen by some view, for the backward projection pass (one
+    // atomic per warp; a warp's Gaussians stay consecutive in the list)
+    const unsigned sn = __ballot_sync(kFull, seen);
+    if (sn) {
+      const int leader = __ffs(sn) - 1;
+      uint32_t slot = 0;
+      if (lane == leader) slot = atomicAdd(ws.counters + kGaussCount, (uint32_t)__popc(sn));
+      slot = __shfl_sync(kFull, slot, leader);
+      if (seen) ws.gauss_list[slot + __popc(sn & ((1u << lane) - 1u))] = (uint32_t)g;
     }
   }
   if (smem_buckets) {

@@ -318,14 +318,16 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   float(*s_gsh)[256] = reinterpret_cast<float(*)[256]>(s_dyn);
   float(*s_sh)[256] = reinterpret_cast<float(*)[256]>(s_dyn + 3 * K * 256);
   const int64_t n = ws.n;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in_range = g < n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (ws.counters[kStatus] != 0) return;
-
-  bool any = false;
-  if (in_range)
-    for (int v = 0; v < ws.views; ++v) any |= !rect_empty(ws.rects[(int64_t)v * n + g]);
+  // one thread per Gaussian of the list of those seen by some view, so that
+  // warps are full although most of the map is outside every view
+  const uint32_t count = ws.counters[kGaussCount];
+  if ((uint64_t)blockIdx.x * blockDim.x >= count) return;  // the whole CTA
+  const uint64_t li = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool any = li < count;
+  const int64_t g = any ? (int64_t)ws.gauss_list[li] : 0;
+  const bool in_range = any;
   const bool want_pose = a.grad_pose != nullptr;
   if (!want_pose && !__any_sync(kFull, any)) return;
 
