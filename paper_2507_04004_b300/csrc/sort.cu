@@ -17,30 +17,55 @@ constexpr int kScanThreads = 1024;
 constexpr int kLongCap = 16384;      // keys sorted by a 1024-thread CTA (128 KB)
 
 // Exclusive scan of n counts by one CTA: start[i] = sum of counts before i,
-// cursor[i] = start[i]; returns the 64-bit total (to every thread).
+// cursor[i] = start[i]; returns the 64-bit total (to every thread).  Each
+// warp owns a contiguous segment and walks it 32 consecutive counts at a
+// time (coalesced), with shuffle scans; a scan over the warp totals links
+// the segments.
 __device__ unsigned long long block_scan(const uint32_t* count, uint32_t* start, uint32_t* cursor, int64_t n) {
-  __shared__ unsigned long long part[kScanThreads];
-  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
-  const int64_t b = threadIdx.x * per, e = min(n, b + per);
+  constexpr int NW = kScanThreads / 32;
+  __shared__ unsigned long long wbase[NW + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = (n + NW - 1) / NW;
+  const int64_t b = min(n, (int64_t)warp * seg), e = min(n, b + seg);
   unsigned long long s = 0;
-  for (int64_t i = b; i < e; ++i) s += count[i];
-  part[threadIdx.x] = s;
+#pragma unroll 4
+  for (int64_t i = b + lane; i < e; i += 32) s += count[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if (lane == 0) wbase[warp] = s;
   __syncthreads();
-  // Hillis-Steele inclusive scan of the partial sums
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    unsigned long long add = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
-    __syncthreads();
-    part[threadIdx.x] += add;
-    __syncthreads();
+  if (warp == 0) {
+    const unsigned long long v = wbase[lane];  // NW == 32
+    unsigned long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    wbase[lane] = inc - v;
+    if (lane == 31) wbase[NW] = inc;
   }
-  unsigned long long run = part[threadIdx.x] - s;
-  for (int64_t i = b; i < e; ++i) {
-    const uint32_t st = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
-    start[i] = st;
-    cursor[i] = st;
-    run += count[i];
+  __syncthreads();
+  unsigned long long run = wbase[warp];
+#pragma unroll 2
+  for (int64_t i0 = b; i0 < e; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const unsigned long long c = i < e ? count[i] : 0u;
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (i < e) {
+      const unsigned long long ex = run + inc - c;
+      const uint32_t st = ex > 0xffffffffull ? 0xffffffffu : (uint32_t)ex;
+      start[i] = st;
+      cursor[i] = st;
+    }
+    run += __shfl_sync(kFull, inc, 31);
   }
-  const unsigned long long total = part[kScanThreads - 1];
+  const unsigned long long total = wbase[NW];
   __syncthreads();
   return total;
 }
