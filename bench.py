@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
+    p.add_argument("--tracking-frames", type=int, default=32,
+                   help="frames in the tracking measurement (0 skips it): 1M Gaussians SH1, 640x512, N_t = 30")
     p.add_argument("--serving-requests", type=int, default=2000,
                    help="requests in the serving measurement (0 skips it); the full serving workload has 10,000")
     return p.parse_args()
@@ -328,6 +330,51 @@ def serving_workload(n_requests: int, seed: int = 2507_04004 + 5, n_calib: int =
     return g, reqs[:n_requests], np.cumsum(gaps), reqs[n_requests:]
 
 
+def run_tracking(args, dev):
+    """Pose tracking with the map fixed (N_t = 30 Adam iterations of
+    1/2 L1 + 1/2 D-SSIM per frame, all frames as one batch, one captured
+    graph): frames per second and the pose error before and after."""
+    import numpy as np
+    import torch
+
+    from paper_2507_04004_b300 import synth
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
+    from paper_2507_04004_b300.track import PoseTracker
+    V = args.tracking_frames
+    w = synth.tracking(n_frames=V)
+    gm = GaussianMap.from_host(w.gmap, device=dev)
+    H, W = 512, 640
+    r = Rasterizer(gm.n, V, W, H, device=dev)
+    targets = r.render(gm, cameras_tensor(w.meta["gt_cams"], device=dev)).rgb.clone()  # images at the true poses
+    del r
+    tr = PoseTracker(gm, V, W, H, iters=30, device=dev)
+    q = cameras_tensor(w.cams, device=dev)
+    for _ in range(2):  # sizing pass, capture, first replay
+        xi, loss = tr.track(q, targets)
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        xi, loss = tr.track(q, targets)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    xi = xi.cpu().numpy().astype(np.float64)
+    true = -w.meta["xi"]
+    rot0 = np.degrees(np.linalg.norm(true[:, 3:], axis=1))
+    rot1 = np.degrees(np.linalg.norm(xi[:, 3:] - true[:, 3:], axis=1))
+    tr0 = np.linalg.norm(true[:, :3], axis=1)
+    tr1 = np.linalg.norm(xi[:, :3] - true[:, :3], axis=1)
+    return {"workload": f"1M Gaussians SH1, {V} frames 640x512 (fx = 500) tracked together, N_t = 30, "
+                        "loss 1/2 L1 + 1/2 D-SSIM, start GT Exp(xi) with theta ~ N(0, 0.02 rad), rho ~ N(0, 0.05 m)",
+            "ms_per_batch": round(ms, 3), "frames_per_s": round(V / (ms / 1e3), 1),
+            "ms_per_iteration": round(ms / 30, 4),
+            "rot_err_deg_median": [round(float(np.median(rot0)), 4), round(float(np.median(rot1)), 4)],
+            "trans_err_m_median": [round(float(np.median(tr0)), 4), round(float(np.median(tr1)), 4)],
+            "note": "errors [before, after]; timed: the captured 30-iteration graph incl. the status read-back"}
+
+
 def run_serving(args, dev):
     """p50/p99 latency under Poisson arrivals and closed-loop throughput,
     batched server vs plain one-request-at-a-time rendering."""
@@ -562,10 +609,14 @@ def run_ours(args):
     total_px = d.sum(px_step * args.steps)
     value = total_px / (ms / 1e3) / 1e6
 
-    serving = None
-    if d.rank == 0 and args.serving_requests > 0:
+    serving = tracking = None
+    if d.rank == 0 and (args.serving_requests > 0 or args.tracking_frames > 0):
         del out, grads
         torch.cuda.empty_cache()
+    if d.rank == 0 and args.tracking_frames > 0:
+        tracking = run_tracking(args, d.dev)
+        torch.cuda.empty_cache()
+    if d.rank == 0 and args.serving_requests > 0:
         serving = run_serving(args, d.dev)
 
     cpu = None
@@ -588,6 +639,7 @@ def run_ours(args):
                 "gpu_launches": int(launches),
                 "roofline": roofline,
                 "cpu_baseline": cpu,
+                "tracking": tracking,
                 "serving": serving,
                 "kernels": kernels,
                 "work": {"visible_entries": n_visible, "pairs": n_pairs, "row_items": n_rows,

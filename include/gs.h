@@ -166,17 +166,21 @@ gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb
                         float* t_final, uint32_t* n_contrib, gs_stream_t stream);
 
 /* Backward pass (Eq. depth_loss back through Eq. rendered_* and the
- * projection).  Pixel adjoints are either the fused loss (tgt_rgb != NULL):
+ * projection).  Pixel adjoints are the fused loss (tgt_rgb != NULL):
  *   L_v = w_rgb mean_{3HW} |C^ - C| + w_depth / |M_d| sum_{D_s>0, O^>0} |D^/O^ - D_s|,
- *   |M_d| = #(D_s > 0) per view, L = sum_v L_v, sign(0) = 0;
- * or the caller's dL/dC^ [V][3][H][W], dL/dD^ [V][H][W], dL/dO^ [V][H][W]
- * (tgt_rgb == NULL; any of the three may be NULL = zero).  Recomputes each
+ *   |M_d| = #(D_s > 0) per view, L = sum_v L_v, sign(0) = 0,
+ * plus the caller's dL/dC^ [V][3][H][W], dL/dD^ [V][H][W], dL/dO^ [V][H][W]
+ * where given (any of the three may be NULL = zero; with tgt_rgb == NULL they
+ * are the whole adjoint, e.g. of an autograd graph; with it they add further
+ * loss terms such as gs_dssim's gradient).  Recomputes each
  * pixel's blending state back to front from t_final and n_contrib.
  * Gradients are ADDED to grad_* (caller zeroes them): grad_mean [3][N],
  * grad_log_scale [3][N], grad_quat [4][N], grad_logit_opacity [N],
  * grad_sh_dc [3][N], grad_sh_rest [K-1][3][N] (FP32 even for BF16 SH; may be
  * NULL when sh_degree == 0), grad_pose [V][6] = dL/d(rho, theta) of
- * T_v Exp(xi) (may be NULL), loss_out [V] (may be NULL; added to). */
+ * T_v Exp(xi) (may be NULL), loss_out [V] (may be NULL; added to).  The six
+ * parameter-gradient pointers may also all be NULL when grad_pose is given:
+ * the pose gradient alone (camera tracking with the map fixed). */
 gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
                         const float* rgb, const float* depth, const float* opac, const float* t_final,
                         const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
@@ -194,6 +198,46 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
 gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
                            const gs_workspace* ws, const int32_t* pix_idx, int32_t n_pix, float* J, float* rgb_out,
                            gs_stream_t stream);
+
+/* D-SSIM term of the mapping loss (Sec. "Map Optimization") and of the
+ * tracking loss (Eq. tracking_loss): per view, D = 1 - mean SSIM(img, tgt)
+ * over its 3 channels and H x W pixels, SSIM of Wang et al. under an 11 x 11
+ * Gaussian window (sigma 1.5, zero padding, C1 = 1e-4, C2 = 9e-4; the paper
+ * takes the term from 3D Gaussian Splatting), computed with separable filters
+ * (Sec. "Additional Strategies" (c)).  img, tgt: device [V][3][H][W] FP32.
+ * Adds weight * D_v to loss[v] (loss may be NULL) and weight * dD_v/dimg to
+ * dl_dimg [V][3][H][W] (may be NULL; e.g. the buffer later passed to
+ * gs_render_bwd as dl_drgb).  scratch: caller-owned device buffer of
+ * gs_dssim_scratch_bytes(V, H, W) bytes, 256-byte aligned, overwritten.
+ * GS_ERR_ARG for missing pointers or sizes, GS_ERR_UNSUPPORTED for more than
+ * 21845 views. */
+size_t gs_dssim_scratch_bytes(int32_t n_views, int32_t height, int32_t width);
+gs_status gs_dssim(const float* img, const float* tgt, int32_t n_views, int32_t height, int32_t width, float weight,
+                   float* loss, float* dl_dimg, void* scratch, gs_stream_t stream);
+
+/* Camera tracking with the map fixed (Sec. "Camera Factor (Option 2)": N_t
+ * Adam iterations on the pose for the loss of Eq. tracking_loss).  The pose
+ * of view v is the right perturbation T_v = T0_v Exp(xi_v) of an initial
+ * world-to-camera transform, xi = (rho, theta) translation first, the
+ * convention of gs_render_bwd's grad_pose.
+ * gs_pose_apply: cams_out[v] = cams0[v] with R, t replaced by those of
+ * T0_v Exp(xi_v) (Rodrigues rotation, V-matrix translation); all device
+ * pointers, xi [V][6].  gs_adam_pose: one Adam step (Kingma and Ba, bias
+ * corrected) on xi [V][6] with gradient grad [V][6] (cleared afterwards, for
+ * the next gs_render_bwd to add into), first/second moments m, v [V][6] and a
+ * device step counter (int32, start at 0); lr per component of xi.  With
+ * loss_dev [V] (the loss at the current xi, e.g. gs_render_bwd's loss_out),
+ * best_loss_dev [V] (start at +inf) and best_xi_dev [V][6] all given, the
+ * iterate of lowest loss so far is kept per view (all three NULL: not kept). */
+typedef struct {
+  float lr[6];
+  float beta1, beta2, eps;
+} gs_adam_config;
+gs_status gs_pose_apply(const gs_camera* cams0_dev, const float* xi_dev, int32_t n_views, gs_camera* cams_out_dev,
+                        gs_stream_t stream);
+gs_status gs_adam_pose(float* xi_dev, float* grad_dev, float* m_dev, float* v_dev, int32_t* step_dev,
+                       int32_t n_views, const gs_adam_config* cfg, const float* loss_dev, float* best_loss_dev,
+                       float* best_xi_dev, gs_stream_t stream);
 
 /* Forward render that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc - code running

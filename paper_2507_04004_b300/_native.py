@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_PKG, "libgsb300.so")
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(7)
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_trace_start",
+            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
+            "gs_dssim", "gs_pose_apply", "gs_adam_pose", "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
 
@@ -51,6 +52,10 @@ class gs_layout(C.Structure):
                                           "keys_alt", "sorted_ids", "view_stats", "total")]
 
 
+class gs_adam_config(C.Structure):
+    _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class GsError(RuntimeError):
     def __init__(self, fn: str, code: int):
         super().__init__(f"{fn} failed: {status_str(code)} ({code})")
@@ -82,6 +87,11 @@ def lib():
         L.gs_render_fwd_noalloc.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_frame), C.POINTER(gs_config),
                                             P, P, P, P, P, P, P]
         L.gs_render_fwd_noalloc.restype = I32
+        L.gs_dssim_scratch_bytes.argtypes = [I32, I32, I32]
+        L.gs_dssim_scratch_bytes.restype = C.c_size_t
+        L.gs_dssim.argtypes = [P, P, I32, I32, I32, F, P, P, P, P]
+        L.gs_pose_apply.argtypes = [P, P, I32, P, P]
+        L.gs_adam_pose.argtypes = [P, P, P, P, P, I32, C.POINTER(gs_adam_config), P, P, P, P]
         L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
         L.gs_trace_start.restype = I32
         L.gs_trace_stop.argtypes = []
@@ -92,7 +102,7 @@ def lib():
         L.gs_status_str.restype = C.c_char_p
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
-                     "gs_pose_jacobian", "gs_workspace_layout"):
+                     "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose"):
             getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -153,6 +163,28 @@ def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth,
 def gs_pose_jacobian(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, pix, n_pix: int, J, rgb, stream: int) -> None:
     check("gs_pose_jacobian", lib().gs_pose_jacobian(C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(pix),
                                                      int(n_pix), _ptr(J), _ptr(rgb), C.c_void_p(stream)))
+
+
+def gs_dssim_scratch_bytes(n_views: int, height: int, width: int) -> int:
+    return int(lib().gs_dssim_scratch_bytes(int(n_views), int(height), int(width)))
+
+
+def gs_dssim(img, tgt, n_views: int, height: int, width: int, weight: float, loss, dl_dimg, scratch,
+             stream: int) -> None:
+    check("gs_dssim", lib().gs_dssim(_ptr(img), _ptr(tgt), int(n_views), int(height), int(width), float(weight),
+                                     _ptr(loss), _ptr(dl_dimg), _ptr(scratch), C.c_void_p(stream)))
+
+
+def gs_pose_apply(cams0, xi, n_views: int, cams_out, stream: int) -> None:
+    check("gs_pose_apply", lib().gs_pose_apply(_ptr(cams0), _ptr(xi), int(n_views), _ptr(cams_out),
+                                               C.c_void_p(stream)))
+
+
+def gs_adam_pose(xi, grad, m, v, step, n_views: int, cfg: "gs_adam_config", stream: int, loss=None,
+                 best_loss=None, best_xi=None) -> None:
+    check("gs_adam_pose", lib().gs_adam_pose(_ptr(xi), _ptr(grad), _ptr(m), _ptr(v), _ptr(step), int(n_views),
+                                             C.byref(cfg), _ptr(loss), _ptr(best_loss), _ptr(best_xi),
+                                             C.c_void_p(stream)))
 
 
 def gs_render_fwd_noalloc(m: gs_map, cams, frame: gs_frame, cfg: gs_config, rgb, depth, opac, t_final, n_contrib,

@@ -207,8 +207,14 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
   if ((s = check_map(map, ws)) != GS_OK) return s;
   if ((s = check_cfg(cfg)) != GS_OK) return s;
   if (!cams_dev || !t_final || !n_contrib) return GS_ERR_ARG;
-  if (!grad_mean || !grad_log_scale || !grad_quat || !grad_logit_opacity || !grad_sh_dc) return GS_ERR_ARG;
-  if (map->sh_degree > 0 && !grad_sh_rest) return GS_ERR_ARG;
+  // parameter gradients: all given, or none (pose gradient only)
+  const bool params = grad_mean || grad_log_scale || grad_quat || grad_logit_opacity || grad_sh_dc || grad_sh_rest;
+  if (params) {
+    if (!grad_mean || !grad_log_scale || !grad_quat || !grad_logit_opacity || !grad_sh_dc) return GS_ERR_ARG;
+    if (map->sh_degree > 0 && !grad_sh_rest) return GS_ERR_ARG;
+  } else if (!grad_pose) {
+    return GS_ERR_ARG;
+  }
   if (tgt_rgb) {
     if (!rgb) return GS_ERR_ARG;
     if (tgt_depth && w_depth != 0.f && (!depth || !opac)) return GS_ERR_ARG;
@@ -237,6 +243,38 @@ gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const g
                                           reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_pose_apply(const gs_camera* cams0_dev, const float* xi_dev, int32_t n_views, gs_camera* cams_out_dev,
+                        gs_stream_t stream) {
+  if (!cams0_dev || !xi_dev || !cams_out_dev || n_views < 1) return GS_ERR_ARG;
+  return cuda_status(launch_pose_apply(cams0_dev, xi_dev, n_views, cams_out_dev,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_adam_pose(float* xi_dev, float* grad_dev, float* m_dev, float* v_dev, int32_t* step_dev,
+                       int32_t n_views, const gs_adam_config* cfg, const float* loss_dev, float* best_loss_dev,
+                       float* best_xi_dev, gs_stream_t stream) {
+  if (!xi_dev || !grad_dev || !m_dev || !v_dev || !step_dev || !cfg || n_views < 1) return GS_ERR_ARG;
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps > 0.f))
+    return GS_ERR_ARG;
+  if ((loss_dev || best_loss_dev || best_xi_dev) && !(loss_dev && best_loss_dev && best_xi_dev)) return GS_ERR_ARG;
+  return cuda_status(launch_adam_pose(xi_dev, grad_dev, m_dev, v_dev, step_dev, n_views, *cfg, loss_dev,
+                                      best_loss_dev, best_xi_dev, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t gs_dssim_scratch_bytes(int32_t n_views, int32_t height, int32_t width) {
+  if (n_views < 1 || height < 1 || width < 1) return 0;
+  return dssim_scratch_bytes(n_views, height, width);
+}
+
+gs_status gs_dssim(const float* img, const float* tgt, int32_t n_views, int32_t height, int32_t width, float weight,
+                   float* loss, float* dl_dimg, void* scratch, gs_stream_t stream) {
+  if (!img || !tgt || !scratch || n_views < 1 || height < 1 || width < 1) return GS_ERR_ARG;
+  if ((int64_t)n_views * 3 > 65535) return GS_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return GS_ERR_ARG;
+  return cuda_status(launch_dssim(img, tgt, n_views, height, width, weight, loss, dl_dimg, scratch,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+}
+
 gs_status gs_trace_start(void* const* events, int32_t capacity, int32_t* kernel_ids) {
   if (!events || capacity < 1) return GS_ERR_ARG;
   g_trace.events = reinterpret_cast<cudaEvent_t*>(const_cast<void**>(events));
@@ -256,7 +294,7 @@ const char* gs_kernel_name(int32_t id) {
   static const char* names[kKNumKernels] = {"project",     "scan",           "scatter_rows",  "sort_small",
                                             "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
                                             "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
-                                            "rows_emit"};
+                                            "rows_emit",   "ssim_fwd",       "ssim_bwd"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -245,6 +245,17 @@ __device__ __forceinline__ float blend_p2(float4 g0, float4 g1, float px, float 
   return col_p2(col_terms(g0, g1, px), py);
 }
 
+// 2^x on the special-function unit (PTX ex2.approx.ftz.f32: relative error
+// near 2^-22, subnormal results flushed to zero).  Every alpha that takes
+// part in compositing is >= alpha_min, far from the subnormal range; the
+// forward, backward and Jacobian kernels all use this one function, so they
+// see the same alpha.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Packed FP32 pairs: the blend kernels evaluate two vertically adjacent
 // pixels per instruction with the sm_100+ f32x2 FMA/ADD/MUL.  Each half is
 // rounded exactly like the scalar __fmaf_rn / __fadd_rn / __fmul_rn, so

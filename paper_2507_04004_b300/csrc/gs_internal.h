@@ -11,7 +11,7 @@ namespace gsb {
 // Kernel ids reported by the tracing hook (gs_trace_start).
 enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
-  kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKNumKernels
+  kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);
@@ -24,6 +24,13 @@ int sm_count();
 cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                            cudaStream_t st);
 cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st);
+size_t dssim_scratch_bytes(int V, int H, int W);
+cudaError_t launch_pose_apply(const gs_camera* cams0, const float* xi, int V, gs_camera* cams_out, cudaStream_t st);
+cudaError_t launch_adam_pose(float* xi, float* grad, float* m, float* s, int32_t* step, int V,
+                             const gs_adam_config& hp, const float* loss, float* best_loss, float* best_xi,
+                             cudaStream_t st);
+cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W, float weight, float* loss,
+                         float* dl_dimg, void* scratch, cudaStream_t st);
 cudaError_t launch_render_fwd(const gs_config& cfg, const Ws& ws, float* rgb, float* depth, float* opac,
                               float* t_final, uint32_t* n_contrib, cudaStream_t st);
 

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128) k_pose_jacobian(gs_map map, const gs_came
     const Staged sg = stage_gaussian(r0, r1);
     const float p2 = blend_p2(sg.g0, sg.g1, px, py);
     if (!(p2 >= lt)) continue;
-    const float araw = exp2f(p2);
+    const float araw = ex2_approx(p2);
     const bool clamped = araw > cfg.alpha_max;
     const float al = fminf(cfg.alpha_max, araw);
     const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));

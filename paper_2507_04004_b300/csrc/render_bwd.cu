@@ -138,6 +138,14 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
           loss += a.w_depth * fabsf(rd) / nd;
         }
       }
+      // further pixel adjoints of other loss terms (e.g. D-SSIM) add to the fused ones
+      if (a.dl_drgb) {
+        gC0[k] += a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
+        gC1[k] += a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
+        gC2[k] += a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
+      }
+      if (a.dl_ddepth) gD[k] += a.dl_ddepth[v * HW + p];
+      if (a.dl_dopac) gO[k] += a.dl_dopac[v * HW + p];
     } else {
       if (a.dl_drgb) {
         gC0[k] = a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
         const bool a0 = act[2 * h], a1 = act[2 * h + 1];
-        const float e0 = exp2f(p2[h].x), e1 = exp2f(p2[h].y);
+        const float e0 = ex2_approx(p2[h].x), e1 = ex2_approx(p2[h].y);
         float2 al, ag;
         if (decltype(clamp)::value) {
           al = make_float2(a0 ? fminf(a_max, e0) : 0.f, a1 ? fminf(a_max, e1) : 0.f);
@@ -503,7 +511,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
       __syncthreads();
     }
   }
-  if (!any) return;
+  if (!any || !a.grad_mean) return;  // no parameter gradients wanted: pose only
   // quaternion: R(q^) entries -> q^ -> q (normalisation)
   const float gw = 2.f * (-qz * g_R[0][1] + qy * g_R[0][2] + qz * g_R[1][0] - qx * g_R[1][2] - qy * g_R[2][0] +
                           qx * g_R[2][1]);

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
         // would drop under t_min (then it is done and this Gaussian is not blended)
         const float2 p2 = col_p2x2(ct, Y[h]);
         const bool a0 = !done[2 * h] & (p2.x >= lt), a1 = !done[2 * h + 1] & (p2.y >= lt);
-        const float2 al = make_float2(fminf(a_max, exp2f(p2.x)), fminf(a_max, exp2f(p2.y)));
+        const float2 al = make_float2(fminf(a_max, ex2_approx(p2.x)), fminf(a_max, ex2_approx(p2.y)));
         const float2 Tc = mul2(T[h], fma2(al, f2(-1.f), f2(1.f)));
         const bool s0 = a0 & (Tc.x < t_min), s1 = a1 & (Tc.y < t_min);
         const bool k0 = a0 & !s0, k1 = a1 & !s1;

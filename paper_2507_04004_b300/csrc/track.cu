@@ -1,0 +1,108 @@
+// Camera tracking against a fixed map (Sec. "Camera Factor (Option 2)"): the
+// pose of each frame is optimised for N_t Adam iterations on the loss of
+// Eq. tracking_loss while the Gaussians stay fixed.  The pose is
+// parameterised as the right perturbation T_v = T0_v Exp(xi_v) of an initial
+// world-to-camera transform, xi = (rho, theta), the same convention as the
+// pose gradient of Eq. 3dgs_jacobi in gs_render_bwd, so that gradient is the
+// Adam gradient as it stands.  Two small kernels: apply the perturbation to
+// the camera batch, and the Adam step on every view's xi.
+#include <cmath>
+
+#include "gs_internal.h"
+
+namespace gsb {
+
+// Exp of a twist xi = (rho, theta): R = exp([theta]x) (Rodrigues), t = V rho,
+// V = I + (1 - cos p)/p^2 [theta]x + (p - sin p)/p^3 [theta]x^2, p = |theta|;
+// series for small p.  Writes cams_out[v] = cams0[v] * Exp(xi[v]):
+// R = R0 R_xi, t = R0 V rho + t0, intrinsics copied.
+__global__ void k_pose_apply(const gs_camera* __restrict__ cams0, const float* __restrict__ xi, int V,
+                             gs_camera* __restrict__ cams_out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float* x = xi + 6 * v;
+  const float r0 = x[0], r1 = x[1], r2 = x[2], w0 = x[3], w1 = x[4], w2 = x[5];
+  const float p2 = w0 * w0 + w1 * w1 + w2 * w2;
+  float a, b, c;  // sin p / p, (1 - cos p) / p^2, (p - sin p) / p^3
+  if (p2 < 1e-8f) {
+    a = 1.f - p2 / 6.f;
+    b = 0.5f - p2 / 24.f;
+    c = 1.f / 6.f - p2 / 120.f;
+  } else {
+    const float p = sqrtf(p2);
+    const float s = sinf(p), co = cosf(p);
+    a = s / p;
+    b = (1.f - co) / p2;
+    c = (p - s) / (p2 * p);
+  }
+  // [w]x and [w]x^2
+  const float K[3][3] = {{0.f, -w2, w1}, {w2, 0.f, -w0}, {-w1, w0, 0.f}};
+  float K2[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[i][j] = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
+  float R[3][3], Vm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const float id = i == j ? 1.f : 0.f;
+      R[i][j] = id + a * K[i][j] + b * K2[i][j];
+      Vm[i][j] = id + b * K[i][j] + c * K2[i][j];
+    }
+  const float tx[3] = {Vm[0][0] * r0 + Vm[0][1] * r1 + Vm[0][2] * r2, Vm[1][0] * r0 + Vm[1][1] * r1 + Vm[1][2] * r2,
+                       Vm[2][0] * r0 + Vm[2][1] * r1 + Vm[2][2] * r2};
+  const gs_camera c0 = cams0[v];
+  gs_camera out = c0;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j)
+      out.R[3 * i + j] = c0.R[3 * i + 0] * R[0][j] + c0.R[3 * i + 1] * R[1][j] + c0.R[3 * i + 2] * R[2][j];
+    out.t[i] = c0.R[3 * i + 0] * tx[0] + c0.R[3 * i + 1] * tx[1] + c0.R[3 * i + 2] * tx[2] + c0.t[i];
+  }
+  cams_out[v] = out;
+}
+
+// One Adam step (Kingma and Ba) on every view's xi with per-component
+// learning rates; the step counter lives on the device so that a captured
+// loop of iterations replays correctly.  The gradient is cleared for the next
+// backward pass (which adds to it).  With loss / best_loss / best_xi given,
+// the iterate whose loss (evaluated before this step) is the lowest so far is
+// kept per view.
+__global__ void k_adam_pose(float* __restrict__ xi, float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ s, int32_t* __restrict__ step, int V, gs_adam_config hp,
+                            const float* __restrict__ loss, float* __restrict__ best_loss,
+                            float* __restrict__ best_xi) {
+  const int t = *step + 1;
+  const bool keep = loss && best_loss && best_xi;
+  for (int i = threadIdx.x; i < 6 * V; i += blockDim.x) {
+    if (keep && loss[i / 6] < best_loss[i / 6]) best_xi[i] = xi[i];
+  }
+  __syncthreads();  // every component has compared against the old best before it changes
+  if (keep)
+    for (int v = threadIdx.x; v < V; v += blockDim.x)
+      if (loss[v] < best_loss[v]) best_loss[v] = loss[v];
+  for (int i = threadIdx.x; i < 6 * V; i += blockDim.x) {
+    const float g = grad[i];
+    const float mi = hp.beta1 * m[i] + (1.f - hp.beta1) * g;
+    const float si = hp.beta2 * s[i] + (1.f - hp.beta2) * g * g;
+    m[i] = mi;
+    s[i] = si;
+    const float mh = mi / (1.f - powf(hp.beta1, (float)t));
+    const float sh = si / (1.f - powf(hp.beta2, (float)t));
+    xi[i] -= hp.lr[i % 6] * mh / (sqrtf(sh) + hp.eps);
+    grad[i] = 0.f;
+  }
+  __syncthreads();  // one block: every thread has read *step before it advances
+  if (threadIdx.x == 0) *step = t;
+}
+
+cudaError_t launch_pose_apply(const gs_camera* cams0, const float* xi, int V, gs_camera* cams_out, cudaStream_t st) {
+  k_pose_apply<<<(V + 63) / 64, 64, 0, st>>>(cams0, xi, V, cams_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_pose(float* xi, float* grad, float* m, float* s, int32_t* step, int V,
+                             const gs_adam_config& hp, const float* loss, float* best_loss, float* best_xi,
+                             cudaStream_t st) {
+  k_adam_pose<<<1, 1024, 0, st>>>(xi, grad, m, s, step, V, hp, loss, best_loss, best_xi);
+  return cudaGetLastError();
+}
+
+}  // namespace gsb

@@ -204,14 +204,17 @@ class Rasterizer:
 
     def backward(self, gmap: GaussianMap, cams: torch.Tensor, out: RenderOut, tgt_rgb=None, tgt_depth=None,
                  w_rgb: float = 1.0, w_depth: float = 0.0, dl_drgb=None, dl_ddepth=None, dl_dopac=None,
-                 grads: Grads | None = None, pose: bool = True) -> Grads:
+                 grads: Grads | None = None, pose: bool = True, params: bool = True) -> Grads:
         """Adds dL/dparams into ``grads`` (zeros when None) for the fused loss
-        (``tgt_rgb`` given) or the external pixel adjoints ``dl_*``."""
+        (``tgt_rgb`` given; ``dl_*`` given as well add further loss terms) or
+        the external pixel adjoints ``dl_*`` alone.  ``params=False``: the
+        pose gradient (and loss) only, the map held fixed."""
         g = grads if grads is not None else self.new_grads(gmap)
+        pg = (lambda t: t) if params else (lambda t: None)
         N.gs_render_bwd(gmap.struct(), cams, self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final,
-                        out.n_contrib, tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, g.mean,
-                        g.log_scale, g.quat, g.logit_opacity, g.sh_dc,
-                        g.sh_rest if gmap.sh_degree > 0 else None, g.pose if pose else None, g.loss,
+                        out.n_contrib, tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, pg(g.mean),
+                        pg(g.log_scale), pg(g.quat), pg(g.logit_opacity), pg(g.sh_dc),
+                        pg(g.sh_rest) if gmap.sh_degree > 0 else None, g.pose if pose else None, g.loss,
                         self._stream())
         return g
 
@@ -259,3 +262,25 @@ def rasterize(rast: Rasterizer, cams, xi, gmap_params: dict, sh_degree: int):
     p = gmap_params
     return RasterizeFn.apply(rast, cams, xi, p["mean"], p["log_scale"], p["quat"], p["logit_opacity"], p["sh_dc"],
                              p["sh_rest"], sh_degree)
+
+
+class DSSIM:
+    """D-SSIM term (1 - mean SSIM per view, the 3DGS definition the paper's
+    mapping and tracking losses use) on [V][3][H][W] images, through
+    ``gs_dssim``; holds the scratch buffer for one image geometry."""
+
+    def __init__(self, n_views: int, height: int, width: int, device="cuda"):
+        self.shape = (int(n_views), int(height), int(width))
+        nbytes = N.gs_dssim_scratch_bytes(*self.shape)
+        self._buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self._buf.data_ptr()) % 256
+        self.scratch = self._buf[off:off + nbytes]
+
+    def __call__(self, img: torch.Tensor, tgt: torch.Tensor, weight: float = 1.0, loss: torch.Tensor | None = None,
+                 dl_dimg: torch.Tensor | None = None) -> None:
+        """Adds weight * D_v to loss[v] and weight * dD_v/dimg to dl_dimg (either may be None)."""
+        V, H, W = self.shape
+        if img.shape != (V, 3, H, W) or tgt.shape != img.shape:
+            raise ValueError("image batch does not match the D-SSIM geometry")
+        N.gs_dssim(img, tgt, V, H, W, weight, loss, dl_dimg, self.scratch,
+                   torch.cuda.current_stream(img.device).cuda_stream)

@@ -215,6 +215,35 @@ def test_tiny_fused_loss_gradients(oracle):
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
 
 
+def test_fused_loss_plus_external_adjoints_and_pose_only(oracle):
+    """The fused loss with further pixel adjoints added equals the sum of the
+    two backward passes (linearity in the pixel adjoints), and the pose-only
+    backward (no parameter gradients) gives the pose gradient of the full one."""
+    w = synth.tiny()
+    m = host_map(w.gmap)
+    tgt_d = _tiny_depth_target(oracle, w, m)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    tr = torch.as_tensor(w.tgt_rgb, device="cuda")
+    td = torch.as_tensor(tgt_d, device="cuda")
+    rng = np.random.default_rng(12)
+    er = torch.as_tensor(1e-4 * rng.normal(size=(1, 3, 96, 128)).astype(np.float32), device="cuda")
+    ed = torch.as_tensor(1e-5 * rng.normal(size=(1, 96, 128)).astype(np.float32), device="cuda")
+    fused = lambda **k: grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb,
+                                                     w_depth=w.w_depth, **k))
+    g1 = fused()
+    g2 = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=er, dl_ddepth=ed))
+    g3 = fused(dl_drgb=er, dl_ddepth=ed)
+    for k in GRAD_KEYS + ("pose",):
+        if g1[k].size:  # sh_rest is empty at SH degree 0
+            assert rel_err(g3[k], g1[k] + g2[k]) <= 1e-5, k
+    gp = rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth, params=False)
+    gp = grads_to_numpy(gp)
+    assert rel_err(gp["pose"], g1["pose"]) <= 1e-5
+    assert gp["loss"][0] == pytest.approx(g1["loss"][0], rel=1e-6)
+    for k in GRAD_KEYS:
+        assert not np.any(gp[k]), k
+
+
 def test_alpha_clamp_path(oracle):
     """A fifth of the Gaussians with opacity 0.9975, so that alpha is clamped
     at alpha_max near their centres (the blend kernels take a separate path
