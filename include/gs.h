@@ -239,6 +239,55 @@ gs_status gs_adam_pose(float* xi_dev, float* grad_dev, float* m_dev, float* v_de
                        int32_t n_views, const gs_adam_config* cfg, const float* loss_dev, float* best_loss_dev,
                        float* best_xi_dev, gs_stream_t stream);
 
+/* Sparse Adam over the map (Sec. "Additional Strategies" (a)): one Adam step
+ * (Kingma and Ba, bias corrected with the device step counter step_dev,
+ * advanced by one) on the Gaussians that took part in the workspace's last
+ * gs_project batch (those with a tile box in some view); every other
+ * Gaussian keeps its parameters and moments.  params / grads / m / v: FP32
+ * SoA arrays in the gs_map layout (n = the workspace's Gaussian count; sh_rest
+ * [K-1][3][N] may be NULL at sh_degree 0).  The gradients of the updated
+ * Gaussians are cleared afterwards.  Learning rates per attribute; the paper
+ * takes those of 3D Gaussian Splatting without decay. */
+typedef struct {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* logit_opacity;
+  float* sh_dc;
+  float* sh_rest;
+} gs_param_set;
+typedef struct {
+  float lr_mean, lr_log_scale, lr_quat, lr_logit_opacity, lr_sh_dc, lr_sh_rest;
+  float beta1, beta2, eps;
+} gs_adam_map_config;
+gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_param_set* params,
+                         const gs_param_set* grads, const gs_param_set* m, const gs_param_set* v, int32_t* step_dev,
+                         const gs_adam_map_config* cfg, gs_stream_t stream);
+
+/* Map expansion (Sec. "Expansion of Gaussian Map"): from the opacity map O
+ * of a new keyframe (gs_render_fwd's opac, [H][W] of one view), the mask
+ * O < tau (the paper: 0.99) marks newly observed regions, and only the points
+ * projecting into it initialise new Gaussians.
+ * gs_expand_select: points [3][P] world positions (device), cam_dev one
+ * camera, cfg->near_z the near plane; writes the indices of the selected
+ * points, ascending, to idx_out [P] and their number to *count_out (device
+ * uint32).  A point is selected iff its depth exceeds near_z and the pixel
+ * containing its projection (pixel i spans [i, i + 1)) lies in the image with
+ * O < tau.  scratch: gs_expand_scratch_bytes(P) bytes, 256-byte aligned.
+ * gs_expand_init: writes the *count_dev new Gaussians for idx_dev into dst at
+ * [first, first + count) of FP32 SoA arrays holding n_dst Gaussians (entries
+ * past n_dst are dropped): mean = the point, log-scales log(2 d / fx) (two
+ * pixels across at depth d), quaternion (1, 0, 0, 0), opacity init_opacity,
+ * SH DC from rgb_dev [3][P] in [0, 1] (colour = 0.5 + Y_00 DC), higher SH 0
+ * (readings: the paper takes the initialisation from its predecessors). */
+size_t gs_expand_scratch_bytes(int64_t n_points);
+gs_status gs_expand_select(const float* points_dev, int64_t n_points, const gs_camera* cam_dev, const gs_config* cfg,
+                           const float* opac_dev, int32_t height, int32_t width, float tau, void* scratch,
+                           int32_t* idx_out, uint32_t* count_out, gs_stream_t stream);
+gs_status gs_expand_init(const float* points_dev, const float* rgb_dev, int64_t n_points, const int32_t* idx_dev,
+                         const uint32_t* count_dev, const gs_camera* cam_dev, int64_t first, const gs_param_set* dst,
+                         int64_t n_dst, int32_t sh_degree, float init_opacity, gs_stream_t stream);
+
 /* Forward render that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc - code running
  * inside a host framework that owns all device memory (an inference-engine

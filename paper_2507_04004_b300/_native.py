@@ -15,7 +15,8 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
-            "gs_dssim", "gs_pose_apply", "gs_adam_pose", "gs_trace_start",
+            "gs_dssim", "gs_pose_apply", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
+            "gs_expand_select", "gs_expand_init", "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
 
@@ -56,6 +57,15 @@ class gs_adam_config(C.Structure):
     _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class gs_param_set(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("mean", "log_scale", "quat", "logit_opacity", "sh_dc", "sh_rest")]
+
+
+class gs_adam_map_config(C.Structure):
+    _fields_ = [(k, C.c_float) for k in ("lr_mean", "lr_log_scale", "lr_quat", "lr_logit_opacity", "lr_sh_dc",
+                                         "lr_sh_rest", "beta1", "beta2", "eps")]
+
+
 class GsError(RuntimeError):
     def __init__(self, fn: str, code: int):
         super().__init__(f"{fn} failed: {status_str(code)} ({code})")
@@ -91,6 +101,12 @@ def lib():
         L.gs_dssim_scratch_bytes.restype = C.c_size_t
         L.gs_dssim.argtypes = [P, P, I32, I32, I32, F, P, P, P, P]
         L.gs_pose_apply.argtypes = [P, P, I32, P, P]
+        L.gs_expand_scratch_bytes.argtypes = [I64]
+        L.gs_expand_scratch_bytes.restype = C.c_size_t
+        L.gs_expand_select.argtypes = [P, I64, P, C.POINTER(gs_config), P, I32, I32, F, P, P, P, P]
+        L.gs_expand_init.argtypes = [P, P, I64, P, P, P, I64, C.POINTER(gs_param_set), I64, I32, F, P]
+        L.gs_sparse_adam.argtypes = [C.POINTER(gs_workspace), I32] + [C.POINTER(gs_param_set)] * 4 + [
+            P, C.POINTER(gs_adam_map_config), P]
         L.gs_adam_pose.argtypes = [P, P, P, P, P, I32, C.POINTER(gs_adam_config), P, P, P, P]
         L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
         L.gs_trace_start.restype = I32
@@ -102,7 +118,8 @@ def lib():
         L.gs_status_str.restype = C.c_char_p
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
-                     "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose"):
+                     "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose",
+                     "gs_sparse_adam", "gs_expand_select", "gs_expand_init"):
             getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -185,6 +202,38 @@ def gs_adam_pose(xi, grad, m, v, step, n_views: int, cfg: "gs_adam_config", stre
     check("gs_adam_pose", lib().gs_adam_pose(_ptr(xi), _ptr(grad), _ptr(m), _ptr(v), _ptr(step), int(n_views),
                                              C.byref(cfg), _ptr(loss), _ptr(best_loss), _ptr(best_xi),
                                              C.c_void_p(stream)))
+
+
+def param_set(t) -> gs_param_set:
+    """gs_param_set of an object with the six SoA tensors (GaussianMap or Grads)."""
+    rest = getattr(t, "sh_rest")
+    return gs_param_set(*(C.c_void_p(x.data_ptr()) if x is not None and x.numel() else None
+                          for x in (t.mean, t.log_scale, t.quat, t.logit_opacity, t.sh_dc, rest)))
+
+
+def gs_sparse_adam(ws: gs_workspace, sh_degree: int, params: gs_param_set, grads: gs_param_set, m: gs_param_set,
+                   v: gs_param_set, step, cfg: gs_adam_map_config, stream: int) -> None:
+    check("gs_sparse_adam", lib().gs_sparse_adam(C.byref(ws), int(sh_degree), C.byref(params), C.byref(grads),
+                                                 C.byref(m), C.byref(v), _ptr(step), C.byref(cfg),
+                                                 C.c_void_p(stream)))
+
+
+def gs_expand_scratch_bytes(n_points: int) -> int:
+    return int(lib().gs_expand_scratch_bytes(int(n_points)))
+
+
+def gs_expand_select(points, n_points: int, cam, cfg: gs_config, opac, height: int, width: int, tau: float, scratch,
+                     idx, count, stream: int) -> None:
+    check("gs_expand_select", lib().gs_expand_select(_ptr(points), int(n_points), _ptr(cam), C.byref(cfg),
+                                                     _ptr(opac), int(height), int(width), float(tau),
+                                                     _ptr(scratch), _ptr(idx), _ptr(count), C.c_void_p(stream)))
+
+
+def gs_expand_init(points, rgb, n_points: int, idx, count, cam, first: int, dst: gs_param_set, n_dst: int,
+                   sh_degree: int, init_opacity: float, stream: int) -> None:
+    check("gs_expand_init", lib().gs_expand_init(_ptr(points), _ptr(rgb), int(n_points), _ptr(idx), _ptr(count),
+                                                 _ptr(cam), int(first), C.byref(dst), int(n_dst), int(sh_degree),
+                                                 float(init_opacity), C.c_void_p(stream)))
 
 
 def gs_render_fwd_noalloc(m: gs_map, cams, frame: gs_frame, cfg: gs_config, rgb, depth, opac, t_final, n_contrib,

@@ -1,6 +1,7 @@
 // C ABI of the rasterizer: argument checks, workspace layout, launches.
 // The operations themselves are defined in the header next to each entry
 // point (arxiv 2507.04004 references there).
+#include <cmath>
 #include <cstring>
 
 #include "gs_internal.h"
@@ -243,6 +244,53 @@ gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const g
                                           reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_param_set* params,
+                         const gs_param_set* grads, const gs_param_set* m, const gs_param_set* v, int32_t* step_dev,
+                         const gs_adam_map_config* cfg, gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if (!params || !grads || !m || !v || !step_dev || !cfg || sh_degree < 0 || sh_degree > 3) return GS_ERR_ARG;
+  for (const gs_param_set* q : {params, grads, m, v}) {
+    if (!q->mean || !q->log_scale || !q->quat || !q->logit_opacity || !q->sh_dc) return GS_ERR_ARG;
+    if (sh_degree > 0 && !q->sh_rest) return GS_ERR_ARG;
+  }
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps > 0.f))
+    return GS_ERR_ARG;
+  return cuda_status(launch_sparse_adam(resolve_ws(ws, L), sh_degree, *params, *grads, *m, *v, step_dev, *cfg,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t gs_expand_scratch_bytes(int64_t n_points) {
+  if (n_points < 1 || n_points >= (int64_t(1) << 31)) return 0;
+  return expand_scratch_bytes(n_points);
+}
+
+gs_status gs_expand_select(const float* points_dev, int64_t n_points, const gs_camera* cam_dev, const gs_config* cfg,
+                           const float* opac_dev, int32_t height, int32_t width, float tau, void* scratch,
+                           int32_t* idx_out, uint32_t* count_out, gs_stream_t stream) {
+  if (!points_dev || !cam_dev || !opac_dev || !scratch || !idx_out || !count_out) return GS_ERR_ARG;
+  if (n_points < 1 || n_points >= (int64_t(1) << 31) || height < 1 || width < 1) return GS_ERR_ARG;
+  gs_status s = check_cfg(cfg);
+  if (s != GS_OK) return s;
+  if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return GS_ERR_ARG;
+  return cuda_status(launch_expand_select(points_dev, n_points, cam_dev, opac_dev, height, width, tau, cfg->near_z,
+                                          scratch, idx_out, count_out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_expand_init(const float* points_dev, const float* rgb_dev, int64_t n_points, const int32_t* idx_dev,
+                         const uint32_t* count_dev, const gs_camera* cam_dev, int64_t first, const gs_param_set* dst,
+                         int64_t n_dst, int32_t sh_degree, float init_opacity, gs_stream_t stream) {
+  if (!points_dev || !rgb_dev || !idx_dev || !count_dev || !cam_dev || !dst) return GS_ERR_ARG;
+  if (n_points < 1 || first < 0 || n_dst < first || sh_degree < 0 || sh_degree > 3) return GS_ERR_ARG;
+  if (!dst->mean || !dst->log_scale || !dst->quat || !dst->logit_opacity || !dst->sh_dc) return GS_ERR_ARG;
+  if (sh_degree > 0 && !dst->sh_rest) return GS_ERR_ARG;
+  if (!(init_opacity > 0.f && init_opacity < 1.f)) return GS_ERR_ARG;
+  const float logit = std::log(init_opacity / (1.f - init_opacity));
+  return cuda_status(launch_expand_init(points_dev, rgb_dev, n_points, idx_dev, count_dev, cam_dev, first, n_dst,
+                                        sh_degree, logit, *dst, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 gs_status gs_pose_apply(const gs_camera* cams0_dev, const float* xi_dev, int32_t n_views, gs_camera* cams_out_dev,
                         gs_stream_t stream) {
   if (!cams0_dev || !xi_dev || !cams_out_dev || n_views < 1) return GS_ERR_ARG;
@@ -294,7 +342,7 @@ const char* gs_kernel_name(int32_t id) {
   static const char* names[kKNumKernels] = {"project",     "scan",           "scatter_rows",  "sort_small",
                                             "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
                                             "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
-                                            "rows_emit",   "ssim_fwd",       "ssim_bwd"};
+                                            "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -11,7 +11,8 @@ namespace gsb {
 // Kernel ids reported by the tracing hook (gs_trace_start).
 enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
-  kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKNumKernels
+  kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
+  kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);
@@ -25,6 +26,16 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_co
                            cudaStream_t st);
 cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st);
 size_t dssim_scratch_bytes(int V, int H, int W);
+cudaError_t launch_sparse_adam(const Ws& ws, int32_t sh_degree, const gs_param_set& p, const gs_param_set& g,
+                               const gs_param_set& m, const gs_param_set& v, int32_t* step,
+                               const gs_adam_map_config& hp, cudaStream_t st);
+size_t expand_scratch_bytes(int64_t P);
+cudaError_t launch_expand_select(const float* pts, int64_t P, const gs_camera* cam, const float* opac, int H, int W,
+                                 float tau, float near, void* scratch, int32_t* out_idx, uint32_t* count,
+                                 cudaStream_t st);
+cudaError_t launch_expand_init(const float* pts, const float* rgb, int64_t P, const int32_t* idx,
+                               const uint32_t* count, const gs_camera* cam, int64_t first, int64_t n_dst,
+                               int32_t sh_degree, float logit_init, const gs_param_set& dst, cudaStream_t st);
 cudaError_t launch_pose_apply(const gs_camera* cams0, const float* xi, int V, gs_camera* cams_out, cudaStream_t st);
 cudaError_t launch_adam_pose(float* xi, float* grad, float* m, float* s, int32_t* step, int V,
                              const gs_adam_config& hp, const float* loss, float* best_loss, float* best_xi,

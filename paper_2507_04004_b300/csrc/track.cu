@@ -106,3 +106,62 @@ cudaError_t launch_adam_pose(float* xi, float* grad, float* m, float* s, int32_t
 }
 
 }  // namespace gsb
+
+namespace gsb {
+
+// Sparse Adam over the map (Sec. "Additional Strategies" (a)): only the
+// Gaussians that take part in the rendering of the last projected batch (the
+// workspace's list of Gaussians seen by some view) are updated; the others
+// keep their parameters and moments.  One thread per listed Gaussian walks its
+// parameter rows; the gradients of the updated Gaussians are cleared, so the
+// gradient buffers are zero again for the next backward pass without a clear
+// of the whole map.
+__global__ void __launch_bounds__(256) k_sparse_adam(Ws ws, int32_t K, gs_param_set p, gs_param_set g,
+                                                     gs_param_set m, gs_param_set v, const int32_t* __restrict__ step,
+                                                     gs_adam_map_config hp) {
+  const uint32_t count = ws.counters[kGaussCount];
+  const int64_t n = ws.n;
+  const float t = (float)(*step + 1);
+  const float c1 = 1.f / (1.f - powf(hp.beta1, t)), c2 = 1.f / (1.f - powf(hp.beta2, t));
+  for (uint64_t li = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; li < count;
+       li += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = ws.gauss_list[li];
+    auto rows = [&](float* P, float* G, float* M, float* S, int nrows, float lr) {
+      for (int r = 0; r < nrows; ++r) {
+        const int64_t e = (int64_t)r * n + gi;
+        const float gr = G[e];
+        const float mi = hp.beta1 * M[e] + (1.f - hp.beta1) * gr;
+        const float si = hp.beta2 * S[e] + (1.f - hp.beta2) * gr * gr;
+        M[e] = mi;
+        S[e] = si;
+        P[e] -= lr * (mi * c1) / (sqrtf(si * c2) + hp.eps);
+        G[e] = 0.f;
+      }
+    };
+    rows(p.mean, g.mean, m.mean, v.mean, 3, hp.lr_mean);
+    rows(p.log_scale, g.log_scale, m.log_scale, v.log_scale, 3, hp.lr_log_scale);
+    rows(p.quat, g.quat, m.quat, v.quat, 4, hp.lr_quat);
+    rows(p.logit_opacity, g.logit_opacity, m.logit_opacity, v.logit_opacity, 1, hp.lr_logit_opacity);
+    rows(p.sh_dc, g.sh_dc, m.sh_dc, v.sh_dc, 3, hp.lr_sh_dc);
+    if (K > 1) rows(p.sh_rest, g.sh_rest, m.sh_rest, v.sh_rest, 3 * (K - 1), hp.lr_sh_rest);
+  }
+}
+
+__global__ void k_step_advance(int32_t* step) { *step += 1; }
+
+cudaError_t launch_sparse_adam(const Ws& ws, int32_t sh_degree, const gs_param_set& p, const gs_param_set& g,
+                               const gs_param_set& m, const gs_param_set& v, int32_t* step,
+                               const gs_adam_map_config& hp, cudaStream_t st) {
+  const int32_t K = (sh_degree + 1) * (sh_degree + 1);
+  const int64_t need = (ws.n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  trace_begin(kKSparseAdam, st);
+  k_sparse_adam<<<(unsigned)(need < cap ? need : cap), 256, 0, st>>>(ws, K, p, g, m, v, step, hp);
+  trace_end(st);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  k_step_advance<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
+}
+
+}  // namespace gsb

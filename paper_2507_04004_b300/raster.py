@@ -11,6 +11,7 @@ Eq. 3dgs_jacobi), Sec. "Fast Tile-based Culling" and Eq. depth_loss.
 from __future__ import annotations
 
 from dataclasses import dataclass
+from types import SimpleNamespace
 
 import numpy as np
 import torch
@@ -284,3 +285,62 @@ class DSSIM:
             raise ValueError("image batch does not match the D-SSIM geometry")
         N.gs_dssim(img, tgt, V, H, W, weight, loss, dl_dimg, self.scratch,
                    torch.cuda.current_stream(img.device).cuda_stream)
+
+
+class SparseAdam:
+    """Sparse Adam on an FP32 map (Sec. "Additional Strategies" (a)) through
+    ``gs_sparse_adam``: after a backward pass, one Adam step on the Gaussians
+    the rasterizer's last projection saw, their gradients cleared.  Learning
+    rates default to those of 3D Gaussian Splatting without decay (the paper's
+    setting); ``spatial_scale`` multiplies the position rate (3DGS scales it by
+    the scene extent)."""
+
+    def __init__(self, gmap: GaussianMap, lr_mean: float = 1.6e-4, lr_log_scale: float = 5e-3,
+                 lr_quat: float = 1e-3, lr_logit_opacity: float = 0.05, lr_sh_dc: float = 2.5e-3,
+                 lr_sh_rest: float = 2.5e-3 / 20, betas=(0.9, 0.999), eps: float = 1e-15,
+                 spatial_scale: float = 1.0):
+        if gmap.sh_bf16:
+            raise ValueError("sparse Adam updates FP32 maps")
+        z = lambda t: torch.zeros_like(t)
+        mk = lambda: SimpleNamespace(mean=z(gmap.mean), log_scale=z(gmap.log_scale), quat=z(gmap.quat),
+                                     logit_opacity=z(gmap.logit_opacity), sh_dc=z(gmap.sh_dc),
+                                     sh_rest=z(gmap.sh_rest))
+        self.m, self.v = mk(), mk()
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=gmap.mean.device)
+        self.cfg = N.gs_adam_map_config(lr_mean * spatial_scale, lr_log_scale, lr_quat, lr_logit_opacity, lr_sh_dc,
+                                        lr_sh_rest, betas[0], betas[1], eps)
+
+    def step(self, gmap: GaussianMap, grads: Grads, rast: Rasterizer) -> None:
+        N.gs_sparse_adam(rast.ws, gmap.sh_degree, N.param_set(gmap), N.param_set(grads), N.param_set(self.m),
+                         N.param_set(self.v), self.step_count, self.cfg, rast._stream())
+
+
+def expand_map(gmap: GaussianMap, points: torch.Tensor, colours: torch.Tensor, cam: torch.Tensor,
+               opac: torch.Tensor, tau: float = 0.99, init_opacity: float = 0.1,
+               config: dict | None = None) -> tuple[GaussianMap, torch.Tensor]:
+    """Map expansion (Sec. "Expansion of Gaussian Map") for one keyframe:
+    points / colours [3][P] (world, RGB in [0, 1]), cam [1][16], opac [H][W]
+    (the keyframe's rendered opacity).  Returns the grown FP32 map (the old
+    Gaussians first) and the indices of the points that became Gaussians."""
+    if gmap.sh_bf16:
+        raise ValueError("map expansion writes FP32 maps")
+    dev = points.device
+    P = int(points.shape[1])
+    H, W = int(opac.shape[0]), int(opac.shape[1])
+    st = torch.cuda.current_stream(dev).cuda_stream
+    nbytes = N.gs_expand_scratch_bytes(P)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    off = (-buf.data_ptr()) % 256
+    idx = torch.empty(P, dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int32, device=dev)
+    N.gs_expand_select(points, P, cam, make_config(**(config or {})), opac, H, W, tau, buf[off:off + nbytes], idx,
+                       count, st)
+    k = int(count.item())
+    n0, n1 = gmap.n, gmap.n + k
+    grow = lambda t: torch.cat([t, torch.empty(*t.shape[:-1], k, dtype=t.dtype, device=dev)], dim=-1).contiguous()
+    out = GaussianMap(grow(gmap.mean), grow(gmap.log_scale), grow(gmap.quat), grow(gmap.logit_opacity),
+                      grow(gmap.sh_dc), grow(gmap.sh_rest), gmap.sh_degree)
+    if k:
+        N.gs_expand_init(points, colours, P, idx, count, cam, n0, N.param_set(out), n1, gmap.sh_degree,
+                         init_opacity, st)
+    return out, idx[:k]
