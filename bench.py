@@ -170,6 +170,7 @@ def source_hash(*names) -> str:
 # Which source file holds each kernel (for matching ncu traffic to source).
 KERNEL_SRC = {"project": "project.cu", "scatter_rows": "project.cu", "rows_count": "project.cu",
               "rows_emit": "project.cu", "scan_buckets": "sort.cu", "scan": "sort.cu", "sort_small": "sort.cu",
+              "sort_medium": "sort.cu",
               "sort_long": "sort.cu", "render_fwd": "render_fwd.cu", "count_depth": "render_bwd.cu",
               "render_bwd": "render_bwd.cu", "preprocess_bwd": "render_bwd.cu", "pose_jacobian": "jacobian.cu"}
 

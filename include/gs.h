@@ -106,7 +106,7 @@ typedef struct {
 /* Byte offsets of the workspace's parts (for inspection and tests). */
 typedef struct {
   size_t counters;    /* uint32[16]: [0] status, [1] pairs (or row items) needed, [2] visible entries,
-                         [3] long tiles, [4] row items, [5] Gaussians in gauss_list */
+                         [3] long tiles, [4] row items, [5] Gaussians in gauss_list, [6] medium tiles */
   size_t records;     /* float4[V*N][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
   size_t rects;       /* uint32[V*N][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
   size_t adjoints;    /* float4[V*N][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */
@@ -115,7 +115,8 @@ typedef struct {
   size_t tile_count;  /* uint32[V*T]: pairs per tile, T = ceil(W/16) * ceil(H/16) */
   size_t tile_start;  /* uint32[V*T]: first pair of each tile in the sorted order */
   size_t tile_cursor; /* uint32[V*T]: fill cursor used while binning */
-  size_t long_tiles;  /* uint32[V*T]: tiles too long for the single-CTA shared-memory sort */
+  size_t long_tiles;  /* uint32[V*T]: tiles for the long-bin sort (from the front) and for the
+                         medium-bin sort (from the back) */
   size_t bucket_count;  /* uint32[V*ceil(H/16)]: row items per (view, tile row) */
   size_t bucket_start;  /* uint32[V*ceil(H/16)] */
   size_t bucket_cursor; /* uint32[V*ceil(H/16)] */

@@ -342,7 +342,8 @@ const char* gs_kernel_name(int32_t id) {
   static const char* names[kKNumKernels] = {"project",     "scan",           "scatter_rows",  "sort_small",
                                             "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
                                             "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
-                                            "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam"};
+                                            "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam",
+                                            "sort_medium"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -33,7 +33,7 @@ struct Ws {
   uint32_t* tile_count;   // [V*T]
   uint32_t* tile_start;   // [V*T]
   uint32_t* tile_cursor;  // [V*T]
-  uint32_t* long_tiles;   // [V*T]
+  uint32_t* long_tiles;   // [V*T] long bins from the front, medium bins from the back
   uint32_t* bucket_count;   // [V*tiles_y] row items per (view, tile row)
   uint32_t* bucket_start;   // [V*tiles_y]
   uint32_t* bucket_cursor;  // [V*tiles_y]
@@ -48,7 +48,9 @@ struct Ws {
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
 
-enum CounterSlot { kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4, kGaussCount = 5 };
+enum CounterSlot {
+  kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4, kGaussCount = 5, kMediumCount = 6
+};
 
 struct Cam {
   float R[9], t[3], fx, fy, cx, cy;

@@ -12,7 +12,7 @@ namespace gsb {
 enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
   kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
-  kKNumKernels
+  kKSortMedium, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);

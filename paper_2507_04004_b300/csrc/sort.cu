@@ -6,8 +6,8 @@
 // the projection, an exclusive scan here, and binning by per-tile cursors in
 // the emit kernel); the remaining 64 bits (depth key bits << 32 | Gaussian
 // index) are unique inside a bin and are sorted per tile in shared memory
-// (bitonic network), with a merge of sorted runs for the rare bins longer
-// than one CTA's shared memory.  The result for each tile is its Gaussians in
+// (by size class: warp bitonic, CTA radix in a small or a medium CTA, bitonic
+// network with a merge of sorted runs for the rare bins longer than that).  The result for each tile is its Gaussians in
 // front-to-back order, as the compositing of Eq. rendered_rgb needs.
 #include "gs_internal.h"
 
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ws ws) {
   if (threadIdx.x == 0) {
     ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     ws.counters[kLongCount] = 0;
+    ws.counters[kMediumCount] = 0;
     if (total > (unsigned long long)ws.cap) ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
   }
 }
@@ -188,40 +189,30 @@ __device__ __forceinline__ void warp_sort_bin(const Ws& ws, uint32_t start, int 
   }
 }
 
-constexpr int kRadixCap = 2048;  // bins sorted by one CTA's radix sort in shared memory
-constexpr int kRadixThreads = 256;
+// CTA radix sort of one bin held in shared memory: stable LSD radix sort on
+// the 32-bit depth key (8-bit digits; a pass whose digit is the same for
+// every key is skipped), each warp ranking its contiguous share with
+// __match_any_sync, then short runs of equal keys ordered by (key, Gaussian
+// index).  NT threads, bins of up to CAP keys.
+template <int NT, int CAP>
+struct RadixSmem {
+  uint32_t key[2][CAP];
+  uint32_t val[2][CAP];
+  uint32_t hist[NT / 32][256];
+  uint32_t tot[256];
+  int skip[8];  // one flag per pass: no thread can still be reading a reset flag
+};
 
-// One CTA per bin.  Bins of up to 64 keys: warp register bitonic on the full
-// 64-bit key.  Up to kRadixCap keys: stable LSD radix sort on the 32-bit depth
-// key (8-bit digits; a pass whose digit is the same for every key is skipped),
-// each warp ranking its contiguous share with __match_any_sync, then short
-// runs of equal keys ordered by (key, Gaussian index).  Longer bins go to the
-// long-bin list.
-__global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
-  constexpr int NW = kRadixThreads / 32;
-  __shared__ uint32_t s_key[2][kRadixCap];
-  __shared__ uint32_t s_val[2][kRadixCap];
-  __shared__ uint32_t s_hist[NW][256];
-  __shared__ uint32_t s_tot[256];
-  __shared__ int s_skip[8];  // one flag per pass: no thread can still be reading a reset flag
-  if (ws.counters[kStatus] != 0) return;
-  const int64_t t = blockIdx.x;
-  const int n = (int)ws.tile_count[t];
-  if (n == 0) return;
-  const uint32_t start = ws.tile_start[t];
+template <int NT, int CAP>
+__device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT, CAP>& sm) {
+  constexpr int NW = NT / 32;
+  auto& s_key = sm.key;
+  auto& s_val = sm.val;
+  auto& s_hist = sm.hist;
+  auto& s_tot = sm.tot;
+  auto& s_skip = sm.skip;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (n > kRadixCap) {
-    if (threadIdx.x == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
-    return;
-  }
-  if (n <= 64) {
-    if (warp == 0) {
-      if (n <= 32) warp_sort_bin<1>(ws, start, n, lane);
-      else warp_sort_bin<2>(ws, start, n, lane);
-    }
-    return;
-  }
-  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const unsigned long long k = ws.keys[start + i];
     s_key[0][i] = (uint32_t)(k >> 32);
     s_val[0][i] = (uint32_t)(k & 0xffffffffull);
@@ -232,22 +223,23 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
   int src = 0, pass = 0;
   // one stable LSD pass on the 8-bit digit at `shift`
   auto radix_pass = [&](int shift) {
-    for (int i = threadIdx.x; i < NW * 256; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < NW * 256; i += NT) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&s_hist[warp][(s_key[src][i] >> shift) & 255u], 1u);
     __syncthreads();
     {
       // digit-major exclusive scan: offsets[w][d] = sum_{d' < d} tot[d'] + sum_{w' < w} hist[w'][d]
-      const int d = threadIdx.x;
-      uint32_t run = 0;
+      for (int d = threadIdx.x; d < 256; d += NT) {
+        uint32_t run = 0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t h = s_hist[w][d];
-        s_hist[w][d] = run;
-        run += h;
+        for (int w = 0; w < NW; ++w) {
+          const uint32_t h = s_hist[w][d];
+          s_hist[w][d] = run;
+          run += h;
+        }
+        s_tot[d] = run;
+        if (run == (uint32_t)n) s_skip[pass] = 1;
       }
-      s_tot[d] = run;
-      if (run == (uint32_t)n) s_skip[pass] = 1;
     }
     __syncthreads();
     if (s_skip[pass]) {  // every key has this digit: the pass keeps the order
@@ -271,9 +263,9 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
         for (int q = 0; q < 8; ++q) { const uint32_t c = v[q]; s_tot[lane * 8 + q] = run; run += c; }
       }
       __syncthreads();
-      const int d = threadIdx.x;
+      for (int d = threadIdx.x; d < 256; d += NT)
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s_hist[w][d] += s_tot[d];
+        for (int w = 0; w < NW; ++w) s_hist[w][d] += s_tot[d];
     }
     __syncthreads();
     const int dst = src ^ 1;
@@ -304,7 +296,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
   radix_pass(24);
   if (threadIdx.x == 0) s_tot[0] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const uint32_t hi = s_key[src][i] >> 16;
     if (i == 0 || (s_key[src][i - 1] >> 16) != hi) {
       int e = i + 1;
@@ -323,7 +315,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
   }
   const uint32_t mask = full ? 0xffffffffu : 0xffff0000u;
   // runs of equal (masked) keys: insertion sort on (key, Gaussian index)
-  for (int i = threadIdx.x; i < n; i += kRadixThreads) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const uint32_t k = s_key[src][i] & mask;
     if ((i == 0 || (s_key[src][i - 1] & mask) != k) && i + 1 < n && (s_key[src][i + 1] & mask) == k) {
       int e = i + 1;
@@ -342,7 +334,54 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_small(Ws ws) {
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kRadixThreads) ws.sorted_ids[start + i] = s_val[src][i];
+  for (int i = threadIdx.x; i < n; i += NT) ws.sorted_ids[start + i] = s_val[src][i];
+}
+
+// Bins are sorted by size class: up to 64 keys by one warp (register bitonic
+// on the full 64-bit key), up to kSmallCap by a kSmallThreads-thread CTA per
+// bin (small shared memory, so many bins share an SM), up to kMediumCap by a
+// persistent kMediumThreads-thread CTA over the medium list (filled from the
+// end of long_tiles), longer ones by k_sort_long.
+constexpr int kSmallThreads = 128, kSmallCap = 1024;
+constexpr int kMediumThreads = 256, kMediumCap = 2048;
+
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(Ws ws) {
+  __shared__ RadixSmem<kSmallThreads, kSmallCap> sm;
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t t = blockIdx.x;
+  const int n = (int)ws.tile_count[t];
+  if (n == 0) return;
+  const uint32_t start = ws.tile_start[t];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (n > kMediumCap) {
+    if (threadIdx.x == 0) ws.long_tiles[atomicAdd(ws.counters + kLongCount, 1u)] = (uint32_t)t;
+    return;
+  }
+  if (n > kSmallCap) {
+    const int64_t ntiles = (int64_t)ws.views * ws.tiles_per_view;
+    if (threadIdx.x == 0) ws.long_tiles[ntiles - 1 - atomicAdd(ws.counters + kMediumCount, 1u)] = (uint32_t)t;
+    return;
+  }
+  if (n <= 64) {
+    if (warp == 0) {
+      if (n <= 32) warp_sort_bin<1>(ws, start, n, lane);
+      else warp_sort_bin<2>(ws, start, n, lane);
+    }
+    return;
+  }
+  cta_radix_bin<kSmallThreads, kSmallCap>(ws, start, n, sm);
+}
+
+__global__ void __launch_bounds__(kMediumThreads) k_sort_medium(Ws ws) {
+  __shared__ RadixSmem<kMediumThreads, kMediumCap> sm;
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t ntiles = (int64_t)ws.views * ws.tiles_per_view;
+  const uint32_t nm = ws.counters[kMediumCount];
+  for (uint32_t li = blockIdx.x; li < nm; li += gridDim.x) {
+    const int64_t t = ws.long_tiles[ntiles - 1 - li];
+    cta_radix_bin<kMediumThreads, kMediumCap>(ws, ws.tile_start[t], (int)ws.tile_count[t], sm);
+    __syncthreads();  // the next bin reuses the buffers and flags
+  }
 }
 
 // Merge-path split: number of elements of A among the first d outputs of
@@ -425,7 +464,11 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   if ((err = launch_rows(ws, 2, st)) != cudaSuccess) return err;
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKSortSmall, st);
-  k_sort_small<<<ntiles, kRadixThreads, 0, st>>>(ws);
+  k_sort_small<<<ntiles, kSmallThreads, 0, st>>>(ws);
+  trace_end(st);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  trace_begin(kKSortMedium, st);
+  k_sort_medium<<<sm_count() * 4, kMediumThreads, 0, st>>>(ws);
   trace_end(st);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;

@@ -18,6 +18,7 @@ namespace {
 constexpr int kT = 32;             // output tile edge
 constexpr int kR = 5;              // window radius
 constexpr int kS = kT + 2 * kR;    // staged edge (42)
+constexpr int kS2 = kS / 2;        // staged row pairs (21)
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -25,18 +26,79 @@ struct Win {
   float w[2 * kR + 1];  // normalised 1D Gaussian; the 2D window is its outer product
 };
 
-// Row pass over the staged block: out[r][c] = sum_k w[k] in[r][c + k] for
-// the kS rows and kT output columns, for NM maps at once.
+// Stage one plane over the tile and its 5-pixel halo (zero outside the
+// image) with rows paired, s[i][c] = (v[2i][c], v[2i + 1][c]), so that the
+// row filter handles two rows per packed FP32x2 instruction.
+__device__ __forceinline__ void stage_pairs(const float* __restrict__ plane, int H, int W, int x0, int y0,
+                                            float2 (*s)[kS]) {
+  for (int i = threadIdx.x; i < kS2 * kS; i += blockDim.x) {
+    const int rp = i / kS, c = i - rp * kS;
+    const int gx = x0 + c, gy = y0 + 2 * rp;
+    const bool cx = gx >= 0 && gx < W;
+    const float a = (cx && gy >= 0 && gy < H) ? plane[(int64_t)gy * W + gx] : 0.f;
+    const float b = (cx && gy + 1 >= 0 && gy + 1 < H) ? plane[(int64_t)(gy + 1) * W + gx] : 0.f;
+    s[rp][c] = make_float2(a, b);
+  }
+}
+
+// Row filter of NM maps formed from the staged planes by map_of (two rows and
+// four output columns per thread: each of the 14 inputs is loaded and its
+// products formed once), into out[m][row][col] for the kS rows and kT columns.
+template <int NM, class F>
+__device__ __forceinline__ void row_filter(const Win& win, F map_of, float (*out)[kS][kT]) {
+  for (int it = threadIdx.x; it < kS2 * (kT / 4); it += blockDim.x) {
+    const int rp = it / (kT / 4), c0 = (it - rp * (kT / 4)) * 4;
+    float2 a[4][NM];
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) a[o][m] = f2(0.f);
+#pragma unroll
+    for (int j = 0; j < 4 + 2 * kR; ++j) {
+      float2 v[NM];
+      map_of(rp, c0 + j, v);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int k = j - o;
+        if (k >= 0 && k <= 2 * kR) {
+          const float2 wk = f2(win.w[k]);
+#pragma unroll
+          for (int m = 0; m < NM; ++m) a[o][m] = fma2(wk, v[m], a[o][m]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        out[m][2 * rp][c0 + o] = a[o][m].x;
+        out[m][2 * rp + 1][c0 + o] = a[o][m].y;
+      }
+  }
+}
+
+// Column filter: thread t covers columns (2 cp, 2 cp + 1) as one packed pair
+// and rows 2 rg, 2 rg + 1 of the tile (cp = t % 16, rg = t / 16).
 template <int NM>
-__device__ __forceinline__ void row_pass(const Win& win, float (*in)[kS][kS], float (*out)[kS][kT]) {
-  for (int i = threadIdx.x; i < kS * kT; i += blockDim.x) {
-    const int r = i / kT, c = i - r * kT;
+__device__ __forceinline__ void col_filter(const Win& win, float (*in)[kS][kT], float2 (*res)[NM]) {
+  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
 #pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      float acc = 0.f;
+  for (int o = 0; o < 2; ++o)
 #pragma unroll
-      for (int k = 0; k <= 2 * kR; ++k) acc = fmaf(win.w[k], in[m][r][c + k], acc);
-      out[m][r][c] = acc;
+    for (int m = 0; m < NM; ++m) res[o][m] = f2(0.f);
+#pragma unroll
+  for (int i = 0; i < 2 + 2 * kR; ++i) {
+    float2 v[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) v[m] = *reinterpret_cast<const float2*>(&in[m][r0 + i][c]);
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const int k = i - o;
+      if (k >= 0 && k <= 2 * kR) {
+        const float2 wk = f2(win.w[k]);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) res[o][m] = fma2(wk, v[m], res[o][m]);
+      }
     }
   }
 }
@@ -46,73 +108,55 @@ __device__ __forceinline__ void row_pass(const Win& win, float (*in)[kS][kS], fl
 // Forward: SSIM at every pixel, the view's loss, and the derivative maps
 //   D1 = dS/dmu_x - 2 mu_x dS/ds_xx - mu_y dS/ds_xy, D2 = dS/ds_xx, D3 = dS/ds_xy
 // (S depends on x through the window sums G*x, G*x^2 and G*(x y)).
-__global__ void __launch_bounds__(256) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
+// 256 threads per 32 x 32 tile.
+__global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
                                                   int H, int W, Win win, float* __restrict__ dmaps,
                                                   float* __restrict__ ssim_sum) {
-  __shared__ float s_in[2][kS][kS];
-  __shared__ float s_h[5][kS][kT];
+  __shared__ float2 s_x[kS2][kS], s_y[kS2][kS];
+  __shared__ __align__(16) float s_h[5][kS][kT];
   __shared__ float s_red[8];
   const int tiles_x = (W + kT - 1) / kT;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int plane = blockIdx.y;  // view * 3 + channel
   const int64_t HW = (int64_t)H * W;
-  const float* x = img + plane * HW;
-  const float* y = tgt + plane * HW;
   const int x0 = tx * kT - kR, y0 = ty * kT - kR;
-  for (int i = threadIdx.x; i < kS * kS; i += blockDim.x) {
-    const int r = i / kS, c = i - r * kS;
-    const int gy = y0 + r, gx = x0 + c;
-    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    s_in[0][r][c] = in ? x[(int64_t)gy * W + gx] : 0.f;
-    s_in[1][r][c] = in ? y[(int64_t)gy * W + gx] : 0.f;
-  }
+  stage_pairs(img + plane * HW, H, W, x0, y0, s_x);
+  stage_pairs(tgt + plane * HW, H, W, x0, y0, s_y);
   __syncthreads();
-  // row pass of x, y, x^2, y^2, x y
-  for (int i = threadIdx.x; i < kS * kT; i += blockDim.x) {
-    const int r = i / kT, c = i - r * kT;
-    float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float xv = s_in[0][r][c + k], yv = s_in[1][r][c + k], w = win.w[k];
-      a[0] = fmaf(w, xv, a[0]);
-      a[1] = fmaf(w, yv, a[1]);
-      a[2] = fmaf(w, xv * xv, a[2]);
-      a[3] = fmaf(w, yv * yv, a[3]);
-      a[4] = fmaf(w, xv * yv, a[4]);
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m) s_h[m][r][c] = a[m];
-  }
+  // window sums of x, y, x^2, y^2, x y
+  row_filter<5>(win, [&](int rp, int c, float2* v) {
+    const float2 xv = s_x[rp][c], yv = s_y[rp][c];
+    v[0] = xv; v[1] = yv; v[2] = mul2(xv, xv); v[3] = mul2(yv, yv); v[4] = mul2(xv, yv);
+  }, s_h);
   __syncthreads();
-  // column pass and the per-pixel SSIM terms
+  float2 m[2][5];
+  col_filter<5>(win, s_h, m);
   float local = 0.f;
-  for (int i = threadIdx.x; i < kT * kT; i += blockDim.x) {
-    const int r = i / kT, c = i - r * kT;
-    const int gy = ty * kT + r, gx = tx * kT + c;
-    if (gy >= H || gx >= W) continue;
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
+  float* d = dmaps + (int64_t)plane * 3 * HW;
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float w = win.w[k];
+  for (int o = 0; o < 2; ++o)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) m[q] = fmaf(w, s_h[q][r + k][c], m[q]);
+    for (int hx = 0; hx < 2; ++hx) {
+      const int gy = ty * kT + r0 + o, gx = tx * kT + c + hx;
+      if (gy >= H || gx >= W) continue;
+      const float mx = hx ? m[o][0].y : m[o][0].x, my = hx ? m[o][1].y : m[o][1].x;
+      const float exx = hx ? m[o][2].y : m[o][2].x, eyy = hx ? m[o][3].y : m[o][3].x;
+      const float exy = hx ? m[o][4].y : m[o][4].x;
+      const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+      const float a1 = 2.f * mx * my + kC1, a2 = 2.f * sxy + kC2;
+      const float b1 = mx * mx + my * my + kC1, b2 = sxx + syy + kC2;
+      const float ib = 1.f / (b1 * b2);
+      const float sv = a1 * a2 * ib;
+      const float ds_dmx = 2.f * my * a2 * ib - sv * 2.f * mx / b1;
+      const float ds_dsxx = -sv / b2;
+      const float ds_dsxy = 2.f * a1 * ib;
+      const int64_t p = (int64_t)gy * W + gx;
+      d[p] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
+      d[HW + p] = ds_dsxx;
+      d[2 * HW + p] = ds_dsxy;
+      local += sv;
     }
-    const float mx = m[0], my = m[1];
-    const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-    const float a1 = 2.f * mx * my + kC1, a2 = 2.f * sxy + kC2;
-    const float b1 = mx * mx + my * my + kC1, b2 = sxx + syy + kC2;
-    const float ib = 1.f / (b1 * b2);
-    const float s = a1 * a2 * ib;
-    const float ds_dmx = 2.f * my * a2 * ib - s * 2.f * mx / b1;
-    const float ds_dsxx = -s / b2;
-    const float ds_dsxy = 2.f * a1 * ib;
-    const int64_t p = (int64_t)gy * W + gx;
-    float* d = dmaps + (int64_t)plane * 3 * HW;
-    d[p] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
-    d[HW + p] = ds_dsxx;
-    d[2 * HW + p] = ds_dsxy;
-    local += s;
-  }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
   __syncthreads();
@@ -129,42 +173,38 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float* __restrict__ img,
 __global__ void __launch_bounds__(256) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
                                                   int H, int W, Win win, const float* __restrict__ dmaps,
                                                   float scale, float* __restrict__ dl_dimg) {
-  __shared__ float s_in[3][kS][kS];
-  __shared__ float s_h[3][kS][kT];
+  __shared__ float2 s_d[3][kS2][kS];
+  __shared__ __align__(16) float s_h[3][kS][kT];
   const int tiles_x = (W + kT - 1) / kT;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int plane = blockIdx.y;
   const int64_t HW = (int64_t)H * W;
   const float* d = dmaps + (int64_t)plane * 3 * HW;
   const int x0 = tx * kT - kR, y0 = ty * kT - kR;
-  for (int i = threadIdx.x; i < kS * kS; i += blockDim.x) {
-    const int r = i / kS, c = i - r * kS;
-    const int gy = y0 + r, gx = x0 + c;
-    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    const int64_t p = (int64_t)gy * W + gx;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) s_in[m][r][c] = in ? d[m * HW + p] : 0.f;
-  }
+  for (int q = 0; q < 3; ++q) stage_pairs(d + q * HW, H, W, x0, y0, s_d[q]);
   __syncthreads();
-  row_pass<3>(win, s_in, s_h);
+  row_filter<3>(win, [&](int rp, int c, float2* v) {
+    v[0] = s_d[0][rp][c]; v[1] = s_d[1][rp][c]; v[2] = s_d[2][rp][c];
+  }, s_h);
   __syncthreads();
+  float2 m[2][3];
+  col_filter<3>(win, s_h, m);
   const float* x = img + plane * HW;
   const float* y = tgt + plane * HW;
   float* out = dl_dimg + plane * HW;
-  for (int i = threadIdx.x; i < kT * kT; i += blockDim.x) {
-    const int r = i / kT, c = i - r * kT;
-    const int gy = ty * kT + r, gx = tx * kT + c;
-    if (gy >= H || gx >= W) continue;
-    float m[3] = {0.f, 0.f, 0.f};
+  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; ++k) {
-      const float w = win.w[k];
+  for (int o = 0; o < 2; ++o)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) m[q] = fmaf(w, s_h[q][r + k][c], m[q]);
+    for (int hx = 0; hx < 2; ++hx) {
+      const int gy = ty * kT + r0 + o, gx = tx * kT + c + hx;
+      if (gy >= H || gx >= W) continue;
+      const int64_t p = (int64_t)gy * W + gx;
+      const float s0 = hx ? m[o][0].y : m[o][0].x, s1 = hx ? m[o][1].y : m[o][1].x;
+      const float s2 = hx ? m[o][2].y : m[o][2].x;
+      out[p] += scale * (s0 + 2.f * x[p] * s1 + y[p] * s2);
     }
-    const int64_t p = (int64_t)gy * W + gx;
-    out[p] += scale * (m[0] + 2.f * x[p] * m[1] + y[p] * m[2]);
-  }
 }
 
 __global__ void k_ssim_loss(const float* __restrict__ ssim_sum, int V, float n, float weight, float* __restrict__ loss) {

@@ -131,10 +131,11 @@ def test_long_tiles_and_merge_path(oracle):
     _check_images(o_r, out, 0, "long tiles")
 
 
-@pytest.mark.parametrize("n,lo,hi", [(900, 65, 768), (2600, 769, 2048)])
+@pytest.mark.parametrize("n,lo,hi", [(900, 65, 1024), (2600, 1025, 2048)])
 def test_bin_size_classes(oracle, n, lo, hi):
-    """Bins sorted by one warp (65..768 keys) and by one CTA (769..2,048
-    keys): tile lists bit-exact against the oracle."""
+    """Bins sorted by a small CTA per bin (65..1,024 keys) and by the
+    persistent medium-bin CTAs (1,025..2,048 keys): tile lists bit-exact
+    against the oracle."""
     rng = np.random.default_rng(6)
     g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
     cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 40.0, 24.0, 20.0, 48, 40)
