@@ -29,7 +29,7 @@
 namespace gsb {
 
 constexpr int kMaxBuckets = 4096;  // buckets counted in shared memory (else global atomics)
-constexpr int kMaxWindow = 8192;   // tiles of one CTA's row window kept in shared memory
+constexpr int kMaxWindow = 2048;   // tiles of one CTA's row window kept in shared memory (two rows of 8K pixels)
 
 template <int DEG, bool BF16>
 __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera* __restrict__ cams, gs_config cfg,
@@ -393,7 +393,7 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_co
 }
 
 cudaError_t launch_rows(const Ws& ws, int phase, cudaStream_t st) {
-  const unsigned grid = (unsigned)(sm_count() * 4);
+  const unsigned grid = (unsigned)(sm_count() * 8);
   if (phase == 0) {
     trace_begin(kKScatterRows, st);
     k_scatter_rows<<<grid, 256, 0, st>>>(ws);
