@@ -80,12 +80,14 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
         const bool k0 = a0 & !s0, k1 = a1 & !s1;
         done[2 * h] |= s0;
         done[2 * h + 1] |= s1;
-        const float2 w = mul2(make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f), T[h]);
+        // alpha of a blended pixel, 0 otherwise: T (1 - 0) = T leaves the others as they are
+        const float2 ak = make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f);
+        const float2 w = mul2(ak, T[h]);
         C0[h] = fma2(cr, w, C0[h]);
         C1[h] = fma2(cg, w, C1[h]);
         C2[h] = fma2(cb, w, C2[h]);
         D[h] = fma2(dep, w, D[h]);
-        T[h] = make_float2(k0 ? Tc.x : T[h].x, k1 ? Tc.y : T[h].y);
+        T[h] = mul2(T[h], fma2(ak, f2(-1.f), f2(1.f)));
         last[2 * h] = k0 ? nxt : last[2 * h];
         last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
         all_done &= done[2 * h] & done[2 * h + 1];
