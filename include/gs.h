@@ -122,6 +122,7 @@ typedef struct {
   size_t bucket_cursor; /* uint32[V*ceil(H/16)] */
   size_t row_items;   /* uint32[cap][2]: (entry v*N + g, bucket), one per (Gaussian, tile row of its box) */
   size_t row_span;    /* uint32[cap]: kept tile columns of each row item */
+  size_t cta_counts;  /* uint32[2048][2 ceil(W/16)]: pairs per tile in each binning CTA's tile-row window */
   size_t keys;        /* uint64[cap]: (depth key bits << 32 | Gaussian index), binned by tile */
   size_t keys_alt;    /* uint64[cap]: merge buffer for very long tiles */
   size_t sorted_ids;  /* uint32[cap]: Gaussian index of each pair, sorted by (tile, depth key, index) */

@@ -49,7 +49,7 @@ class gs_layout(C.Structure):
     _fields_ = [(k, C.c_size_t) for k in ("counters", "records", "rects", "adjoints", "visible", "gauss_list",
                                           "tile_count",
                                           "tile_start", "tile_cursor", "long_tiles", "bucket_count",
-                                          "bucket_start", "bucket_cursor", "row_items", "row_span", "keys",
+                                          "bucket_start", "bucket_cursor", "row_items", "row_span", "cta_counts", "keys",
                                           "keys_alt", "sorted_ids", "view_stats", "total")]
 
 

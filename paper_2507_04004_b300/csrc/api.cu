@@ -41,6 +41,7 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   L->bucket_cursor = take((size_t)B * sizeof(uint32_t));
   L->row_items = take((size_t)cap * sizeof(uint2));
   L->row_span = take((size_t)cap * sizeof(uint32_t));
+  L->cta_counts = take((size_t)kRowsGridMax * 2 * ((f->width + 15) / 16) * sizeof(uint32_t));
   L->keys = take((size_t)cap * sizeof(unsigned long long));
   L->keys_alt = take((size_t)cap * sizeof(unsigned long long));
   L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
@@ -67,6 +68,7 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.bucket_cursor = reinterpret_cast<uint32_t*>(b + L.bucket_cursor);
   ws.row_items = reinterpret_cast<uint2*>(b + L.row_items);
   ws.row_span = reinterpret_cast<uint32_t*>(b + L.row_span);
+  ws.cta_counts = reinterpret_cast<uint32_t*>(b + L.cta_counts);
   ws.keys = reinterpret_cast<unsigned long long*>(b + L.keys);
   ws.keys_alt = reinterpret_cast<unsigned long long*>(b + L.keys_alt);
   ws.sorted_ids = reinterpret_cast<uint32_t*>(b + L.sorted_ids);

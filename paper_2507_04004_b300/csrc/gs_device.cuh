@@ -39,6 +39,7 @@ struct Ws {
   uint32_t* bucket_cursor;  // [V*tiles_y]
   uint2* row_items;         // [cap] (entry v*N + g, bucket v*tiles_y + ty), grouped by bucket
   uint32_t* row_span;       // [cap] packed kept-tile span of each row item
+  uint32_t* cta_counts;     // [kRowsGridMax][2 * tiles_x] pairs per tile of each binning CTA's window
   unsigned long long* keys;      // [cap]
   unsigned long long* keys_alt;  // [cap]
   uint32_t* sorted_ids;   // [cap]
@@ -47,6 +48,10 @@ struct Ws {
   int64_t cap;
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
+
+// Most CTAs the binning kernels launch (their per-CTA tile counts have a
+// workspace slot each).
+constexpr int kRowsGridMax = 2048;
 
 enum CounterSlot {
   kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4, kGaussCount = 5, kMediumCount = 6

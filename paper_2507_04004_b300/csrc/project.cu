@@ -286,8 +286,14 @@ __global__ void __launch_bounds__(256) k_rows_count(Ws ws) {
   }
   if (smem) {
     __syncthreads();
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x)
+    // the window's counts also go to this CTA's slot, where k_rows_emit (same
+    // grid, same item ranges) picks them up instead of counting again
+    const bool keep = nwin <= 2 * tiles_x && blockIdx.x < kRowsGridMax;
+    uint32_t* mine = ws.cta_counts + (size_t)blockIdx.x * 2 * tiles_x;
+    for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
       if (s_cnt[i]) atomicAdd(ws.tile_count + win0 + i, s_cnt[i]);
+      if (keep) mine[i] = s_cnt[i];
+    }
   }
 }
 
@@ -304,7 +310,11 @@ __global__ void __launch_bounds__(256) k_rows_emit(Ws ws) {
   const int nwin = (rr.b_last - rr.b_first + 1) * tiles_x;
   const bool smem = nwin <= kMaxWindow;
   const int64_t n = ws.n;
-  if (smem) {
+  if (smem && nwin <= 2 * tiles_x && blockIdx.x < kRowsGridMax) {
+    // this CTA's window counts, kept by k_rows_count for the same item range
+    const uint32_t* mine = ws.cta_counts + (size_t)blockIdx.x * 2 * tiles_x;
+    for (int i = threadIdx.x; i < nwin; i += blockDim.x) s_cnt[i] = mine[i];
+  } else if (smem) {
     for (int i = threadIdx.x; i < nwin; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     for (uint32_t i = rr.lo + threadIdx.x; i < rr.hi; i += blockDim.x) {
@@ -321,6 +331,8 @@ __global__ void __launch_bounds__(256) k_rows_emit(Ws ws) {
           if (tile_kept(el, tx, ty, ws.width, ws.height)) atomicAdd(s_cnt + (row0 + tx - win0), 1u);
       }
     }
+  }
+  if (smem) {
     __syncthreads();
     // reserve this CTA's range in each tile bin; s_cnt then counts down as the
     // CTA fills it, so an index below zero (never expected: both loops take
@@ -393,7 +405,7 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_co
 }
 
 cudaError_t launch_rows(const Ws& ws, int phase, cudaStream_t st) {
-  const unsigned grid = (unsigned)(sm_count() * 8);
+  const unsigned grid = (unsigned)(sm_count() * 8 < kRowsGridMax ? sm_count() * 8 : kRowsGridMax);
   if (phase == 0) {
     trace_begin(kKScatterRows, st);
     k_scatter_rows<<<grid, 256, 0, st>>>(ws);
