@@ -342,7 +342,7 @@ __device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT,
 // bin (small shared memory, so many bins share an SM), up to kMediumCap by a
 // persistent kMediumThreads-thread CTA over the medium list (filled from the
 // end of long_tiles), longer ones by k_sort_long.
-constexpr int kSmallThreads = 128, kSmallCap = 1024;
+constexpr int kSmallThreads = 128, kSmallCap = 768;
 constexpr int kMediumThreads = 256, kMediumCap = 2048;
 
 __global__ void __launch_bounds__(kSmallThreads) k_sort_small(Ws ws) {

@@ -131,10 +131,10 @@ def test_long_tiles_and_merge_path(oracle):
     _check_images(o_r, out, 0, "long tiles")
 
 
-@pytest.mark.parametrize("n,lo,hi", [(900, 65, 1024), (2600, 1025, 2048)])
+@pytest.mark.parametrize("n,lo,hi", [(900, 65, 768), (2600, 769, 2048)])
 def test_bin_size_classes(oracle, n, lo, hi):
-    """Bins sorted by a small CTA per bin (65..1,024 keys) and by the
-    persistent medium-bin CTAs (1,025..2,048 keys): tile lists bit-exact
+    """Bins sorted by a small CTA per bin (65..768 keys) and by the
+    persistent medium-bin CTAs (769..2,048 keys): tile lists bit-exact
     against the oracle."""
     rng = np.random.default_rng(6)
     g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
