@@ -263,6 +263,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async), their commit and
+// the wait for all of a thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Packed FP32 pairs: the blend kernels evaluate two vertically adjacent
 // pixels per instruction with the sm_100+ f32x2 FMA/ADD/MUL.  Each half is
 // rounded exactly like the scalar __fmaf_rn / __fadd_rn / __fmul_rn, so

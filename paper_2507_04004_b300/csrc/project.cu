@@ -35,6 +35,11 @@ template <int DEG, bool BF16>
 __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera* __restrict__ cams, gs_config cfg,
                                                  Ws ws) {
   __shared__ uint32_t s_bucket[kMaxBuckets];
+  // FP32 SH: each thread's 3K coefficients are copied asynchronously into its
+  // own shared-memory column when it starts a Gaussian, so the DRAM latency
+  // overlaps the first view's projection (dynamic shared memory, 3K x 256 floats)
+  extern __shared__ float s_shc[];
+  constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t n = ws.n;
   const int nb = ws.views * ws.tiles_y;
   const bool smem_buckets = nb <= kMaxBuckets;
@@ -57,6 +62,17 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
       qw = map.quat[g]; qx = map.quat[n + g]; qy = map.quat[2 * n + g]; qz = map.quat[3 * n + g];
       ls[0] = map.log_scale[g]; ls[1] = map.log_scale[n + g]; ls[2] = map.log_scale[2 * n + g];
       logit = map.logit_opacity[g];
+    }
+    if (!BF16) {
+      cp_async_wait_all();  // the previous Gaussian's copies (long done) before the column is refilled
+      if (in_range) {
+        const float* dc = static_cast<const float*>(map.sh_dc);
+        const float* rest = static_cast<const float*>(map.sh_rest);
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q)
+          cp_async4(s_shc + q * blockDim.x + threadIdx.x, q < 3 ? dc + q * n + g : rest + (int64_t)(q - 3) * n + g);
+      }
+      cp_async_commit();
     }
     const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
     const bool g_ok = in_range && qq > 0.f;
@@ -145,12 +161,16 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         dx *= inv; dy *= inv; dz *= inv;
         float Y[16];
         sh_basis<DEG>(dx, dy, dz, Y);
-        constexpr int K = (DEG + 1) * (DEG + 1);
+        if (!BF16) cp_async_wait_all();
   #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           float acc = 0.5f;
   #pragma unroll
-          for (int k = 0; k < K; ++k) acc += sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch) * Y[k];
+          for (int k = 0; k < K; ++k) {
+            const float cf = BF16 ? sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch)
+                                  : s_shc[(k == 0 ? ch : 3 * k + ch) * blockDim.x + threadIdx.x];
+            acc += cf * Y[k];
+          }
           rgb[ch] = fmaxf(acc, 0.f);
         }
       }
@@ -381,8 +401,11 @@ static cudaError_t launch_project_t(const gs_map& map, const gs_camera* cams, co
   const int64_t need = (ws.n + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 6;
   const unsigned grid = (unsigned)(need < cap ? need : cap);
+  const size_t smem = BF16 ? 0 : (size_t)3 * (DEG + 1) * (DEG + 1) * 256 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_project<DEG, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   trace_begin(kKProject, st);
-  k_project<DEG, BF16><<<grid, 256, 0, st>>>(map, cams, cfg, ws);
+  k_project<DEG, BF16><<<grid, 256, smem, st>>>(map, cams, cfg, ws);
   trace_end(st);
   return cudaGetLastError();
 }
