@@ -263,20 +263,20 @@ def run_reference(args):
 
 def run_e2e(args, d, rast, gm, w, px_step):
     """Same metric through the public API from host buffers: every step
-    uploads its keyframes (targets, depth maps, cameras) from pinned memory on
-    a copy stream (double-buffered) and reads the loss back."""
+    uploads its keyframes (8-bit images, LiDAR depth pairs, cameras) from
+    pinned memory on a copy stream (double-buffered), unpacks them there, and
+    reads the loss back."""
     import torch
 
-    from paper_2507_04004_b300.pipeline import MappingStep
+    from paper_2507_04004_b300 import synth
+    from paper_2507_04004_b300.pipeline import HostKeyframes, MappingStep
     from paper_2507_04004_b300.raster import cameras_tensor
-    host_rgb = torch.as_tensor(w.tgt_rgb).pin_memory()
-    host_depth = torch.as_tensor(w.tgt_depth).pin_memory()
-    host_cams = cameras_tensor(w.cams, device="cpu").pin_memory()
+    kf = HostKeyframes.from_dense(synth.to_uint8(w.tgt_rgb), w.tgt_depth, cameras_tensor(w.cams, device="cpu"))
     ms_step = MappingStep(rast, gm, w.w_rgb, w.w_depth)
     e_steps = max(10, min(args.steps, 50))
-    slot = ms_step.upload(host_rgb, host_depth, host_cams)
+    slot = ms_step.upload(kf)
     for _ in range(3):
-        nxt = ms_step.upload(host_rgb, host_depth, host_cams)
+        nxt = ms_step.upload(kf)
         ms_step.step(slot)
         slot = nxt
     torch.cuda.synchronize()
@@ -284,9 +284,9 @@ def run_e2e(args, d, rast, gm, w, px_step):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record()
-    slot = ms_step.upload(host_rgb, host_depth, host_cams)
+    slot = ms_step.upload(kf)
     for i in range(e_steps):
-        nxt = ms_step.upload(host_rgb, host_depth, host_cams) if i + 1 < e_steps else None
+        nxt = ms_step.upload(kf) if i + 1 < e_steps else None
         ms_step.step(slot)
         slot = nxt
     e1.record()

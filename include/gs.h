@@ -266,6 +266,17 @@ gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_par
                          const gs_param_set* grads, const gs_param_set* m, const gs_param_set* v, int32_t* step_dev,
                          const gs_adam_map_config* cfg, gs_stream_t stream);
 
+/* Keyframe unpacking (Sec. "Additional Strategies" (e): keyframes are moved
+ * host -> device asynchronously; moving them compact keeps the copy behind
+ * the kernels): rgb8 [V][3][H][W] 8-bit colour -> rgb [V][3][H][W] = c / 255;
+ * if depth_idx is given, depth [V][H][W] is cleared and, for view v, the
+ * entries depth_offsets[v] .. depth_offsets[v + 1] - 1 of (depth_idx = pixel
+ * y W + x, depth_val) are written (indices outside the image are skipped).
+ * All pointers device; depth_* may be NULL (colour only). */
+gs_status gs_unpack_keyframes(const uint8_t* rgb8_dev, int32_t n_views, int32_t height, int32_t width,
+                              float* rgb_dev, const int32_t* depth_idx_dev, const float* depth_val_dev,
+                              const int32_t* depth_offsets_dev, float* depth_dev, gs_stream_t stream);
+
 /* Map expansion (Sec. "Expansion of Gaussian Map"): from the opacity map O
  * of a new keyframe (gs_render_fwd's opac, [H][W] of one view), the mask
  * O < tau (the paper: 0.99) marks newly observed regions, and only the points

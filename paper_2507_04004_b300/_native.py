@@ -15,7 +15,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
-            "gs_dssim", "gs_pose_apply", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
+            "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
@@ -101,6 +101,7 @@ def lib():
         L.gs_dssim_scratch_bytes.restype = C.c_size_t
         L.gs_dssim.argtypes = [P, P, I32, I32, I32, F, P, P, P, P]
         L.gs_pose_apply.argtypes = [P, P, I32, P, P]
+        L.gs_unpack_keyframes.argtypes = [P, I32, I32, I32, P, P, P, P, P, P]
         L.gs_expand_scratch_bytes.argtypes = [I64]
         L.gs_expand_scratch_bytes.restype = C.c_size_t
         L.gs_expand_select.argtypes = [P, I64, P, C.POINTER(gs_config), P, I32, I32, F, P, P, P, P]
@@ -119,7 +120,7 @@ def lib():
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose",
-                     "gs_sparse_adam", "gs_expand_select", "gs_expand_init"):
+                     "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes"):
             getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -216,6 +217,13 @@ def gs_sparse_adam(ws: gs_workspace, sh_degree: int, params: gs_param_set, grads
     check("gs_sparse_adam", lib().gs_sparse_adam(C.byref(ws), int(sh_degree), C.byref(params), C.byref(grads),
                                                  C.byref(m), C.byref(v), _ptr(step), C.byref(cfg),
                                                  C.c_void_p(stream)))
+
+
+def gs_unpack_keyframes(rgb8, n_views: int, height: int, width: int, rgb, depth_idx, depth_val, depth_offsets, depth,
+                        stream: int) -> None:
+    check("gs_unpack_keyframes", lib().gs_unpack_keyframes(_ptr(rgb8), int(n_views), int(height), int(width),
+                                                           _ptr(rgb), _ptr(depth_idx), _ptr(depth_val),
+                                                           _ptr(depth_offsets), _ptr(depth), C.c_void_p(stream)))
 
 
 def gs_expand_scratch_bytes(n_points: int) -> int:

@@ -263,6 +263,15 @@ gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_par
                                         reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_unpack_keyframes(const uint8_t* rgb8_dev, int32_t n_views, int32_t height, int32_t width,
+                              float* rgb_dev, const int32_t* depth_idx_dev, const float* depth_val_dev,
+                              const int32_t* depth_offsets_dev, float* depth_dev, gs_stream_t stream) {
+  if (!rgb8_dev || !rgb_dev || n_views < 1 || height < 1 || width < 1) return GS_ERR_ARG;
+  if (depth_idx_dev && (!depth_val_dev || !depth_offsets_dev || !depth_dev)) return GS_ERR_ARG;
+  return cuda_status(launch_unpack_keyframes(rgb8_dev, n_views, height, width, rgb_dev, depth_idx_dev, depth_val_dev,
+                                             depth_offsets_dev, depth_dev, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 size_t gs_expand_scratch_bytes(int64_t n_points) {
   if (n_points < 1 || n_points >= (int64_t(1) << 31)) return 0;
   return expand_scratch_bytes(n_points);

@@ -29,6 +29,8 @@ size_t dssim_scratch_bytes(int V, int H, int W);
 cudaError_t launch_sparse_adam(const Ws& ws, int32_t sh_degree, const gs_param_set& p, const gs_param_set& g,
                                const gs_param_set& m, const gs_param_set& v, int32_t* step,
                                const gs_adam_map_config& hp, cudaStream_t st);
+cudaError_t launch_unpack_keyframes(const uint8_t* rgb8, int V, int H, int W, float* rgb, const int32_t* idx,
+                                    const float* val, const int32_t* offsets, float* depth, cudaStream_t st);
 size_t expand_scratch_bytes(int64_t P);
 cudaError_t launch_expand_select(const float* pts, int64_t P, const gs_camera* cam, const float* opac, int H, int W,
                                  float tau, float near, void* scratch, int32_t* out_idx, uint32_t* count,

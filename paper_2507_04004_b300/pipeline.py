@@ -3,15 +3,66 @@
 arxiv 2507.04004, Sec. "Additional Strategies" (e): keyframe images and sparse
 depth maps live in pinned host memory and are moved with asynchronous copies
 on their own stream, so the upload of the next batch overlaps the kernels of
-the current one.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the
-rasterizer (projection, binning/sort, compositing, fused loss backward) over
-a batch of keyframes and returns the per-view loss as a pinned host tensor.
+the current one.  A keyframe travels in the form a sensor delivers it: the
+camera image as 8-bit RGB, the LiDAR depth map as its valid pixels only
+((pixel index, depth) pairs, a few percent of the image); ``gs_unpack_keyframes``
+expands both on the device, on the copy stream, into the FP32 planes the loss
+reads.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
+(projection, binning/sort, compositing, fused loss backward) over a batch of
+keyframes and returns the per-view loss as a pinned host tensor.
 """
 from __future__ import annotations
 
+from dataclasses import dataclass
+
+import numpy as np
 import torch
 
+from . import _native as N
 from .raster import GaussianMap, Grads, Rasterizer, RenderOut
+
+
+def pack_sparse_depth(depth: np.ndarray):
+    """Dense depth maps [V][H][W] (0 = no depth) -> (idx [M] int32 pixel
+    y W + x, val [M] float32, offsets [V + 1] int32), view by view in pixel
+    order."""
+    V = depth.shape[0]
+    flat = np.asarray(depth, np.float32).reshape(V, -1)
+    idx, val, offs = [], [], [0]
+    for v in range(V):
+        nz = np.flatnonzero(flat[v] > 0)
+        idx.append(nz.astype(np.int32))
+        val.append(flat[v, nz])
+        offs.append(offs[-1] + nz.size)
+    return np.concatenate(idx), np.concatenate(val), np.asarray(offs, np.int32)
+
+
+@dataclass
+class HostKeyframes:
+    """One batch of V keyframes in pinned host memory.
+
+    rgb8 [V][3][H][W] uint8; depth_idx [M] int32 (pixel y W + x within its
+    view) and depth_val [M] float32, the valid LiDAR depths of view v being
+    entries depth_offsets[v] .. depth_offsets[v + 1] - 1 (depth_offsets
+    [V + 1] int32); cams [V][16] float32 (the rasterizer's camera records)."""
+    rgb8: torch.Tensor
+    depth_idx: torch.Tensor
+    depth_val: torch.Tensor
+    depth_offsets: torch.Tensor
+    cams: torch.Tensor
+
+    @staticmethod
+    def from_dense(rgb8: np.ndarray, depth: np.ndarray, cams: torch.Tensor, pin: bool = True) -> "HostKeyframes":
+        """Packs an 8-bit image batch and dense depth maps (0 = no depth)."""
+        idx, val, offs = pack_sparse_depth(depth)
+        host = lambda t: t.pin_memory() if pin else t
+        arr = lambda a: host(torch.as_tensor(np.ascontiguousarray(a)))
+        return HostKeyframes(arr(np.asarray(rgb8, np.uint8)), arr(idx), arr(val), arr(offs),
+                             host(cams.to("cpu", torch.float32).contiguous()))
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size()
+                   for t in (self.rgb8, self.depth_idx, self.depth_val, self.depth_offsets, self.cams))
 
 
 class MappingStep:
@@ -24,7 +75,12 @@ class MappingStep:
         self.copy_stream = torch.cuda.Stream(device=dev)
         self.slots = []
         for _ in range(2):
+            # the pair buffers hold a full image per view, so any depth map fits
             self.slots.append(dict(
+                rgb8=torch.empty(V, 3, H, W, dtype=torch.uint8, device=dev),
+                idx=torch.empty(V * H * W, dtype=torch.int32, device=dev),
+                val=torch.empty(V * H * W, dtype=torch.float32, device=dev),
+                offsets=torch.empty(V + 1, dtype=torch.int32, device=dev),
                 rgb=torch.empty(V, 3, H, W, device=dev), depth=torch.empty(V, H, W, device=dev),
                 cams=torch.empty(V, 16, device=dev), ready=torch.cuda.Event(), free=torch.cuda.Event()))
         f = dict(device=dev, dtype=torch.float32)
@@ -32,20 +88,32 @@ class MappingStep:
                              torch.empty(V, H, W, **f), torch.empty(V, H, W, dtype=torch.int32, device=dev))
         self.grads: Grads = rast.new_grads(gmap)
         self.loss_host = torch.empty(V, dtype=torch.float32, pin_memory=True)
-        self.h2d_bytes = (V * 3 * H * W + V * H * W + V * 16) * 4
+        self.h2d_bytes = 0  # bytes of the last upload
         self.d2h_bytes = V * 4
         self._next = 0
 
-    def upload(self, host_rgb: torch.Tensor, host_depth: torch.Tensor, host_cams: torch.Tensor) -> dict:
-        """Queue the copy of one batch (pinned host tensors) on the copy stream."""
+    def upload(self, kf: HostKeyframes) -> dict:
+        """Queue the copy of one batch (pinned host tensors, kept alive by the
+        caller until the batch's step has run) and its unpacking on the copy
+        stream."""
+        V, H, W = self.rast.views, self.rast.height, self.rast.width
+        m = kf.depth_idx.numel()
+        if tuple(kf.rgb8.shape) != (V, 3, H, W) or kf.depth_offsets.numel() != V + 1 or m > V * H * W:
+            raise ValueError("keyframe batch does not match the rasterizer's views and image size")
         slot = self.slots[self._next]
         self._next ^= 1
-        with torch.cuda.stream(self.copy_stream):
-            self.copy_stream.wait_event(slot["free"])
-            slot["rgb"].copy_(host_rgb, non_blocking=True)
-            slot["depth"].copy_(host_depth, non_blocking=True)
-            slot["cams"].copy_(host_cams, non_blocking=True)
-            slot["ready"].record(self.copy_stream)
+        cs = self.copy_stream
+        with torch.cuda.stream(cs):
+            cs.wait_event(slot["free"])
+            slot["rgb8"].copy_(kf.rgb8, non_blocking=True)
+            slot["idx"][:m].copy_(kf.depth_idx, non_blocking=True)
+            slot["val"][:m].copy_(kf.depth_val, non_blocking=True)
+            slot["offsets"].copy_(kf.depth_offsets, non_blocking=True)
+            slot["cams"].copy_(kf.cams, non_blocking=True)
+            N.gs_unpack_keyframes(slot["rgb8"], V, H, W, slot["rgb"], slot["idx"], slot["val"], slot["offsets"],
+                                  slot["depth"], cs.cuda_stream)
+            slot["ready"].record(cs)
+        self.h2d_bytes = kf.nbytes()
         return slot
 
     def step(self, slot: dict) -> torch.Tensor:

@@ -126,6 +126,19 @@ def smooth_target(rng, height, width, n_waves=6, noise=0.1) -> np.ndarray:
     return np.clip(out, 0.0, 1.0).astype(np.float32)
 
 
+def quantize_8bit(img) -> np.ndarray:
+    """The image as an 8-bit camera delivers it, in float32: round(255 c) / 255
+    (an IEEE float32 division, the value the device's unpacking of the byte
+    gives)."""
+    k = np.round(np.clip(img, 0.0, 1.0) * 255.0).astype(np.float32)
+    return (k / np.float32(255.0)).astype(np.float32)
+
+
+def to_uint8(img) -> np.ndarray:
+    """Bytes of an image whose values are multiples of 1/255."""
+    return np.round(np.asarray(img, np.float64) * 255.0).astype(np.uint8)
+
+
 def lidar_depth(cam, centre_world, Rcw, box_lo, box_hi, n_rings=32, n_az=1800, elev_deg=15.0,
                 track_step=0.1, target_frac=0.03, max_scans=10) -> tuple[np.ndarray, float]:
     """Sparse depth map [H][W] (0 = none) from a spinning LiDAR at the camera.
@@ -208,7 +221,7 @@ def mapping(seed=SEED_BASE + 2, n=500_000, width=1280, height=720, focal=700.0, 
             yaws=None, sh_bf16=False, degenerate_frac=0.0, w_rgb=0.8, w_depth=0.2) -> Workload:
     """Map in a 60x20x60 m box around a straight keyframe track along +z
     (0.5 m spacing); each view carries a LiDAR sparse depth map and a smooth
-    random target image."""
+    random target image (8-bit, as a camera delivers it)."""
     rng = np.random.default_rng(seed)
     lo, hi = (-30.0, -10.0, -30.0), (30.0, 10.0, 30.0)
     g = random_map(rng, n, lo, hi, sh_degree, degenerate_frac=degenerate_frac)
@@ -223,7 +236,7 @@ def mapping(seed=SEED_BASE + 2, n=500_000, width=1280, height=720, focal=700.0, 
         cams.append(cam)
         depths.append(d)
         fracs.append(f)
-        tgts.append(smooth_target(rng, height, width))
+        tgts.append(quantize_8bit(smooth_target(rng, height, width)))
     return Workload("mapping", g, cams, np.stack(tgts), np.stack(depths), w_rgb, w_depth, sh_bf16,
                     meta=dict(depth_frac=fracs, box=(lo, hi)))
 
