@@ -85,121 +85,160 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
     const float o = 1.f / (1.f + expf(-logit));
     const float q_thr = 2.f * logf(o / cfg.alpha_min);
     bool seen = false;  // a non-empty box in some view
-    for (int v = 0; v < ws.views; ++v) {
-      const int64_t e = (int64_t)v * n + g;
-      const Cam cam = load_cam(cams, v);
-      const float3 mh = to_camera(cam, mw[0], mw[1], mw[2]);
-      bool ok = g_ok && (mh.z > cfg.near_z);
-      // Warp-level early stop: every lane of the warp is cut by the near plane.
-      if (!__any_sync(kFull, ok)) {
-        if (in_range) ws.rects[e] = empty_rect();
-        continue;
-      }
-      const float z = ok ? mh.z : 1.f;
-      const float iz = 1.f / z;
-      const float mx = __fmaf_rn(cam.fx * mh.x, iz, cam.cx);
-      const float my = __fmaf_rn(cam.fy * mh.y, iz, cam.cy);
-      // affine Jacobian of the projection with x/z, y/z clamped
-      const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
-      const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
-      const float txc = fminf(limx, fmaxf(-limx, mh.x * iz));
-      const float tyc = fminf(limy, fmaxf(-limy, mh.y * iz));
-      const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz;
-      const float j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
-      float m0[3], m1[3];
-  #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
-        m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
-      }
-      // U = S R_g^T m0, V = S R_g^T m1; Sigma' = [[U.U, U.V], [U.V, V.V]] + dil I
-      float U[3], Vv[3];
-  #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float s = sc[k];
-        U[k] = s * (Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2]);
-        Vv[k] = s * (Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2]);
-      }
-      const float uu = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
-      const float vv = Vv[0] * Vv[0] + Vv[1] * Vv[1] + Vv[2] * Vv[2];
-      const float uv = U[0] * Vv[0] + U[1] * Vv[1] + U[2] * Vv[2];
-      const float dil = cfg.dilation;
-      const float A = uu + dil, B = uv, C = vv + dil;
-      // det Sigma' = |U x V|^2 + dil (|U|^2 + |V|^2) + dil^2 (no cancellation)
-      const float cx0 = U[1] * Vv[2] - U[2] * Vv[1], cx1 = U[2] * Vv[0] - U[0] * Vv[2],
-                  cx2 = U[0] * Vv[1] - U[1] * Vv[0];
-      const float det = cx0 * cx0 + cx1 * cx1 + cx2 * cx2 + dil * (uu + vv) + dil * dil;
-      ok = ok && det > 0.f;
-      const float idet = ok ? 1.f / det : 0.f;
-      const float ca = C * idet, cb = -B * idet, cc = A * idet;
-      ok = ok && q_thr > 0.f && ca > 0.f && cc > 0.f;
-
-      // Tile box from the axis-aligned extent of the ellipse q <= q_thr
-      // (|dx| <= sqrt(q_thr Sigma'_xx), |dy| <= sqrt(q_thr Sigma'_yy)), one pixel of slack.
-      int tx0 = 1, ty0 = 0, tx1 = 0, ty1 = 0;
-      if (ok) {
-        const float hx = sqrtf(q_thr * A), hy = sqrtf(q_thr * C);
-        const float Wf = (float)(ws.width - 1), Hf = (float)(ws.height - 1);
-        const float px0 = floorf(mx - hx - 0.5f) - 1.f, px1 = ceilf(mx + hx - 0.5f) + 1.f;
-        const float py0 = floorf(my - hy - 0.5f) - 1.f, py1 = ceilf(my + hy - 0.5f) + 1.f;
-        if (px1 < 0.f || py1 < 0.f || px0 > Wf || py0 > Hf || !(px0 <= px1) || !(py0 <= py1)) {
-          ok = false;
-        } else {
-          tx0 = (int)fmaxf(px0, 0.f) >> 4;
-          tx1 = (int)fminf(px1, Wf) >> 4;
-          ty0 = (int)fmaxf(py0, 0.f) >> 4;
-          ty1 = (int)fminf(py1, Hf) >> 4;
+    // Views are taken 32 at a time.  A cheap pass marks each lane's candidate
+    // views: in front of the near plane and not provably off-screen.  The
+    // screen half-width of the box is sqrt(q_thr Sigma'_xx) with Sigma'_xx <=
+    // s_max^2 |m0|^2 + dilation and |m0| <= |j00| |r0| + |j02| |r2| (r the
+    // camera's rows); the bound below adds a relative and a one-pixel margin
+    // for rounding, so it only drops views that the exact test drops.  The
+    // full projection then runs over each lane's candidates only, so that
+    // lanes are not left idle when a Gaussian is outside most views.
+    const float s2max = fmaxf(sc[0], fmaxf(sc[1], sc[2])) * fmaxf(sc[0], fmaxf(sc[1], sc[2]));
+    const float Wf = (float)(ws.width - 1), Hf = (float)(ws.height - 1);
+    for (int v0 = 0; v0 < ws.views; v0 += 32) {
+      const int nv = min(32, ws.views - v0);
+      uint32_t cand = 0;
+      for (int j = 0; j < nv; ++j) {
+        const int v = v0 + j;
+        const Cam cam = load_cam(cams, v);
+        const float3 mh = to_camera(cam, mw[0], mw[1], mw[2]);
+        bool c = g_ok && q_thr > 0.f && mh.z > cfg.near_z;
+        if (c) {
+          const float iz = 1.f / mh.z;
+          const float mx = __fmaf_rn(cam.fx * mh.x, iz, cam.cx);
+          const float my = __fmaf_rn(cam.fy * mh.y, iz, cam.cy);
+          const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
+          const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
+          const float txc = fminf(limx, fmaxf(-limx, mh.x * iz));
+          const float tyc = fminf(limy, fmaxf(-limy, mh.y * iz));
+          const float n0 = sqrtf(cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2]);
+          const float n1 = sqrtf(cam.R[3] * cam.R[3] + cam.R[4] * cam.R[4] + cam.R[5] * cam.R[5]);
+          const float n2 = sqrtf(cam.R[6] * cam.R[6] + cam.R[7] * cam.R[7] + cam.R[8] * cam.R[8]);
+          const float a0 = fabsf(cam.fx * iz) * n0 + fabsf(cam.fx * txc * iz) * n2;
+          const float a1 = fabsf(cam.fy * iz) * n1 + fabsf(cam.fy * tyc * iz) * n2;
+          const float hxb = 1.001f * sqrtf(q_thr * (1.001f * s2max * a0 * a0 + cfg.dilation)) + 1.f;
+          const float hyb = 1.001f * sqrtf(q_thr * (1.001f * s2max * a1 * a1 + cfg.dilation)) + 1.f;
+          if (mx - hxb - 1.5f > Wf + 1.f || mx + hxb + 0.5f < -1.f || my - hyb - 1.5f > Hf + 1.f ||
+              my + hyb + 0.5f < -1.f)
+            c = false;
         }
+        if (c) cand |= 1u << j;
+        else if (in_range) ws.rects[(int64_t)v * n + g] = empty_rect();
       }
+      // warp-uniform loop (the list append below takes a ballot of all lanes)
+      while (__any_sync(kFull, cand != 0)) {
+        const bool act = cand != 0;
+        const int v = act ? v0 + __ffs(cand) - 1 : v0;
+        cand &= cand - 1;
+        const int64_t e = (int64_t)v * n + g;
+        const Cam cam = load_cam(cams, v);
+        const float3 mh = to_camera(cam, mw[0], mw[1], mw[2]);
+        bool ok = act && g_ok && (mh.z > cfg.near_z);
+        const float z = ok ? mh.z : 1.f;
+        const float iz = 1.f / z;
+        const float mx = __fmaf_rn(cam.fx * mh.x, iz, cam.cx);
+        const float my = __fmaf_rn(cam.fy * mh.y, iz, cam.cy);
+        // affine Jacobian of the projection with x/z, y/z clamped
+        const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
+        const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
+        const float txc = fminf(limx, fmaxf(-limx, mh.x * iz));
+        const float tyc = fminf(limy, fmaxf(-limy, mh.y * iz));
+        const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz;
+        const float j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
+        float m0[3], m1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
+          m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
+        }
+        // U = S R_g^T m0, V = S R_g^T m1; Sigma' = [[U.U, U.V], [U.V, V.V]] + dil I
+        float U[3], Vv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float s = sc[k];
+          U[k] = s * (Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2]);
+          Vv[k] = s * (Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2]);
+        }
+        const float uu = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+        const float vv = Vv[0] * Vv[0] + Vv[1] * Vv[1] + Vv[2] * Vv[2];
+        const float uv = U[0] * Vv[0] + U[1] * Vv[1] + U[2] * Vv[2];
+        const float dil = cfg.dilation;
+        const float A = uu + dil, B = uv, C = vv + dil;
+        // det Sigma' = |U x V|^2 + dil (|U|^2 + |V|^2) + dil^2 (no cancellation)
+        const float cx0 = U[1] * Vv[2] - U[2] * Vv[1], cx1 = U[2] * Vv[0] - U[0] * Vv[2],
+                    cx2 = U[0] * Vv[1] - U[1] * Vv[0];
+        const float det = cx0 * cx0 + cx1 * cx1 + cx2 * cx2 + dil * (uu + vv) + dil * dil;
+        ok = ok && det > 0.f;
+        const float idet = ok ? 1.f / det : 0.f;
+        const float ca = C * idet, cb = -B * idet, cc = A * idet;
+        ok = ok && q_thr > 0.f && ca > 0.f && cc > 0.f;
 
-      // View-dependent colour: dir = (mu - c_w) / |mu - c_w|.
-      float rgb[3] = {0.f, 0.f, 0.f};
-      if (ok) {
-        const float3 cw = camera_centre(cam);
-        float dx = mw[0] - cw.x, dy = mw[1] - cw.y, dz = mw[2] - cw.z;
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
-        float Y[16];
-        sh_basis<DEG>(dx, dy, dz, Y);
-        if (!BF16) cp_async_wait_all();
-  #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          float acc = 0.5f;
-  #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float cf = BF16 ? sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch)
-                                  : s_shc[(k == 0 ? ch : 3 * k + ch) * blockDim.x + threadIdx.x];
-            acc += cf * Y[k];
+        // Tile box from the axis-aligned extent of the ellipse q <= q_thr
+        // (|dx| <= sqrt(q_thr Sigma'_xx), |dy| <= sqrt(q_thr Sigma'_yy)), one pixel of slack.
+        int tx0 = 1, ty0 = 0, tx1 = 0, ty1 = 0;
+        if (ok) {
+          const float hx = sqrtf(q_thr * A), hy = sqrtf(q_thr * C);
+          const float px0 = floorf(mx - hx - 0.5f) - 1.f, px1 = ceilf(mx + hx - 0.5f) + 1.f;
+          const float py0 = floorf(my - hy - 0.5f) - 1.f, py1 = ceilf(my + hy - 0.5f) + 1.f;
+          if (px1 < 0.f || py1 < 0.f || px0 > Wf || py0 > Hf || !(px0 <= px1) || !(py0 <= py1)) {
+            ok = false;
+          } else {
+            tx0 = (int)fmaxf(px0, 0.f) >> 4;
+            tx1 = (int)fminf(px1, Wf) >> 4;
+            ty0 = (int)fmaxf(py0, 0.f) >> 4;
+            ty1 = (int)fminf(py1, Hf) >> 4;
           }
-          rgb[ch] = fmaxf(acc, 0.f);
         }
-      }
 
-      // Single exit: record, cleared adjoint slot, tile box, row-item counts.
-      if (ok) {
-        float4* rec = ws.records + 3 * e;
-        rec[0] = make_float4(mx, my, ca, cb);
-        rec[1] = make_float4(cc, o, mh.z, q_thr);
-        rec[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
-        float4* adj = ws.adjoints + 3 * e;
-        adj[0] = adj[1] = adj[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int b0 = v * ws.tiles_y;
-        for (int ty = ty0; ty <= ty1; ++ty) {
-          if (smem_buckets) atomicAdd(s_bucket + b0 + ty, 1u);
-          else atomicAdd(ws.bucket_count + b0 + ty, 1u);
+        // View-dependent colour: dir = (mu - c_w) / |mu - c_w|.
+        float rgb[3] = {0.f, 0.f, 0.f};
+        if (ok) {
+          const float3 cw = camera_centre(cam);
+          float dx = mw[0] - cw.x, dy = mw[1] - cw.y, dz = mw[2] - cw.z;
+          const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+          dx *= inv; dy *= inv; dz *= inv;
+          float Y[16];
+          sh_basis<DEG>(dx, dy, dz, Y);
+          if (!BF16) cp_async_wait_all();
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const float cf = BF16 ? sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch)
+                                    : s_shc[(k == 0 ? ch : 3 * k + ch) * blockDim.x + threadIdx.x];
+              acc += cf * Y[k];
+            }
+            rgb[ch] = fmaxf(acc, 0.f);
+          }
         }
+
+        // Single exit: record, cleared adjoint slot, tile box, row-item counts.
+        if (ok) {
+          float4* rec = ws.records + 3 * e;
+          rec[0] = make_float4(mx, my, ca, cb);
+          rec[1] = make_float4(cc, o, mh.z, q_thr);
+          rec[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+          float4* adj = ws.adjoints + 3 * e;
+          adj[0] = adj[1] = adj[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const int b0 = v * ws.tiles_y;
+          for (int ty = ty0; ty <= ty1; ++ty) {
+            if (smem_buckets) atomicAdd(s_bucket + b0 + ty, 1u);
+            else atomicAdd(ws.bucket_count + b0 + ty, 1u);
+          }
+        }
+        if (act) ws.rects[e] = ok ? pack_rect(tx0, ty0, tx1, ty1) : empty_rect();
+        // Append visible entries to the compact list, one atomic per warp.
+        const unsigned vis = __ballot_sync(kFull, ok);
+        if (vis) {
+          const int leader = __ffs(vis) - 1;
+          uint32_t slot = 0;
+          if (lane == leader) slot = atomicAdd(ws.counters + kVisibleCount, (uint32_t)__popc(vis));
+          slot = __shfl_sync(kFull, slot, leader);
+          if (ok) ws.visible[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
+        }
+        seen |= ok;
       }
-      if (in_range) ws.rects[e] = ok ? pack_rect(tx0, ty0, tx1, ty1) : empty_rect();
-      // Append visible entries to the compact list, one atomic per warp.
-      const unsigned vis = __ballot_sync(kFull, ok);
-      if (vis) {
-        const int leader = __ffs(vis) - 1;
-        uint32_t slot = 0;
-        if (lane == leader) slot = atomicAdd(ws.counters + kVisibleCount, (uint32_t)__popc(vis));
-        slot = __shfl_sync(kFull, slot, leader);
-        if (ok) ws.visible[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
-      }
-      seen |= ok;
     }
     // Gaussians seen by some view, for the backward projection pass (one
     // atomic per warp; a warp's Gaussians stay consecutive in the list)

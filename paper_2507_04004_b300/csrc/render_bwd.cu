@@ -313,10 +313,11 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
 // Chain of the 2D adjoints through the projection, per Gaussian over all
 // views; parameter gradients are added once per Gaussian (no atomics), pose
 // partials are reduced per view across the CTA.
+constexpr int kPoseSmemViews = 256;  // per-CTA pose sums in shared memory up to this many views
+
 template <int DEG, bool BF16>
 __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_camera* __restrict__ cams,
                                                         gs_config cfg, Ws ws, BwdArgs a) {
-  __shared__ float s_pose[8][6];
   constexpr int K = (DEG + 1) * (DEG + 1);
   // SH gradient accumulators and the Gaussian's SH coefficients live in
   // shared memory (one column per thread): coefficients are fetched once, with
@@ -325,8 +326,10 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   extern __shared__ float s_dyn[];
   float(*s_gsh)[256] = reinterpret_cast<float(*)[256]>(s_dyn);
   float(*s_sh)[256] = reinterpret_cast<float(*)[256]>(s_dyn + 3 * K * 256);
+  // per-view pose sums of the CTA (6 V floats after the SH columns), added to
+  // the global pose gradient once per CTA; with more views, global atomics
+  float* s_pose = s_dyn + 2 * 3 * K * 256;
   const int64_t n = ws.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (ws.counters[kStatus] != 0) return;
   // one thread per Gaussian of the list of those seen by some view, so that
   // warps are full although most of the map is outside every view
@@ -338,6 +341,11 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   const bool in_range = any;
   const bool want_pose = a.grad_pose != nullptr;
   if (!want_pose && !__any_sync(kFull, any)) return;
+  const bool pose_smem = want_pose && ws.views <= kPoseSmemViews;
+  if (pose_smem) {  // every warp of the CTA is here (the early return above needs !want_pose)
+    for (int i = threadIdx.x; i < 6 * ws.views; i += blockDim.x) s_pose[i] = 0.f;
+    __syncthreads();
+  }
 
   float mu[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, logit = 0.f;
   if (any) {
@@ -363,153 +371,187 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) s_gsh[k][threadIdx.x] = 0.f;
 
-  for (int v = 0; v < ws.views; ++v) {
-    float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // The per-(Gaussian, view) chain rule; pose[] receives this view's
+  // contribution to the pose gradient.
+  auto view_bwd = [&](const int v, float pose[6]) {
     const int64_t e = (int64_t)v * n + g;
-    const bool vis = in_range && !rect_empty(ws.rects[e]);
-    if (vis) {
-      float4* ad = ws.adjoints + 3 * e;
-      const float4 A0 = ad[0], A1 = ad[1], A2 = ad[2];
-      const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
-      const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
-      const float gcol[3] = {A2.x, A2.y, A2.z};
-      const Cam cam = load_cam(cams, v);
-      const float3 mh = to_camera(cam, mu[0], mu[1], mu[2]);
-      const float iz = 1.f / mh.z;
-      const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
-      const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
-      const float txr = mh.x * iz, tyr = mh.y * iz;
-      const bool clx = txr > limx || txr < -limx, cly = tyr > limy || tyr < -limy;
-      const float txc = fminf(limx, fmaxf(-limx, txr)), tyc = fminf(limy, fmaxf(-limy, tyr));
-      const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz, j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
-      float m0[3], m1[3];
+    float4* ad = ws.adjoints + 3 * e;
+    const float4 A0 = ad[0], A1 = ad[1], A2 = ad[2];
+    const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
+    const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
+    const float gcol[3] = {A2.x, A2.y, A2.z};
+    const Cam cam = load_cam(cams, v);
+    const float3 mh = to_camera(cam, mu[0], mu[1], mu[2]);
+    const float iz = 1.f / mh.z;
+    const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
+    const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
+    const float txr = mh.x * iz, tyr = mh.y * iz;
+    const bool clx = txr > limx || txr < -limx, cly = tyr > limy || tyr < -limy;
+    const float txc = fminf(limx, fmaxf(-limx, txr)), tyc = fminf(limy, fmaxf(-limy, tyr));
+    const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz, j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
+    float m0[3], m1[3];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
-        m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
-      }
-      float U[3], Vv[3], rm0[3], rm1[3];
+    for (int j = 0; j < 3; ++j) {
+      m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
+      m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
+    }
+    float U[3], Vv[3], rm0[3], rm1[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        rm0[k] = Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2];
-        rm1[k] = Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2];
-        U[k] = s[k] * rm0[k];
-        Vv[k] = s[k] * rm1[k];
-      }
-      // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
-      const float qa = R0.z, qb = R0.w, qc = R1.x;
-      // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
-      const float hb = 0.5f * gb;
-      const float P00 = qa * ga + qb * hb, P01 = qa * hb + qb * gc, P10 = qb * ga + qc * hb, P11 = qb * hb + qc * gc;
-      const float gA = -(P00 * qa + P01 * qb);
-      const float gBh = -(P00 * qb + P01 * qc);  // d/dSigma'_01 (one of the two symmetric entries)
-      const float gCc = -(P10 * qb + P11 * qc);
-      const float gB = 2.f * gBh;
-      // A = U.U + dil, B = U.V, C = V.V + dil
-      float gU[3], gV[3];
+    for (int k = 0; k < 3; ++k) {
+      rm0[k] = Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2];
+      rm1[k] = Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2];
+      U[k] = s[k] * rm0[k];
+      Vv[k] = s[k] * rm1[k];
+    }
+    // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
+    const float qa = R0.z, qb = R0.w, qc = R1.x;
+    // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
+    const float hb = 0.5f * gb;
+    const float P00 = qa * ga + qb * hb, P01 = qa * hb + qb * gc, P10 = qb * ga + qc * hb, P11 = qb * hb + qc * gc;
+    const float gA = -(P00 * qa + P01 * qb);
+    const float gBh = -(P00 * qb + P01 * qc);  // d/dSigma'_01 (one of the two symmetric entries)
+    const float gCc = -(P10 * qb + P11 * qc);
+    const float gB = 2.f * gBh;
+    // A = U.U + dil, B = U.V, C = V.V + dil
+    float gU[3], gV[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        gU[k] = 2.f * gA * U[k] + gB * Vv[k];
-        gV[k] = gB * U[k] + 2.f * gCc * Vv[k];
-      }
-      float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k) {
+      gU[k] = 2.f * gA * U[k] + gB * Vv[k];
+      gV[k] = gB * U[k] + 2.f * gCc * Vv[k];
+    }
+    float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
-          gm0[i] += s[k] * gU[k] * Rg[i][k];
-          gm1[i] += s[k] * gV[k] * Rg[i][k];
-        }
-      }
-      // m0 = R^T J0, m1 = R^T J1  ->  dL/dJ0 = R gm0, dL/dJ1 = R gm1
-      float gJ0[3], gJ1[3];
+    for (int k = 0; k < 3; ++k) {
+      g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        gJ0[i] = cam.R[3 * i] * gm0[0] + cam.R[3 * i + 1] * gm0[1] + cam.R[3 * i + 2] * gm0[2];
-        gJ1[i] = cam.R[3 * i] * gm1[0] + cam.R[3 * i + 1] * gm1[1] + cam.R[3 * i + 2] * gm1[2];
-      }
-      const float iz2 = iz * iz;
-      float gx = gmx * cam.fx * iz, gy = gmy * cam.fy * iz;
-      float gz = gdep - gmx * cam.fx * mh.x * iz2 - gmy * cam.fy * mh.y * iz2;
-      gz += -gJ0[0] * cam.fx * iz2 - gJ1[1] * cam.fy * iz2;
-      // J02 = -fx txc / z: unclamped txc = x/z, clamped txc constant
-      gz += gJ0[2] * cam.fx * txc * iz2 * (clx ? 1.f : 2.f);
-      if (!clx) gx += -gJ0[2] * cam.fx * iz2;
-      gz += gJ1[2] * cam.fy * tyc * iz2 * (cly ? 1.f : 2.f);
-      if (!cly) gy += -gJ1[2] * cam.fy * iz2;
-      // dL/dmu through mu_hat = R mu + t
-      float gWm[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) gWm[j] = cam.R[j] * gx + cam.R[3 + j] * gy + cam.R[6 + j] * gz;
-      // colour: raw = sum_k SH_k Y_k(dir) + 0.5, clamped at 0
-      const float3 cw = camera_centre(cam);
-      float dv[3] = {mu[0] - cw.x, mu[1] - cw.y, mu[2] - cw.z};
-      const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-      const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
-      float Y[16];
-      sh_basis<DEG>(dx, dy, dz, Y);
-      float graw[3];
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float raw = 0.5f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
-        graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
-      }
-      // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
-      float wk[16];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        wk[k] = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * s_sh[3 * k + ch][threadIdx.x];
-      }
-      const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
-      const float gdir[3] = {gd3.x, gd3.y, gd3.z};
-      const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
-      const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
-#pragma unroll
-      for (int j = 0; j < 3; ++j) g_mu[j] += gWm[j] + gv[j];
-      g_o += gop;
-      // consume: leave the adjoint area zero for the next backward of this projection
-      ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (want_pose) {
-        // right perturbation T Exp(xi), xi = (rho, theta):
-        //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
-        const float gcw[3] = {-gv[0], -gv[1], -gv[2]};
-        pose[0] = gWm[0] - gcw[0];
-        pose[1] = gWm[1] - gcw[1];
-        pose[2] = gWm[2] - gcw[2];
-        // theta: mu x (R^T g_mu_hat) + gm0 x m0 + gm1 x m1 + g_cw x c_w
-        const float c_w[3] = {cw.x, cw.y, cw.z};
-        pose[3] = mu[1] * gWm[2] - mu[2] * gWm[1] + gm0[1] * m0[2] - gm0[2] * m0[1] + gm1[1] * m1[2] -
-                  gm1[2] * m1[1] + gcw[1] * c_w[2] - gcw[2] * c_w[1];
-        pose[4] = mu[2] * gWm[0] - mu[0] * gWm[2] + gm0[2] * m0[0] - gm0[0] * m0[2] + gm1[2] * m1[0] -
-                  gm1[0] * m1[2] + gcw[2] * c_w[0] - gcw[0] * c_w[2];
-        pose[5] = mu[0] * gWm[1] - mu[1] * gWm[0] + gm0[0] * m0[1] - gm0[1] * m0[0] + gm1[0] * m1[1] -
-                  gm1[1] * m1[0] + gcw[0] * c_w[1] - gcw[1] * c_w[0];
+        g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
+        gm0[i] += s[k] * gU[k] * Rg[i][k];
+        gm1[i] += s[k] * gV[k] * Rg[i][k];
       }
     }
+    // m0 = R^T J0, m1 = R^T J1  ->  dL/dJ0 = R gm0, dL/dJ1 = R gm1
+    float gJ0[3], gJ1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gJ0[i] = cam.R[3 * i] * gm0[0] + cam.R[3 * i + 1] * gm0[1] + cam.R[3 * i + 2] * gm0[2];
+      gJ1[i] = cam.R[3 * i] * gm1[0] + cam.R[3 * i + 1] * gm1[1] + cam.R[3 * i + 2] * gm1[2];
+    }
+    const float iz2 = iz * iz;
+    float gx = gmx * cam.fx * iz, gy = gmy * cam.fy * iz;
+    float gz = gdep - gmx * cam.fx * mh.x * iz2 - gmy * cam.fy * mh.y * iz2;
+    gz += -gJ0[0] * cam.fx * iz2 - gJ1[1] * cam.fy * iz2;
+    // J02 = -fx txc / z: unclamped txc = x/z, clamped txc constant
+    gz += gJ0[2] * cam.fx * txc * iz2 * (clx ? 1.f : 2.f);
+    if (!clx) gx += -gJ0[2] * cam.fx * iz2;
+    gz += gJ1[2] * cam.fy * tyc * iz2 * (cly ? 1.f : 2.f);
+    if (!cly) gy += -gJ1[2] * cam.fy * iz2;
+    // dL/dmu through mu_hat = R mu + t
+    float gWm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gWm[j] = cam.R[j] * gx + cam.R[3 + j] * gy + cam.R[6 + j] * gz;
+    // colour: raw = sum_k SH_k Y_k(dir) + 0.5, clamped at 0
+    const float3 cw = camera_centre(cam);
+    float dv[3] = {mu[0] - cw.x, mu[1] - cw.y, mu[2] - cw.z};
+    const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
+    float Y[16];
+    sh_basis<DEG>(dx, dy, dz, Y);
+    float graw[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
+      graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
+    }
+    // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
+    float wk[16];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      wk[k] = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * s_sh[3 * k + ch][threadIdx.x];
+    }
+    const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
+    const float gdir[3] = {gd3.x, gd3.y, gd3.z};
+    const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
+    const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g_mu[j] += gWm[j] + gv[j];
+    g_o += gop;
+    // consume: leave the adjoint area zero for the next backward of this projection
+    ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (want_pose) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        float val = pose[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(kFull, val, off);
-        if (lane == 0) s_pose[warp][k] = val;
-      }
-      __syncthreads();
-      if (threadIdx.x < 6) {
-        float tot = 0.f;
-        for (int w8 = 0; w8 < 8; ++w8) tot += s_pose[w8][threadIdx.x];
-        if (tot != 0.f) atomicAdd(a.grad_pose + 6 * v + threadIdx.x, tot);
-      }
-      __syncthreads();
+      // right perturbation T Exp(xi), xi = (rho, theta):
+      //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
+      const float gcw[3] = {-gv[0], -gv[1], -gv[2]};
+      pose[0] = gWm[0] - gcw[0];
+      pose[1] = gWm[1] - gcw[1];
+      pose[2] = gWm[2] - gcw[2];
+      // theta: mu x (R^T g_mu_hat) + gm0 x m0 + gm1 x m1 + g_cw x c_w
+      const float c_w[3] = {cw.x, cw.y, cw.z};
+      pose[3] = mu[1] * gWm[2] - mu[2] * gWm[1] + gm0[1] * m0[2] - gm0[2] * m0[1] + gm1[1] * m1[2] -
+                gm1[2] * m1[1] + gcw[1] * c_w[2] - gcw[2] * c_w[1];
+      pose[4] = mu[2] * gWm[0] - mu[0] * gWm[2] + gm0[2] * m0[0] - gm0[0] * m0[2] + gm1[2] * m1[0] -
+                gm1[0] * m1[2] + gcw[2] * c_w[0] - gcw[0] * c_w[2];
+      pose[5] = mu[0] * gWm[1] - mu[1] * gWm[0] + gm0[0] * m0[1] - gm0[1] * m0[0] + gm1[0] * m1[1] -
+                gm1[1] * m1[0] + gcw[0] * c_w[1] - gcw[1] * c_w[0];
     }
+  };
+  // Views are taken 32 at a time.  Each lane collects the views in which its
+  // Gaussian has a non-empty box.  When those sets are much alike across the
+  // warp, the views are taken in turn by all lanes together and the pose sums
+  // are warp reductions; otherwise each lane runs over its own views only (so
+  // that lanes are not left idle when the Gaussians are outside most views)
+  // and adds its pose terms one by one.
+  for (int v0 = 0; v0 < ws.views; v0 += 32) {
+    const int nv = min(32, ws.views - v0);
+    uint32_t vis_mask = 0;
+    if (in_range)
+      for (int j = 0; j < nv; ++j)
+        if (!rect_empty(ws.rects[(int64_t)(v0 + j) * n + g])) vis_mask |= 1u << j;
+    const uint32_t warp_mask = __reduce_or_sync(kFull, vis_mask);
+    const uint32_t most = __reduce_max_sync(kFull, (uint32_t)__popc(vis_mask));
+    if ((uint32_t)__popc(warp_mask) <= most + 1) {
+      for (uint32_t mk = warp_mask; mk; mk &= mk - 1) {
+        const int v = v0 + __ffs(mk) - 1;
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if ((vis_mask >> (v - v0)) & 1u) view_bwd(v, pose);
+        if (want_pose) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) pose[k] += __shfl_xor_sync(kFull, pose[k], off);
+          }
+          if ((threadIdx.x & 31) == 0) {
+            float* dst = (pose_smem ? s_pose : a.grad_pose) + 6 * v;
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+              if (pose[k] != 0.f) atomicAdd(dst + k, pose[k]);
+          }
+        }
+      }
+    } else {
+      while (vis_mask) {
+        const int v = v0 + __ffs(vis_mask) - 1;
+        vis_mask &= vis_mask - 1;
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        view_bwd(v, pose);
+        if (want_pose) {
+          float* dst = (pose_smem ? s_pose : a.grad_pose) + 6 * v;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) atomicAdd(dst + k, pose[k]);
+        }
+      }
+    }
+  }
+  if (pose_smem) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 6 * ws.views; i += blockDim.x)
+      if (s_pose[i] != 0.f) atomicAdd(a.grad_pose + i, s_pose[i]);
   }
   if (!any || !a.grad_mean) return;  // no parameter gradients wanted: pose only
   // quaternion: R(q^) entries -> q^ -> q (normalisation)
@@ -563,7 +605,7 @@ template <int DEG, bool BF16>
 static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                   const BwdArgs& a, cudaStream_t st) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const size_t smem = (size_t)2 * 3 * K * 256 * sizeof(float);
+  const size_t smem = ((size_t)2 * 3 * K * 256 + (ws.views <= kPoseSmemViews ? 6 * ws.views : 0)) * sizeof(float);
   cudaError_t err =
       cudaFuncSetAttribute(k_preprocess_bwd<DEG, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
