@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--views", type=int, default=WORKLOAD["views"], help="keyframes per batch (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    p.add_argument("--no-bucket", action="store_true", help="skip the per-Gaussian (bucket) backward leg")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
     p.add_argument("--tracking-frames", type=int, default=32,
                    help="frames in the tracking measurement (0 skips it): 1M Gaussians SH1, 640x512, N_t = 30")
@@ -373,6 +374,67 @@ def run_mapping_iteration(args, rast, gm, cams, w, tgt_rgb, tgt_depth):
             "ms_per_iteration": round(ms, 4), "mpix_per_s": round(V * H * W / (ms / 1e3) / 1e6, 1)}
 
 
+def run_bucket_backward(args, rast0, gm, cams, tgt_rgb, tgt_depth, w, k_eval):
+    """The headline step with the per-Gaussian (bucket) blend backward of
+    Sec. "Per-Gaussian Backpropagation" in place of the pixel-parallel one
+    (the forward then writes its bucket checkpoints): throughput and
+    per-kernel times on the same map, cameras and targets."""
+    import numpy as np
+    import torch
+
+    from paper_2507_04004_b300 import _native as N
+    from paper_2507_04004_b300.raster import Rasterizer
+    V, H, W = args.views, WORKLOAD["height"], WORKLOAD["width"]
+    rast = Rasterizer(gm.n, V, W, H, pair_capacity=rast0.capacity, device=gm.mean.device, backward="bucket")
+    out = rast.render(gm, cams, check=True)
+    grads = rast.new_grads(gm)
+
+    def step():
+        for t in (grads.mean, grads.log_scale, grads.quat, grads.logit_opacity, grads.sh_dc, grads.sh_rest,
+                  grads.pose, grads.loss):
+            t.zero_()
+        rast.render(gm, cams, check=False, out=out)
+        rast.backward(gm, cams, out, tgt_rgb=tgt_rgb, tgt_depth=tgt_depth, w_rgb=w.w_rgb, w_depth=w.w_depth,
+                      grads=grads)
+
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    n = 30
+    cap = 20 * n + 16
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * cap)]
+    for e in evs:
+        e.record()
+    ids = np.zeros(cap, np.int32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    N.gs_trace_start([e.cuda_event for e in evs], ids)
+    e0.record()
+    for _ in range(n):
+        step()
+    e1.record()
+    e1.synchronize()
+    launches = N.gs_trace_stop()
+    torch.cuda.synchronize()
+    code, _ = rast.status()
+    if code != 0:
+        raise SystemExit(f"workspace status {code} in the bucket-backward leg")
+    ms = e0.elapsed_time(e1) / n
+    per = {}
+    for k in range(min(launches, cap)):
+        a = per.setdefault(N.gs_kernel_name(int(ids[k])), [0, 0.0])
+        a[0] += 1
+        a[1] += evs[2 * k].elapsed_time(evs[2 * k + 1])
+    kern = {k: round(v[1] / v[0], 4) for k, v in sorted(per.items(), key=lambda x: -x[1][1])}
+    bwd_ms = kern.get("render_bwd_bucket", 0.0)
+    res = {"ms_per_step": round(ms, 4), "mpix_per_s": round(V * H * W / (ms / 1e3) / 1e6, 1), "kernels_ms": kern,
+           "blend_bwd_tflops": round(k_eval * 43.0 / (bwd_ms / 1e3) / 1e12, 2) if bwd_ms else None,
+           "bucket_workspace_bytes": int(rast._bucket_buf.numel())}
+    del rast, out, grads
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_tracking(args, dev):
     """Pose tracking with the map fixed (N_t = 30 Adam iterations of
     1/2 L1 + 1/2 D-SSIM per frame, all frames as one batch, one captured
@@ -652,6 +714,10 @@ def run_ours(args):
     total_px = d.sum(px_step * args.steps)
     value = total_px / (ms / 1e3) / 1e6
 
+    bucket = None
+    if d.rank == 0 and not args.no_bucket:
+        bucket = run_bucket_backward(args, rast, gm, cams, tgt_rgb, tgt_depth, w, k_eval)
+
     mapping_iter = None
     if d.rank == 0 and not args.no_e2e:
         mapping_iter = run_mapping_iteration(args, rast, gm, cams, w, tgt_rgb, tgt_depth)
@@ -687,6 +753,7 @@ def run_ours(args):
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "mapping_iteration": mapping_iter,
+                "bucket_backward": bucket,
                 "tracking": tracking,
                 "serving": serving,
                 "kernels": kernels,

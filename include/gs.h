@@ -191,6 +191,34 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
                         float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
                         gs_stream_t stream);
 
+/* Per-Gaussian backward (Sec. "Per-Gaussian Backpropagation"), an
+ * alternative to the pixel-parallel blend backward inside gs_render_bwd with
+ * the same results: the depth-sorted Gaussians of each tile are cut into
+ * buckets of 32, one warp lane per Gaussian, and the tile's pixels stream
+ * through the lanes carrying their transmittance, so each Gaussian's adjoints
+ * are summed in registers and added once per (Gaussian, tile).  The state at
+ * each bucket's start is checkpointed by the forward.
+ *   gs_bucket_workspace_size: bytes of the caller's device buffer for the
+ *     checkpoints (5 floats per pixel per bucket, sized for the workspace's
+ *     pair capacity) and the per-pixel adjoints; 0 on an invalid workspace.
+ *   gs_render_fwd_checkpointed: gs_render_fwd, plus the checkpoints written
+ *     into bucket_ws (device, 256-byte aligned).
+ *   gs_render_bwd_buckets: gs_render_bwd with the same arguments and
+ *     outputs, reading the checkpoints of the gs_render_fwd_checkpointed call
+ *     of the same batch; rgb and depth (that call's outputs) are required. */
+size_t gs_bucket_workspace_size(const gs_workspace* ws);
+gs_status gs_render_fwd_checkpointed(const gs_config* cfg, const gs_workspace* ws, float* rgb, float* depth,
+                                     float* opac, float* t_final, uint32_t* n_contrib, void* bucket_ws,
+                                     gs_stream_t stream);
+gs_status gs_render_bwd_buckets(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                                const gs_workspace* ws, const float* rgb, const float* depth, const float* opac,
+                                const float* t_final, const uint32_t* n_contrib, const float* tgt_rgb,
+                                const float* tgt_depth, float w_rgb, float w_depth, const float* dl_drgb,
+                                const float* dl_ddepth, const float* dl_dopac, float* grad_mean,
+                                float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                                float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
+                                const void* bucket_ws, gs_stream_t stream);
+
 /* Pose Jacobian rows (Eq. 3dgs_jacobi, right perturbation T Exp(xi),
  * xi = (rho, theta)): for n_pix listed pixels per view (pix_idx [V][n_pix],
  * linear index y*W + x, device), J [V][n_pix][3][6] = dC^/dxi by forward-mode

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_PKG, "libgsb300.so")
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(7)
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
+            "gs_render_fwd", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
+            "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
             "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_trace_start",
             "gs_trace_stop",
@@ -92,6 +93,11 @@ def lib():
         L.gs_render_fwd.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace), P, P, P, P, P, P]
         L.gs_render_bwd.argtypes = ([C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace)]
                                     + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P])
+        L.gs_bucket_workspace_size.argtypes = [C.POINTER(gs_workspace)]
+        L.gs_bucket_workspace_size.restype = C.c_size_t
+        L.gs_render_fwd_checkpointed.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace)] + [P] * 7
+        L.gs_render_bwd_buckets.argtypes = ([C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace)]
+                                            + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P, P])
         L.gs_pose_jacobian.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace), P, I32,
                                        P, P, P]
         L.gs_render_fwd_noalloc.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_frame), C.POINTER(gs_config),
@@ -119,6 +125,7 @@ def lib():
         L.gs_status_str.restype = C.c_char_p
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
+                     "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose",
                      "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes"):
             getattr(L, name).restype = I32
@@ -176,6 +183,29 @@ def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth,
         _ptr(n_contrib), _ptr(tgt_rgb), _ptr(tgt_depth), C.c_float(w_rgb), C.c_float(w_depth), _ptr(dl_drgb),
         _ptr(dl_ddepth), _ptr(dl_dopac), _ptr(grad_mean), _ptr(grad_log_scale), _ptr(grad_quat), _ptr(grad_logit),
         _ptr(grad_sh_dc), _ptr(grad_sh_rest), _ptr(grad_pose), _ptr(loss), C.c_void_p(stream)))
+
+
+def gs_bucket_workspace_size(ws: gs_workspace) -> int:
+    return int(lib().gs_bucket_workspace_size(C.byref(ws)))
+
+
+def gs_render_fwd_checkpointed(cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib, bucket_ws: int,
+                               stream: int) -> None:
+    check("gs_render_fwd_checkpointed", lib().gs_render_fwd_checkpointed(
+        C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac), _ptr(t_final), _ptr(n_contrib),
+        C.c_void_p(bucket_ws), C.c_void_p(stream)))
+
+
+def gs_render_bwd_buckets(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib,
+                          tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale,
+                          grad_quat, grad_logit, grad_sh_dc, grad_sh_rest, grad_pose, loss, bucket_ws: int,
+                          stream: int) -> None:
+    check("gs_render_bwd_buckets", lib().gs_render_bwd_buckets(
+        C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac), _ptr(t_final),
+        _ptr(n_contrib), _ptr(tgt_rgb), _ptr(tgt_depth), C.c_float(w_rgb), C.c_float(w_depth), _ptr(dl_drgb),
+        _ptr(dl_ddepth), _ptr(dl_dopac), _ptr(grad_mean), _ptr(grad_log_scale), _ptr(grad_quat), _ptr(grad_logit),
+        _ptr(grad_sh_dc), _ptr(grad_sh_rest), _ptr(grad_pose), _ptr(loss), C.c_void_p(bucket_ws),
+        C.c_void_p(stream)))
 
 
 def gs_pose_jacobian(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, pix, n_pix: int, J, rgb, stream: int) -> None:

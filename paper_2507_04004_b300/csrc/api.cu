@@ -197,15 +197,15 @@ gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 
-gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
-                        const float* rgb, const float* depth, const float* opac, const float* t_final,
-                        const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
-                        float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
-                        float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
-                        float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
-                        gs_stream_t stream) {
-  gs_layout L;
-  gs_status s = check_ws(ws, &L);
+// Argument checks and marshalling shared by both blend backwards.
+static gs_status bwd_args(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                          const float* rgb, const float* depth, const float* opac, const float* t_final,
+                          const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
+                          float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
+                          float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                          float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out, gs_layout* L,
+                          BwdArgs* out) {
+  gs_status s = check_ws(ws, L);
   if (s != GS_OK) return s;
   if ((s = check_map(map, ws)) != GS_OK) return s;
   if ((s = check_cfg(cfg)) != GS_OK) return s;
@@ -229,8 +229,66 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
   a.grad_mean = grad_mean; a.grad_log_scale = grad_log_scale; a.grad_quat = grad_quat;
   a.grad_logit = grad_logit_opacity; a.grad_sh_dc = grad_sh_dc; a.grad_sh_rest = grad_sh_rest;
   a.grad_pose = grad_pose; a.loss = loss_out;
+  *out = a;
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
+                        const float* rgb, const float* depth, const float* opac, const float* t_final,
+                        const uint32_t* n_contrib, const float* tgt_rgb, const float* tgt_depth, float w_rgb,
+                        float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
+                        float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                        float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
+                        gs_stream_t stream) {
+  gs_layout L;
+  BwdArgs a;
+  const gs_status s = bwd_args(map, cams_dev, cfg, ws, rgb, depth, opac, t_final, n_contrib, tgt_rgb, tgt_depth,
+                               w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale, grad_quat,
+                               grad_logit_opacity, grad_sh_dc, grad_sh_rest, grad_pose, loss_out, &L, &a);
+  if (s != GS_OK) return s;
   return cuda_status(launch_render_bwd(*map, cams_dev, *cfg, resolve_ws(ws, L), a,
                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t gs_bucket_workspace_size(const gs_workspace* ws) {
+  gs_layout L;
+  if (check_ws(ws, &L) != GS_OK) return 0;
+  return bucket_ws_bytes(resolve_ws(ws, L));
+}
+
+gs_status gs_render_fwd_checkpointed(const gs_config* cfg, const gs_workspace* ws, float* rgb, float* depth,
+                                     float* opac, float* t_final, uint32_t* n_contrib, void* bucket_ws,
+                                     gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!t_final || !n_contrib || !bucket_ws || (reinterpret_cast<uintptr_t>(bucket_ws) & 255u)) return GS_ERR_ARG;
+  const Ws w = resolve_ws(ws, L);
+  return cuda_status(launch_render_fwd_ckpt(*cfg, w, rgb, depth, opac, t_final, n_contrib,
+                                            resolve_bucket_ws(w, bucket_ws).ckpt,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_render_bwd_buckets(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                                const gs_workspace* ws, const float* rgb, const float* depth, const float* opac,
+                                const float* t_final, const uint32_t* n_contrib, const float* tgt_rgb,
+                                const float* tgt_depth, float w_rgb, float w_depth, const float* dl_drgb,
+                                const float* dl_ddepth, const float* dl_dopac, float* grad_mean,
+                                float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
+                                float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
+                                const void* bucket_ws, gs_stream_t stream) {
+  gs_layout L;
+  BwdArgs a;
+  const gs_status s = bwd_args(map, cams_dev, cfg, ws, rgb, depth, opac, t_final, n_contrib, tgt_rgb, tgt_depth,
+                               w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale, grad_quat,
+                               grad_logit_opacity, grad_sh_dc, grad_sh_rest, grad_pose, loss_out, &L, &a);
+  if (s != GS_OK) return s;
+  if (!rgb || !depth || !bucket_ws || (reinterpret_cast<uintptr_t>(bucket_ws) & 255u)) return GS_ERR_ARG;
+  const Ws w = resolve_ws(ws, L);
+  return cuda_status(launch_render_bwd_bucket(*map, cams_dev, *cfg, w, a,
+                                              resolve_bucket_ws(w, const_cast<void*>(bucket_ws)),
+                                              reinterpret_cast<cudaStream_t>(stream)));
 }
 
 gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
@@ -354,7 +412,8 @@ const char* gs_kernel_name(int32_t id) {
                                             "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
                                             "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
                                             "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam",
-                                            "sort_medium"};
+                                            "sort_medium", "render_fwd_ckpt", "pixel_adjoint",
+                                            "render_bwd_bucket"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -12,7 +12,7 @@ namespace gsb {
 enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
   kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
-  kKSortMedium, kKNumKernels
+  kKSortMedium, kKRenderFwdCkpt, kKPixelAdjoint, kKRenderBwdBucket, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);
@@ -57,6 +57,24 @@ struct BwdArgs {
 };
 cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                               const BwdArgs& a, cudaStream_t st);
+// Stages shared by both blend backwards: per-view loss accumulators and
+// valid-depth counts before the blend stage, the projection backward after it.
+cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                  const BwdArgs& a, cudaStream_t st);
+// Per-Gaussian (bucket) backward: checkpoints written by the forward and the
+// per-pixel adjoints, in one caller buffer of bucket_ws_bytes(ws) bytes.
+struct BucketWs {
+  float* pix;    // [V*T][8][256]: dL/dC_r, C_g, C_b, dL/dD, dL/dO, adjoint-weighted output, n_contrib bits, -
+  float* ckpt;   // [nbuckets][5][256]: T, C_r, C_g, C_b, D at each bucket start
+  int64_t nbuckets;
+};
+size_t bucket_ws_bytes(const Ws& ws);
+BucketWs resolve_bucket_ws(const Ws& ws, void* ptr);
+cudaError_t launch_render_fwd_ckpt(const gs_config& cfg, const Ws& ws, float* rgb, float* depth, float* opac,
+                                   float* t_final, uint32_t* n_contrib, float* ckpt, cudaStream_t st);
+cudaError_t launch_render_bwd_bucket(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                     const BwdArgs& a, const BucketWs& bw, cudaStream_t st);
 cudaError_t launch_pose_jacobian(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                  const int32_t* pix, int32_t n_pix, float* J, float* rgb, cudaStream_t st);
 

@@ -615,8 +615,7 @@ static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
-                              const BwdArgs& a, cudaStream_t st) {
+cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(ws.view_stats, 0, (size_t)ws.views * 4 * sizeof(float), st);
   if (err != cudaSuccess) return err;
   const bool fused = a.tgt_rgb != nullptr;
@@ -629,12 +628,11 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
     trace_end(st);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
-  trace_begin(kKRenderBwd, st);
-  if (fused) k_render_bwd<true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
-  else k_render_bwd<false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
-  trace_end(st);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  return cudaSuccess;
+}
+
+cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                  const BwdArgs& a, cudaStream_t st) {
   const bool bf = map.sh_bf16 != 0;
   switch (map.sh_degree) {
     case 0: return bf ? launch_pre_bwd<0, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<0, false>(map, cams, cfg, ws, a, st);
@@ -642,6 +640,20 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
     case 2: return bf ? launch_pre_bwd<2, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<2, false>(map, cams, cfg, ws, a, st);
     default: return bf ? launch_pre_bwd<3, true>(map, cams, cfg, ws, a, st) : launch_pre_bwd<3, false>(map, cams, cfg, ws, a, st);
   }
+}
+
+cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                              const BwdArgs& a, cudaStream_t st) {
+  cudaError_t err = launch_bwd_prologue(ws, a, st);
+  if (err != cudaSuccess) return err;
+  const bool fused = a.tgt_rgb != nullptr;
+  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  trace_begin(kKRenderBwd, st);
+  if (fused) k_render_bwd<true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  else k_render_bwd<false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  trace_end(st);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  return launch_preprocess_bwd(map, cams, cfg, ws, a, st);
 }
 
 }  // namespace gsb

@@ -5,15 +5,23 @@
 // is read once per kPPT pixels.  The tile's depth-sorted Gaussians are staged
 // 256 at a time and the CTA stops as soon as every pixel's transmittance is
 // exhausted.
+//
+// The checkpointing variant (CKPT) also records, at the start of every
+// 32-Gaussian bucket of the tile's list, each pixel's transmittance and
+// accumulated colour and depth, for the per-Gaussian backward of
+// Sec. "Per-Gaussian Backpropagation" (bucket b of tile t is record
+// (tile_start[t] >> 5) + t + b of the checkpoint array, planes T, C_r, C_g,
+// C_b, D of 256 pixels each, pixel index y * 16 + x within the tile).
 #include "gs_internal.h"
 
 namespace gsb {
 
-template <int PPT>
+template <int PPT, bool CKPT>
 __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, float* __restrict__ rgb,
                                                           float* __restrict__ depth, float* __restrict__ opac,
                                                           float* __restrict__ t_final,
-                                                          uint32_t* __restrict__ n_contrib) {
+                                                          uint32_t* __restrict__ n_contrib,
+                                                          float* __restrict__ ckpt) {
   constexpr int NT = 256 / PPT;  // threads per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
   __shared__ float4 s_g0[256], s_g1[256], s_c[256];
@@ -62,6 +70,20 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     }
     __syncthreads();
     for (uint32_t j = 0; j < nb && !all_done; ++j) {
+      if (CKPT && ((b0 + j) & 31u) == 0) {
+        float* ck = ckpt + ((int64_t)(start >> 5) + tile + ((b0 + j) >> 5)) * (5 * 256);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const int lp = (threadIdx.x & 15) + 16 * (PPT * (threadIdx.x >> 4) + k);
+          const int h = k >> 1;
+          const bool hi = k & 1;
+          ck[lp] = hi ? T[h].y : T[h].x;
+          ck[256 + lp] = hi ? C0[h].y : C0[h].x;
+          ck[512 + lp] = hi ? C1[h].y : C1[h].x;
+          ck[768 + lp] = hi ? C2[h].y : C2[h].x;
+          ck[1024 + lp] = hi ? D[h].y : D[h].x;
+        }
+      }
       const float4 g0 = s_g0[j], g1 = s_g1[j];
       const ColTerms ct = col_terms(g0, g1, px);
       const float4 c = s_c[j];
@@ -120,7 +142,17 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const Ws& ws, float* rgb, fl
                               float* t_final, uint32_t* n_contrib, cudaStream_t st) {
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
   trace_begin(kKRenderFwd, st);
-  k_render_fwd<kFwdPPT><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib);
+  k_render_fwd<kFwdPPT, false><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib,
+                                                                  nullptr);
+  trace_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd_ckpt(const gs_config& cfg, const Ws& ws, float* rgb, float* depth, float* opac,
+                                   float* t_final, uint32_t* n_contrib, float* ckpt, cudaStream_t st) {
+  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  trace_begin(kKRenderFwdCkpt, st);
+  k_render_fwd<kFwdPPT, true><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib, ckpt);
   trace_end(st);
   return cudaGetLastError();
 }

@@ -107,10 +107,18 @@ class Rasterizer:
     The workspace keeps the projected Gaussians and tile lists of the last
     :meth:`render` / :meth:`project_and_sort` call, which :meth:`backward` and
     :meth:`pose_jacobian` reuse.  ``pair_capacity`` grows automatically when a
-    checked call finds the pair buffer too small."""
+    checked call finds the pair buffer too small.
+
+    ``backward``: "pixel" (default) runs the pixel-parallel blend backward;
+    "bucket" the per-Gaussian one of Sec. "Per-Gaussian Backpropagation"
+    (the forward then also writes its bucket checkpoints)."""
 
     def __init__(self, n: int, n_views: int, width: int, height: int, pair_capacity: int | None = None,
-                 config: dict | None = None, device="cuda"):
+                 config: dict | None = None, device="cuda", backward: str = "pixel"):
+        if backward not in ("pixel", "bucket"):
+            raise ValueError("backward must be 'pixel' or 'bucket'")
+        self.backward_mode = backward
+        self._bucket_buf = None
         self.n, self.views, self.width, self.height = int(n), int(n_views), int(width), int(height)
         self.device = torch.device(device)
         self.cfg = make_config(**(config or {}))
@@ -131,6 +139,11 @@ class Rasterizer:
         self.ws = N.gs_workspace(aligned, self.n, self.capacity, self.frame)
         self.layout = N.gs_workspace_layout(self.n, self.frame, self.capacity)
         self._base_off = aligned - base
+        if self.backward_mode == "bucket":
+            self._bucket_buf = None  # release before the new one is sized
+            bsize = N.gs_bucket_workspace_size(self.ws)
+            self._bucket_buf = torch.empty(bsize + 256, dtype=torch.uint8, device=self.device)
+            self.bucket_ws = (self._bucket_buf.data_ptr() + 255) // 256 * 256
 
     @property
     def workspace_bytes(self) -> int:
@@ -193,7 +206,12 @@ class Rasterizer:
             f = dict(device=self.device, dtype=torch.float32)
             out = RenderOut(torch.empty(V, 3, H, W, **f), torch.empty(V, H, W, **f), torch.empty(V, H, W, **f),
                             torch.empty(V, H, W, **f), torch.empty(V, H, W, dtype=torch.int32, device=self.device))
-        N.gs_render_fwd(self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final, out.n_contrib, self._stream())
+        if self.backward_mode == "bucket":
+            N.gs_render_fwd_checkpointed(self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final, out.n_contrib,
+                                         self.bucket_ws, self._stream())
+        else:
+            N.gs_render_fwd(self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final, out.n_contrib,
+                            self._stream())
         return out
 
     def new_grads(self, gmap: GaussianMap) -> Grads:
@@ -212,11 +230,14 @@ class Rasterizer:
         pose gradient (and loss) only, the map held fixed."""
         g = grads if grads is not None else self.new_grads(gmap)
         pg = (lambda t: t) if params else (lambda t: None)
-        N.gs_render_bwd(gmap.struct(), cams, self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final,
-                        out.n_contrib, tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, pg(g.mean),
-                        pg(g.log_scale), pg(g.quat), pg(g.logit_opacity), pg(g.sh_dc),
-                        pg(g.sh_rest) if gmap.sh_degree > 0 else None, g.pose if pose else None, g.loss,
-                        self._stream())
+        args = (gmap.struct(), cams, self.cfg, self.ws, out.rgb, out.depth, out.opac, out.t_final, out.n_contrib,
+                tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, pg(g.mean), pg(g.log_scale),
+                pg(g.quat), pg(g.logit_opacity), pg(g.sh_dc), pg(g.sh_rest) if gmap.sh_degree > 0 else None,
+                g.pose if pose else None, g.loss)
+        if self.backward_mode == "bucket":
+            N.gs_render_bwd_buckets(*args, self.bucket_ws, self._stream())
+        else:
+            N.gs_render_bwd(*args, self._stream())
         return g
 
     def pose_jacobian(self, gmap: GaussianMap, cams: torch.Tensor, pix: torch.Tensor):

@@ -18,11 +18,11 @@ def host_map(g: synth.GaussianMap, sh_bf16=False) -> dict:
     return d
 
 
-def gpu_render(g, cams, sh_bf16=False, capacity=None, config=None):
+def gpu_render(g, cams, sh_bf16=False, capacity=None, config=None, backward="pixel"):
     from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
     gm = GaussianMap.from_host(g, sh_bf16=sh_bf16)
     W, H = cams[0]["width"], cams[0]["height"]
-    rast = Rasterizer(gm.n, len(cams), W, H, pair_capacity=capacity, config=config)
+    rast = Rasterizer(gm.n, len(cams), W, H, pair_capacity=capacity, config=config, backward=backward)
     ct = cameras_tensor(cams)
     out = rast.render(gm, ct)
     torch.cuda.synchronize()

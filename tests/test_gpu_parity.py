@@ -104,6 +104,30 @@ def test_projection_records_match_oracle(oracle):
             np.testing.assert_allclose(rec[v, on, 8 + c], p["rgb"][c, on], atol=2e-6)
 
 
+def test_offscreen_gaussians_reaching_into_the_image(oracle):
+    """Centres outside the image, ellipses (large, anisotropic, many beyond
+    the FOV clamp) reaching into it: the projection's early off-screen cull is
+    conservative, so the tile lists still equal the oracle's in every view."""
+    rng = np.random.default_rng(77)
+    W, H, f, n = 160, 112, 100.0, 6000
+    g = synth.random_map(rng, n, (-1, -1, 2), (1, 1, 6), 1, log_scale_mean=-1.2, log_scale_std=0.9)
+    z = rng.uniform(0.8, 8.0, n)
+    u, v = rng.uniform(-W, 2 * W, n), rng.uniform(-H, 2 * H, n)
+    g.mean[:] = np.stack([(u - W / 2) * z / f, (v - H / 2) * z / f, z]).astype(np.float32)
+    cams = [synth.camera(np.eye(3), np.zeros(3), f, f, W / 2, H / 2, W, H)]
+    for yaw, pitch, roll in ((0.25, 0.0, 0.0), (-0.1, 0.2, 0.3)):
+        R, t = synth.pose_from_centre(synth.yaw_pitch_rotation(yaw, pitch, roll), (0.1, -0.05, 0.2))
+        cams.append(synth.camera(R, t, f, 0.9 * f, W / 2 + 3.0, H / 2 - 2.0, W, H))
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, cams)
+    assert rast.status()[0] == 0
+    outside = (u < 0) | (u >= W) | (v < 0) | (v >= H)
+    ot, og, _ = oracle.tiles(m, cams[0])
+    assert np.isin(np.nonzero(outside)[0], og).sum() > 300  # many off-screen centres do reach in
+    for view, cam in enumerate(cams):
+        compare_tiles(oracle, m, cam, rast, view)
+
+
 @pytest.mark.parametrize("sh_bf16,degenerate", [(False, 0.0), (True, 0.01)])
 def test_multiview_ragged_sh3(oracle, sh_bf16, degenerate):
     g, cams = _mapping_small(degenerate=degenerate)
@@ -202,11 +226,12 @@ def _tiny_depth_target(oracle, w, m):
     return d[None].astype(np.float32)
 
 
-def test_tiny_fused_loss_gradients(oracle):
+@pytest.mark.parametrize("backward", ["pixel", "bucket"])
+def test_tiny_fused_loss_gradients(oracle, backward):
     w = synth.tiny()
     m = host_map(w.gmap)
     tgt_d = _tiny_depth_target(oracle, w, m)
-    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams, backward=backward)
     tr = torch.as_tensor(w.tgt_rgb, device="cuda")
     td = torch.as_tensor(tgt_d, device="cuda")
     g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth))
@@ -216,14 +241,15 @@ def test_tiny_fused_loss_gradients(oracle):
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
 
 
-def test_fused_loss_plus_external_adjoints_and_pose_only(oracle):
+@pytest.mark.parametrize("backward", ["pixel", "bucket"])
+def test_fused_loss_plus_external_adjoints_and_pose_only(oracle, backward):
     """The fused loss with further pixel adjoints added equals the sum of the
     two backward passes (linearity in the pixel adjoints), and the pose-only
     backward (no parameter gradients) gives the pose gradient of the full one."""
     w = synth.tiny()
     m = host_map(w.gmap)
     tgt_d = _tiny_depth_target(oracle, w, m)
-    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams, backward=backward)
     tr = torch.as_tensor(w.tgt_rgb, device="cuda")
     td = torch.as_tensor(tgt_d, device="cuda")
     rng = np.random.default_rng(12)
@@ -245,7 +271,8 @@ def test_fused_loss_plus_external_adjoints_and_pose_only(oracle):
         assert not np.any(gp[k]), k
 
 
-def test_alpha_clamp_path(oracle):
+@pytest.mark.parametrize("backward", ["pixel", "bucket"])
+def test_alpha_clamp_path(oracle, backward):
     """A fifth of the Gaussians with opacity 0.9975, so that alpha is clamped
     at alpha_max near their centres (the blend kernels take a separate path
     for Gaussians whose opacity comes near the clamp): images, last
@@ -257,7 +284,7 @@ def test_alpha_clamp_path(oracle):
     lo[hot] = logit(0.9975)
     w.gmap.logit_opacity[:] = lo.astype(np.float32)
     m = host_map(w.gmap)
-    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams, backward=backward)
     o_r = oracle.render(m, w.cams[0])
     _check_images(o_r, out, 0, "clamped alpha")
     _check_last_contributor(rast, out, o_r, 0)
@@ -277,11 +304,11 @@ def test_alpha_clamp_path(oracle):
     assert np.abs(Jg[ok] - Jo[ok]).max() <= GRAD_TOL * np.abs(Jo[ok]).max()
 
 
-@pytest.mark.parametrize("sh_bf16", [False, True])
-def test_multiview_external_adjoint_gradients(oracle, sh_bf16):
+@pytest.mark.parametrize("sh_bf16,backward", [(False, "pixel"), (True, "pixel"), (False, "bucket")])
+def test_multiview_external_adjoint_gradients(oracle, sh_bf16, backward):
     g, cams = _mapping_small(n=12000, sh_degree=3)
     m = host_map(g, sh_bf16)
-    rast, gm, ct, out = gpu_render(g, cams, sh_bf16=sh_bf16)
+    rast, gm, ct, out = gpu_render(g, cams, sh_bf16=sh_bf16, backward=backward)
     V, H, W = len(cams), cams[0]["height"], cams[0]["width"]
     rng = np.random.default_rng(3)
     er = rng.normal(size=(V, 3, H, W)).astype(np.float32)
@@ -295,11 +322,12 @@ def test_multiview_external_adjoint_gradients(oracle, sh_bf16):
         assert rel_err(gg["pose"][v], o["pose"][v]) <= GRAD_TOL, v
 
 
-def test_mapping_fused_loss_with_lidar_depth(oracle):
+@pytest.mark.parametrize("backward", ["pixel", "bucket"])
+def test_mapping_fused_loss_with_lidar_depth(oracle, backward):
     """Small copy of the mapping workload: LiDAR sparse depth, 0.8 L1 + 0.2 depth."""
     w = synth.mapping(n=30000, width=160, height=96, focal=90.0, n_views=2)
     m = host_map(w.gmap)
-    rast, gm, ct, out = gpu_render(w.gmap, w.cams)
+    rast, gm, ct, out = gpu_render(w.gmap, w.cams, backward=backward)
     t = lambda a: torch.as_tensor(a, device="cuda")
     g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=t(w.tgt_rgb), tgt_depth=t(w.tgt_depth), w_rgb=w.w_rgb,
                                      w_depth=w.w_depth))
@@ -309,10 +337,11 @@ def test_mapping_fused_loss_with_lidar_depth(oracle):
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
 
 
-def test_backward_twice_gives_same_gradients():
+@pytest.mark.parametrize("backward", ["pixel", "bucket"])
+def test_backward_twice_gives_same_gradients(backward):
     """The 2D adjoint area is consumed and cleared by each backward."""
     g, cams = _mapping_small(n=6000)
-    rast, gm, ct, out = gpu_render(g, cams)
+    rast, gm, ct, out = gpu_render(g, cams, backward=backward)
     dl = torch.randn(len(cams), 3, cams[0]["height"], cams[0]["width"], device="cuda")
     g1 = rast.backward(gm, ct, out, dl_drgb=dl)
     g2 = rast.backward(gm, ct, out, dl_drgb=dl)
@@ -376,3 +405,45 @@ def test_equal_depth_keys_sort_by_index(oracle, n):
     assert len(set(oracle.depth_keys(host_map(g), cam).tolist())) == 1
     compare_tiles(oracle, host_map(g), cam, rast, 0)
     _check_images(oracle.render(host_map(g), cam), out, 0, "equal depths")
+
+
+def test_bucket_backward_long_contributor_lists(oracle):
+    """Faint Gaussians in depth (opacity 0.02-0.1), so that pixels blend
+    hundreds of them and each tile's backward spans many 32-Gaussian buckets:
+    the per-Gaussian backward against the oracle and against the
+    pixel-parallel backward."""
+    rng = np.random.default_rng(21)
+    n = 6000
+    g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 30), 1, log_scale_mean=-0.8, log_scale_std=0.3)
+    op = rng.uniform(0.02, 0.1, n)
+    g.logit_opacity[:] = np.log(op / (1 - op)).astype(np.float32)
+    cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 40.0, 24.0, 20.0, 48, 40)
+    m = host_map(g)
+    tgt = rng.random((1, 3, 40, 48)).astype(np.float32)
+    res = {}
+    for backward in ("pixel", "bucket"):
+        rast, gm, ct, out = gpu_render(g, [cam], backward=backward)
+        assert int(out.n_contrib.max()) > 8 * 32
+        res[backward] = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=torch.as_tensor(tgt, device="cuda")))
+    o = oracle.backward(m, [cam], tgt_rgb=tgt, w_rgb=1.0)
+    assert_grads_close(res["bucket"], o, GRAD_KEYS)
+    assert rel_err(res["bucket"]["pose"], o["pose"]) <= GRAD_TOL
+    for k in GRAD_KEYS + ("pose", "loss"):
+        assert rel_err(res["bucket"][k], res["pixel"][k]) <= 2e-4, k
+
+
+def test_bucket_backward_matches_pixel_at_mapping_size():
+    """200k Gaussians, 2 x 1280x720 with LiDAR depth (lists of hundreds,
+    several buckets per tile): both blend backwards give the same loss and
+    gradients (the pixel-parallel one is the oracle-checked path at this size)."""
+    w = synth.mapping(n=200_000, n_views=2)
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    res = {}
+    for backward in ("pixel", "bucket"):
+        rast, gm, ct, out = gpu_render(w.gmap, w.cams, backward=backward)
+        res[backward] = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=t(w.tgt_rgb), tgt_depth=t(w.tgt_depth),
+                                                     w_rgb=w.w_rgb, w_depth=w.w_depth))
+        assert int(out.n_contrib.max()) > 3 * 32
+    np.testing.assert_allclose(res["bucket"]["loss"], res["pixel"]["loss"], rtol=1e-5)
+    for k in GRAD_KEYS + ("pose",):
+        assert rel_err(res["bucket"][k], res["pixel"][k]) <= 2e-4, k
