@@ -200,7 +200,7 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
  * each bucket's start is checkpointed by the forward.
  *   gs_bucket_workspace_size: bytes of the caller's device buffer for the
  *     checkpoints (5 floats per pixel per bucket, sized for the workspace's
- *     pair capacity) and the per-pixel adjoints; 0 on an invalid workspace.
+ *     pair capacity); 0 on an invalid workspace.
  *   gs_render_fwd_checkpointed: gs_render_fwd, plus the checkpoints written
  *     into bucket_ws (device, 256-byte aligned).
  *   gs_render_bwd_buckets: gs_render_bwd with the same arguments and

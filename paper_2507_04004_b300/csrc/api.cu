@@ -412,8 +412,7 @@ const char* gs_kernel_name(int32_t id) {
                                             "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
                                             "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
                                             "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam",
-                                            "sort_medium", "render_fwd_ckpt", "pixel_adjoint",
-                                            "render_bwd_bucket"};
+                                            "sort_medium", "render_fwd_ckpt", "render_bwd_bucket"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

@@ -12,7 +12,7 @@ namespace gsb {
 enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
   kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
-  kKSortMedium, kKRenderFwdCkpt, kKPixelAdjoint, kKRenderBwdBucket, kKNumKernels
+  kKSortMedium, kKRenderFwdCkpt, kKRenderBwdBucket, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);
@@ -62,10 +62,9 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
 cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st);
 cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                   const BwdArgs& a, cudaStream_t st);
-// Per-Gaussian (bucket) backward: checkpoints written by the forward and the
-// per-pixel adjoints, in one caller buffer of bucket_ws_bytes(ws) bytes.
+// Per-Gaussian (bucket) backward: the checkpoints written by the forward, in
+// one caller buffer of bucket_ws_bytes(ws) bytes.
 struct BucketWs {
-  float* pix;    // [V*T][8][256]: dL/dC_r, C_g, C_b, dL/dD, dL/dO, adjoint-weighted output, n_contrib bits, -
   float* ckpt;   // [nbuckets][5][256]: T, C_r, C_g, C_b, D at each bucket start
   int64_t nbuckets;
 };
