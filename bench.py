@@ -518,7 +518,7 @@ def run_serving(args, dev):
     srv = Server(gm, mem_budget=4 << 30, max_views=4, n_streams=4, pairs_per_pixel=8.0, device=dev)
     srv.calibrate(calib)
     srv.warmup({r.key for r in reqs})
-    srv.start()
+    srv.start(prime=calib)
     rs = fresh()
     for r in rs:
         r.future = type(r.future)()
@@ -539,6 +539,7 @@ def run_serving(args, dev):
     out["server_batches"] = srv.batches
     out["server_retries"] = srv.retries
     out["server_runners_added"] = srv.runners_added
+    out["server_runners_added_keys"] = [f"{k} {w}x{h} x{s}" for k, w, h, s in srv.added_keys]
     out["server_grows"] = srv.grows
     out["server_pairs_per_view_max"] = {f"{k[0]} {k[1]}x{k[2]}": v for k, v in srv.pairs_per_view.items()}
     out["server_max_inflight_sort_gib"] = round(srv.max_inflight_bytes / 2 ** 30, 3)

@@ -15,7 +15,10 @@ factor option 2, Sec. "Camera Factor (Option 2)").  The server
   request cameras copied into the graph's camera buffer;
 * runs batches on a pool of streams so that batches formed while others are
   on the GPU overlap with them, and resolves each request's future when its
-  batch's completion event fires.
+  batch's completion event fires;
+* creates a runner that is missing while batches are in flight on a builder
+  thread (workspace allocation and graph capture take milliseconds), so the
+  scheduler keeps launching meanwhile.
 
 All rasterizer work runs in the CUDA kernels of ``libgsb300.so``.  A batch whose
 pair buffer overflowed (device status word) is re-run eagerly with a larger
@@ -136,6 +139,10 @@ class _Runner:
                 self._work()
             finally:
                 g.capture_end()
+            # the first launch of an instantiated graph uploads it to the device
+            # (tens of milliseconds for these graphs): do it here, not on a request
+            g.replay()
+        s.synchronize()
         self.graph = g
 
     def launch(self, reqs, stream):
@@ -217,7 +224,12 @@ class Server:
         self.pairs_sum: dict = collections.defaultdict(float)  # key -> (sum of per-view pair counts, views)
         self.pairs_views: dict = collections.defaultdict(int)
         self.runners_added = 0  # runners created while serving (all others came from warmup)
+        self.added_keys = []    # (kind, W, H, slots) of those
         self.grows = 0          # workspaces re-allocated for a larger pair demand
+        self._build_q: queue.Queue = queue.Queue()
+        self._built: queue.Queue = queue.Queue()
+        self._building = set()
+        self._builder = None
 
     # ---------------------------------------------------------------- setup
     def _capacity(self, key, slots, headroom: float = 1.25):
@@ -263,9 +275,43 @@ class Server:
         self.runners[(key, slots)].append(r)
         if self._thread is not None:
             self.runners_added += 1
+            self.added_keys.append((key[0], key[1], key[2], slots))
         return r
 
-    def warmup(self, keys, copies: int = 3):
+    def _request_build(self, key, slots):
+        if (key, slots) not in self._building:
+            self._building.add((key, slots))
+            self._build_q.put((key, slots, self._capacity(key, slots, headroom=1.6)))
+
+    def _build_loop(self):
+        torch.cuda.set_device(self.device)
+        while True:
+            item = self._build_q.get()
+            if item is None:
+                return
+            key, slots, cap = item
+            try:
+                r = _Runner(self, key, slots, cap)
+                if self.use_graphs:
+                    r.capture(warm=False)
+                self._built.put(r)
+            except BaseException as exc:  # handed to the scheduler, which fails the waiting requests
+                self._built.put(exc)
+
+    def _take_built(self):
+        while True:
+            try:
+                r = self._built.get_nowait()
+            except queue.Empty:
+                return
+            if isinstance(r, BaseException):
+                raise r
+            self.runners[(r.key, r.slots)].append(r)
+            self._building.discard((r.key, r.slots))
+            self.runners_added += 1
+            self.added_keys.append((r.key[0], r.key[1], r.key[2], r.slots))
+
+    def warmup(self, keys, copies: int = 3, pinned_per_key: int = 32):
         """Create and capture runners per (key, slot count) before serving
         (``copies`` of each, two more for single-request batches, which
         overlap most), so that overlapping batches rarely need a new one."""
@@ -278,6 +324,14 @@ class Server:
                     made.append(r)
                 for r in made:
                     r.busy = False
+        # each request's results go to the caller in pinned host tensors from
+        # torch's pinned-memory cache; fill the cache now (a pinned allocation
+        # of megabytes takes milliseconds) so that requests do not pay for it
+        for key in keys:
+            kind, W, H, npix = key
+            shapes = [(npix, 3, 6), (npix, 3)] if kind == "jacobian" else [(3, H, W), (H, W)]
+            held = [torch.empty(sh, pin_memory=True) for _ in range(pinned_per_key) for sh in shapes]
+            del held
         torch.cuda.synchronize(self.device)
 
     # ---------------------------------------------------------------- API
@@ -286,20 +340,45 @@ class Server:
         self.inbox.put(req)
         return req.future
 
-    def start(self):
+    def start(self, prime=None):
+        """Start the scheduler.  ``prime``: sample requests, one batch of each
+        distinct key of which runs on the scheduler thread before it accepts
+        work (first launches from a thread pay one-time costs); their results
+        are dropped."""
+        self._prime = list(prime or [])
+        self._ready = threading.Event()
+        self._builder = threading.Thread(target=self._build_loop, daemon=True)
+        self._builder.start()
         self._thread = threading.Thread(target=self._loop, daemon=True)
         self._thread.start()
+        self._ready.wait()
 
     def stop(self):
         self._stop.set()
         if self._thread is not None:
             self._thread.join()
+        if self._builder is not None:
+            self._build_q.put(None)
+            self._builder.join()
 
     # ---------------------------------------------------------------- loop
     def _loop(self):
         try:
+            torch.cuda.set_device(self.device)
+            seen = set()
+            for r in self._prime:
+                if r.key in seen:
+                    continue
+                seen.add(r.key)
+                for stream in self.streams:
+                    runner = self._free_runner(r.key, 1) or self._runner(r.key, 1)
+                    runner.launch([r], stream)
+                    runner.event.synchronize()
+                    runner.outputs = None
+            self._ready.set()
             self._run()
         except BaseException as exc:  # never leave callers waiting on a dead loop
+            self._ready.set()
             pending = [r for _, rs in self.inflight for r in rs] + [r for q in self.waiting.values() for r in q]
             while not self.inbox.empty():
                 pending.append(self.inbox.get_nowait())
@@ -312,6 +391,7 @@ class Server:
         torch.cuda.set_device(self.device)
         while not self._stop.is_set() or self.inflight or any(self.waiting.values()) or not self.inbox.empty():
             self._drain_inbox()
+            self._take_built()
             self._complete()
             launched = self._schedule()
             if not launched and not self.inflight:
@@ -354,6 +434,10 @@ class Server:
             if need > free and self.inflight:
                 continue
             if runner is None:
+                if self.inflight:
+                    # built on the builder thread; meanwhile smaller batches, or wait for a free runner
+                    self._request_build(key, slots)
+                    continue
                 runner = self._runner(key, slots)
             elif runner.rast.capacity < self._capacity(key, slots, headroom=1.0):
                 # the pair demand seen for this key outgrew the runner: grow it
