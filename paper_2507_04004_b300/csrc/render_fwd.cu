@@ -42,14 +42,19 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   // pixels run in vertical pairs (k = 2h, 2h + 1) through packed FP32 pairs
   constexpr int NP = PPT / 2;
   float2 T[NP], C0[NP], C1[NP], C2[NP], D[NP], Y[NP];
+  // per-pixel alpha threshold in log2: log2(alpha_min) while the pixel
+  // blends, +inf once it is done (or outside the image), so that one
+  // comparison decides whether a Gaussian takes part at the pixel
+  float thr[PPT];
   uint32_t last[PPT];
-  bool done[PPT];
   bool all_done = true;
+  const float inf = __int_as_float(0x7f800000);
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     last[k] = 0;
-    done[k] = !(x < ws.width && yb + k < ws.height);
-    all_done &= done[k];
+    const bool out = !(x < ws.width && yb + k < ws.height);
+    thr[k] = out ? inf : lt;
+    all_done &= out;
   }
 #pragma unroll
   for (int h = 0; h < NP; ++h) {
@@ -89,19 +94,18 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
       const float4 c = s_c[j];
       const float2 cr = f2(c.x), cg = f2(c.y), cb = f2(c.z), dep = f2(g1.z);
       const uint32_t nxt = b0 + j + 1;
-      all_done = true;
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
         // a pixel blends this Gaussian unless it is done, below alpha_min, or
         // would drop under t_min (then it is done and this Gaussian is not blended)
         const float2 p2 = col_p2x2(ct, Y[h]);
-        const bool a0 = !done[2 * h] & (p2.x >= lt), a1 = !done[2 * h + 1] & (p2.y >= lt);
+        const bool a0 = p2.x >= thr[2 * h], a1 = p2.y >= thr[2 * h + 1];
         const float2 al = make_float2(fminf(a_max, ex2_approx(p2.x)), fminf(a_max, ex2_approx(p2.y)));
         const float2 Tc = mul2(T[h], fma2(al, f2(-1.f), f2(1.f)));
         const bool s0 = a0 & (Tc.x < t_min), s1 = a1 & (Tc.y < t_min);
         const bool k0 = a0 & !s0, k1 = a1 & !s1;
-        done[2 * h] |= s0;
-        done[2 * h + 1] |= s1;
+        thr[2 * h] = s0 ? inf : thr[2 * h];
+        thr[2 * h + 1] = s1 ? inf : thr[2 * h + 1];
         // alpha of a blended pixel, 0 otherwise: T (1 - 0) = T leaves the others as they are
         const float2 ak = make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f);
         const float2 w = mul2(ak, T[h]);
@@ -112,7 +116,13 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
         T[h] = mul2(T[h], fma2(ak, f2(-1.f), f2(1.f)));
         last[2 * h] = k0 ? nxt : last[2 * h];
         last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
-        all_done &= done[2 * h] & done[2 * h + 1];
+      }
+      // the thread leaves once all its pixels are done, checked every 8
+      // Gaussians (a done pixel takes no part in the ones in between)
+      if ((j & 7u) == 7u || j + 1 == nb) {
+        all_done = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) all_done &= thr[k] == inf;
       }
     }
     // pixels whose list ended are done only when the whole list is walked
