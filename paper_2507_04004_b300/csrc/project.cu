@@ -29,7 +29,8 @@
 namespace gsb {
 
 constexpr int kMaxBuckets = 4096;  // buckets counted in shared memory (else global atomics)
-constexpr int kMaxWindow = 2048;   // tiles of one CTA's row window kept in shared memory (two rows of 8K pixels)
+constexpr int kMaxWindow = 2048;
+constexpr int kScatterThreads = 512;   // tiles of one CTA's row window kept in shared memory (two rows of 8K pixels)
 
 template <int DEG, bool BF16>
 __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera* __restrict__ cams, gs_config cfg,
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
 // Row items grouped by bucket.  Each CTA takes a contiguous range of the
 // visible list, counts its items per bucket, reserves one range per bucket
 // and fills it.
-__global__ void __launch_bounds__(256) k_scatter_rows(Ws ws) {
+__global__ void __launch_bounds__(kScatterThreads) k_scatter_rows(Ws ws) {
   __shared__ uint32_t s_cnt[kMaxBuckets];
   __shared__ uint32_t s_base[kMaxBuckets];
   if (ws.counters[kStatus] != 0) return;
@@ -469,8 +470,10 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_co
 cudaError_t launch_rows(const Ws& ws, int phase, cudaStream_t st) {
   const unsigned grid = (unsigned)(sm_count() * 8 < kRowsGridMax ? sm_count() * 8 : kRowsGridMax);
   if (phase == 0) {
+    // large CTAs: each reserves its ranges once per bucket it touches, and the
+    // visible list mixes views, so fewer CTAs mean fewer reservations
     trace_begin(kKScatterRows, st);
-    k_scatter_rows<<<grid, 256, 0, st>>>(ws);
+    k_scatter_rows<<<(unsigned)sm_count() * 2, kScatterThreads, 0, st>>>(ws);
   } else if (phase == 1) {
     trace_begin(kKRowsCount, st);
     k_rows_count<<<grid, 256, 0, st>>>(ws);
