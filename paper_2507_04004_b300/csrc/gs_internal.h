@@ -65,8 +65,7 @@ cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, cons
 // Per-Gaussian (bucket) backward: the checkpoints written by the forward, in
 // one caller buffer of bucket_ws_bytes(ws) bytes.
 struct BucketWs {
-  float* ckpt;   // [nbuckets][5][256]: T, C_r, C_g, C_b, D at each bucket start
-  int64_t nbuckets;
+  float* ckpt;   // [cap / 32 + V*T + 1][5][256]: T, C_r, C_g, C_b, D at each bucket start
 };
 size_t bucket_ws_bytes(const Ws& ws);
 BucketWs resolve_bucket_ws(const Ws& ws, void* ptr);

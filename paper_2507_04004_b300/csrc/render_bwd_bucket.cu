@@ -33,9 +33,9 @@ size_t bucket_ws_bytes(const Ws& ws) {
 }
 
 BucketWs resolve_bucket_ws(const Ws& ws, void* ptr) {
+  (void)ws;
   BucketWs b;
   b.ckpt = static_cast<float*>(ptr);
-  b.nbuckets = ws.cap / 32 + (int64_t)ws.views * ws.tiles_per_view + 1;
   return b;
 }
 

@@ -58,3 +58,32 @@ def test_results_alone_equal_results_in_the_mix(use_graphs):
             scale = np.abs(alone["J"]).max()
             assert np.abs(got["J"] - alone["J"]).max() <= 1e-3 * scale
             np.testing.assert_allclose(got["residual"], alone["rgb"] - r.target, atol=1e-6)
+
+
+def test_runners_built_while_serving_give_the_same_results():
+    """Warm-up without multi-view runners, then a burst of one request kind:
+    the runners for larger batches are created while batches are in flight
+    (on the builder thread), and every result still equals the request
+    rendered alone."""
+    from paper_2507_04004_b300.raster import GaussianMap
+    from paper_2507_04004_b300.serve import PlainRenderer, Request, Server
+    rng = np.random.default_rng(2)
+    lo, hi = (-6.0, -2.0, -6.0), (6.0, 2.0, 6.0)
+    g = synth.random_map(rng, 30000, lo, hi, 3, log_scale_mean=-2.3)
+    gm = GaussianMap.from_host(g, sh_bf16=True)
+    reqs = []
+    for centre, Rc in synth.tracking_poses(rng, 40, lo, hi):
+        R, t = synth.pose_from_centre(Rc, centre)
+        reqs.append(Request("render", synth.camera(R, t, 190.0, 190.0, 160, 88, 320, 176)))
+    srv = Server(gm, mem_budget=1 << 30, max_views=4, n_streams=3, pairs_per_pixel=6.0)
+    srv.calibrate(reqs[:2])
+    srv.warmup({reqs[0].key}, copies=0)  # two single-view runners only
+    srv.start(prime=reqs[:1])
+    futs = [srv.submit(r) for r in reqs]
+    res = [f.result(timeout=120) for f in futs]
+    srv.stop()
+    assert srv.runners_added >= 1 and any(s > 1 for *_, s in srv.added_keys)
+    plain = PlainRenderer(gm)
+    for r, got in zip(reqs, res):
+        alone = plain.run(r)
+        assert np.array_equal(got["rgb"], alone["rgb"]) and np.array_equal(got["depth"], alone["depth"])
