@@ -72,8 +72,11 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int la
   return z;
 }
 
-template <bool FUSED, int PPT>
-__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+// DEP: the pixel adjoints of depth and opacity may be nonzero (a depth loss or
+// the caller's depth / opacity adjoints); without them (colour-only losses,
+// e.g. tracking) they and their terms are left out at compile time.
+template <bool FUSED, bool DEP, int PPT>
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
       gC1[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
       r = a.rgb[(3 * (int64_t)v + 2) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 2) * HW + p];
       gC2[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
-      if (a.tgt_depth && a.w_depth != 0.f) {
+      if (DEP && a.tgt_depth && a.w_depth != 0.f) {
         const float ds = a.tgt_depth[v * HW + p];
         const float O = a.opac[v * HW + p], Dp = a.depth[v * HW + p];
         const float nd = ws.view_stats[4 * v + 1];
@@ -144,16 +147,16 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
         gC1[k] += a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
         gC2[k] += a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
       }
-      if (a.dl_ddepth) gD[k] += a.dl_ddepth[v * HW + p];
-      if (a.dl_dopac) gO[k] += a.dl_dopac[v * HW + p];
+      if (DEP && a.dl_ddepth) gD[k] += a.dl_ddepth[v * HW + p];
+      if (DEP && a.dl_dopac) gO[k] += a.dl_dopac[v * HW + p];
     } else {
       if (a.dl_drgb) {
         gC0[k] = a.dl_drgb[(3 * (int64_t)v + 0) * HW + p];
         gC1[k] = a.dl_drgb[(3 * (int64_t)v + 1) * HW + p];
         gC2[k] = a.dl_drgb[(3 * (int64_t)v + 2) * HW + p];
       }
-      if (a.dl_ddepth) gD[k] = a.dl_ddepth[v * HW + p];
-      if (a.dl_dopac) gO[k] = a.dl_dopac[v * HW + p];
+      if (DEP && a.dl_ddepth) gD[k] = a.dl_ddepth[v * HW + p];
+      if (DEP && a.dl_dopac) gO[k] = a.dl_dopac[v * HW + p];
     }
     mx = max(mx, last[k]);
     S[k] = gC0[k] * cfg.bg[0] + gC1[k] * cfg.bg[1] + gC2[k] * cfg.bg[2];
@@ -256,11 +259,12 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 16 : 2048 / (256 / PPT) 
         // transmittance in front of this Gaussian
         T2[h] = mul2(T2[h], make_float2(a0 ? __fdividef(1.f, om.x) : 1.f, a1 ? __fdividef(1.f, om.y) : 1.f));
         const float2 w = mul2(al, T2[h]);
-        const float2 gx = fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, fma2(GD[h], dep, GO[h]))));
+        const float2 gx = DEP ? fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, fma2(GD[h], dep, GO[h]))))
+                              : fma2(C0[h], cr, fma2(C1[h], cg, mul2(C2[h], cb)));
         const float2 e = fma2(S2[h], f2(-1.f), gx);
         const float2 dA = mul2(T2[h], e);  // dL/dalpha
         S2[h] = fma2(al, e, S2[h]);
-        v6 = fma2(GD[h], w, v6);
+        if (DEP) v6 = fma2(GD[h], w, v6);
         v7 = fma2(C0[h], w, v7);
         v8 = fma2(C1[h], w, v8);
         v9 = fma2(C2[h], w, v9);
@@ -648,9 +652,15 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
   if (err != cudaSuccess) return err;
   const bool fused = a.tgt_rgb != nullptr;
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  const bool dep = (fused && a.tgt_depth && a.w_depth != 0.f) || a.dl_ddepth || a.dl_dopac;
   trace_begin(kKRenderBwd, st);
-  if (fused) k_render_bwd<true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
-  else k_render_bwd<false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  if (fused) {
+    if (dep) k_render_bwd<true, true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+    else k_render_bwd<true, false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  } else {
+    if (dep) k_render_bwd<false, true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+    else k_render_bwd<false, false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  }
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   return launch_preprocess_bwd(map, cams, cfg, ws, a, st);
