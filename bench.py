@@ -682,7 +682,7 @@ def run_ours(args):
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     n_sm = torch.cuda.get_device_properties(d.dev).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOP
-    # algorithmic counts per launch ("Roofline accounting")
+    # algorithmic bytes (HBM-bound kernels) or FP32 FLOP (blend kernels) per launch, from the work counters
     sh_bytes = 4 * 3 * (WORKLOAD["sh_degree"] + 1) ** 2
     V = args.views
     alg = {
@@ -690,7 +690,7 @@ def run_ours(args):
         "rows_emit": ("hbm", n_pairs * 8 + n_rows * (8 + 4 + 16)),
         "rows_count": ("hbm", n_rows * (8 + 32 + 4)),
         "sort_small": ("hbm", n_pairs * (8 + 4)),
-        # FP32 FLOP per (pixel, list position up to its last contributor), FMA = 2 (roofline):
+        # FP32 FLOP per (pixel, list position up to its last contributor), FMA = 2:
         # forward: weight 6, exp2 1, clamp 1, transmittance 2, w 1, colour+depth 8  -> 19
         # backward: weight 6, exp2 1, clamp 1, 1-alpha 1, T recovery 1, w 1, adjoint dot 8,
         #           dL/dalpha 2, behind-sum 2, colour+depth sums 8, dL/dpower 1, moments 11 -> 43
