@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-bucket", action="store_true", help="skip the per-Gaussian (bucket) backward leg")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
+    p.add_argument("--reference-seconds", type=float, default=150.0,
+                   help="--impl reference: oracle time spread over the warm-up and timed steps")
     p.add_argument("--tracking-frames", type=int, default=32,
                    help="frames in the tracking measurement (0 skips it): 1M Gaussians SH1, 640x512, N_t = 30")
     p.add_argument("--serving-requests", type=int, default=2000,
@@ -239,7 +241,7 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     w = make_workload(args.n)
-    budget = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    budget = max(0.5, args.reference_seconds / max(1, args.steps + args.warmup))
     cal = {}
     for _ in range(args.warmup):
         oracle_sample(w, budget, cal)

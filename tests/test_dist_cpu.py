@@ -50,3 +50,24 @@ def test_reference_arm_non_zero_rank_exits_without_work(monkeypatch):
     class A:
         steps, warmup, n = 1, 1, 10
     assert bench.run_reference(A()) == 0
+
+
+def test_reference_arm_prints_its_json_line():
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys; a small map and a few seconds of oracle
+    time keep the test short."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "20000", "--steps", "2",
+                        "--warmup", "1", "--reference-seconds", "3"], cwd=root, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "Mpix/s" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
