@@ -319,20 +319,23 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
 // partials are reduced per view across the CTA.
 constexpr int kPoseSmemViews = 256;  // per-CTA pose sums in shared memory up to this many views
 
-template <int DEG, bool BF16>
+// PARAMS: parameter gradients are wanted; without them (the pose gradient
+// alone, the map held fixed) their accumulation is left out at compile time.
+template <int DEG, bool BF16, bool PARAMS>
 __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_camera* __restrict__ cams,
                                                         gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   // SH gradient accumulators and the Gaussian's SH coefficients live in
   // shared memory (one column per thread): coefficients are fetched once, with
   // independent coalesced loads, and reused by every view
-  // (dynamic shared memory: 2 * 3K * 256 floats, up to 96 KB)
+  // (dynamic shared memory: 3K * 256 floats each, up to 48 KB; the gradient
+  // columns only when parameter gradients are wanted)
   extern __shared__ float s_dyn[];
   float(*s_gsh)[256] = reinterpret_cast<float(*)[256]>(s_dyn);
-  float(*s_sh)[256] = reinterpret_cast<float(*)[256]>(s_dyn + 3 * K * 256);
+  float(*s_sh)[256] = reinterpret_cast<float(*)[256]>(s_dyn + (PARAMS ? 3 * K * 256 : 0));
   // per-view pose sums of the CTA (6 V floats after the SH columns), added to
   // the global pose gradient once per CTA; with more views, global atomics
-  float* s_pose = s_dyn + 2 * 3 * K * 256;
+  float* s_pose = s_dyn + (PARAMS ? 2 : 1) * 3 * K * 256;
   const int64_t n = ws.n;
   if (ws.counters[kStatus] != 0) return;
   // one thread per Gaussian of the list of those seen by some view, so that
@@ -373,7 +376,8 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
 
   float g_mu[3] = {0.f, 0.f, 0.f}, g_s[3] = {0.f, 0.f, 0.f}, g_R[3][3] = {{0.f}}, g_o = 0.f;
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) s_gsh[k][threadIdx.x] = 0.f;
+  for (int k = 0; k < 3 * K; ++k)
+    if (PARAMS) s_gsh[k][threadIdx.x] = 0.f;
 
   // The per-(Gaussian, view) chain rule; pose[] receives this view's
   // contribution to the pose gradient.
@@ -426,10 +430,10 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
     float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
+      if (PARAMS) g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
+        if (PARAMS) g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
         gm0[i] += s[k] * gU[k] * Rg[i][k];
         gm1[i] += s[k] * gV[k] * Rg[i][k];
       }
@@ -469,7 +473,8 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
       for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
       graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
+      for (int k = 0; k < K; ++k)
+        if (PARAMS) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
     }
     // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
     float wk[16];
@@ -484,8 +489,9 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
     const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
     const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) g_mu[j] += gWm[j] + gv[j];
-    g_o += gop;
+    for (int j = 0; j < 3; ++j)
+      if (PARAMS) g_mu[j] += gWm[j] + gv[j];
+    if (PARAMS) g_o += gop;
     // consume: leave the adjoint area zero for the next backward of this projection
     ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (want_pose) {
@@ -557,7 +563,7 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
     for (int i = threadIdx.x; i < 6 * ws.views; i += blockDim.x)
       if (s_pose[i] != 0.f) atomicAdd(a.grad_pose + i, s_pose[i]);
   }
-  if (!any || !a.grad_mean) return;  // no parameter gradients wanted: pose only
+  if (!PARAMS || !any) return;  // no parameter gradients wanted: pose only
   // quaternion: R(q^) entries -> q^ -> q (normalisation)
   const float gw = 2.f * (-qz * g_R[0][1] + qy * g_R[0][2] + qz * g_R[1][0] - qx * g_R[1][2] - qy * g_R[2][0] +
                           qx * g_R[2][1]);
@@ -605,18 +611,26 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   }
 }
 
+template <int DEG, bool BF16, bool PARAMS>
+static cudaError_t launch_pre_bwd_t(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
+                                    const BwdArgs& a, cudaStream_t st) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const size_t smem =
+      ((size_t)(PARAMS ? 2 : 1) * 3 * K * 256 + (ws.views <= kPoseSmemViews ? 6 * ws.views : 0)) * sizeof(float);
+  cudaError_t err = cudaFuncSetAttribute(k_preprocess_bwd<DEG, BF16, PARAMS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  trace_begin(kKPreprocessBwd, st);
+  k_preprocess_bwd<DEG, BF16, PARAMS><<<(unsigned)((ws.n + 255) / 256), 256, smem, st>>>(map, cams, cfg, ws, a);
+  trace_end(st);
+  return cudaGetLastError();
+}
+
 template <int DEG, bool BF16>
 static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                   const BwdArgs& a, cudaStream_t st) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  const size_t smem = ((size_t)2 * 3 * K * 256 + (ws.views <= kPoseSmemViews ? 6 * ws.views : 0)) * sizeof(float);
-  cudaError_t err =
-      cudaFuncSetAttribute(k_preprocess_bwd<DEG, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  trace_begin(kKPreprocessBwd, st);
-  k_preprocess_bwd<DEG, BF16><<<(unsigned)((ws.n + 255) / 256), 256, smem, st>>>(map, cams, cfg, ws, a);
-  trace_end(st);
-  return cudaGetLastError();
+  return a.grad_mean ? launch_pre_bwd_t<DEG, BF16, true>(map, cams, cfg, ws, a, st)
+                     : launch_pre_bwd_t<DEG, BF16, false>(map, cams, cfg, ws, a, st);
 }
 
 cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st) {

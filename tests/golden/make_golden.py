@@ -6,7 +6,8 @@ The scene is built by hand: three overlapping Gaussians at different depths
 rotated), SH degree 1, seen by a slightly rotated camera of 24 x 20 pixels (two
 tiles across and two down, both ragged). The expected values are the FP64
 oracle's image (Eq. alpha, Eq. rendered_rgb, rendered_depth, rendered_opacity),
-its per-pixel decision flags, and the loss and gradients of the fused loss of
+each pixel's number of blended Gaussians and last blended Gaussian, its
+per-pixel decision flags, and the loss and gradients of the fused loss of
 Eq. depth_loss (0.8 L1 colour + 0.2 opacity-normalised L1 depth on four LiDAR
 pixels), including the pose gradient of Eq. 3dgs_jacobi.
 
@@ -66,7 +67,7 @@ def compute():
     r = O.render(hm, cam)
     b = O.backward(hm, [cam], tgt_rgb=tr, tgt_depth=td, w_rgb=0.8, w_depth=0.2)
     return dict(rgb=r["rgb"], depth=r["depth"], opac=r["opac"], t_final=r["t_final"], n_contrib=r["n_contrib"],
-                flags=r["flags"], loss=b["loss"], grad_mean=b["mean"], grad_log_scale=b["log_scale"],
+                last_gid=r["last_gid"], flags=r["flags"], loss=b["loss"], grad_mean=b["mean"], grad_log_scale=b["log_scale"],
                 grad_quat=b["quat"], grad_logit_opacity=b["logit_opacity"], grad_sh_dc=b["sh_dc"],
                 grad_sh_rest=b["sh_rest"], grad_pose=b["pose"])
 

@@ -23,7 +23,7 @@ def _expected():
 def test_oracle_reproduces_the_golden_fixture(oracle):
     exp, got = _expected(), compute()
     for k, v in exp.items():
-        if k in ("n_contrib", "flags"):
+        if k in ("n_contrib", "last_gid", "flags"):
             np.testing.assert_array_equal(got[k], v, err_msg=k)
         else:  # gradient sums may be added in another order by the oracle's threads
             np.testing.assert_allclose(got[k], v, rtol=1e-10, atol=1e-15, err_msg=k)
@@ -44,7 +44,14 @@ def test_cuda_path_matches_the_golden_fixture():
     np.testing.assert_allclose(out.rgb[0].cpu().numpy()[:, ok], exp["rgb"][:, ok], atol=1e-4)
     np.testing.assert_allclose(out.opac[0].cpu().numpy()[ok], exp["opac"][ok], atol=1e-4)
     np.testing.assert_allclose(out.depth[0].cpu().numpy()[ok], exp["depth"][ok], atol=1e-4 * max(1.0, exp["depth"].max()))
-    np.testing.assert_array_equal(out.n_contrib[0].cpu().numpy()[ok], exp["n_contrib"][ok])
+    # the last blended Gaussian: the GPU's n_contrib is 1 + its place in the tile's list
+    start, count, ids = (x.cpu().numpy() for x in rast.tile_lists())
+    nc = out.n_contrib[0].cpu().numpy()
+    tw = (cam["width"] + 15) // 16
+    ys, xs = np.nonzero(ok)
+    tiles = (ys // 16) * tw + xs // 16
+    last = np.where(nc[ys, xs] > 0, ids[start[tiles] + np.maximum(nc[ys, xs].astype(np.int64) - 1, 0)], -1)
+    np.testing.assert_array_equal(last, exp["last_gid"][ys, xs])
     t = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda")
     g = rast.backward(gm, ct, out, tgt_rgb=t(tgt_rgb), tgt_depth=t(tgt_depth), w_rgb=0.8, w_depth=0.2)
     assert float(g.loss[0]) == pytest.approx(float(exp["loss"][0]), rel=1e-4)
