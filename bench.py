@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-bucket", action="store_true", help="skip the per-Gaussian (bucket) backward leg")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
+    p.add_argument("--cpu-seconds-one-core", type=float, default=12.0,
+                   help="length of the one-core oracle sample beside the CPU baseline (0 skips it)")
     p.add_argument("--reference-seconds", type=float, default=150.0,
                    help="--impl reference: oracle time spread over the warm-up and timed steps")
     p.add_argument("--tracking-frames", type=int, default=32,
@@ -743,6 +745,15 @@ def run_ours(args):
         cpu = {"value": pix / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"view 0, centred {rect[2]}x{rect[3]} pixel rectangle, fwd+bwd in FP64 "
                          f"({secs:.1f} s)"}
+        if args.cpu_seconds_one_core > 0:
+            nt = O.threads()
+            O.set_threads(1)
+            try:
+                pix1, secs1, rect1 = oracle_sample(w, args.cpu_seconds_one_core)
+            finally:
+                O.set_threads(nt)
+            cpu["one_core"] = {"value": pix1 / secs1 / 1e6, "unit": "Mpix/s", "cores": 1,
+                               "sample": f"view 0, centred {rect1[2]}x{rect1[3]} pixel rectangle ({secs1:.1f} s)"}
     if d.rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": d.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,

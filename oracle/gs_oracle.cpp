@@ -52,6 +52,7 @@
  * mode with dual numbers (exact derivatives of the same FP64 forward code),
  * and so are the per-pixel pose Jacobian rows.
  */
+#include <omp.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -806,6 +807,10 @@ int32_t ocl_pose_jacobian(const ocl_map* m, const ocl_camera* cam, const ocl_con
   }
   return 0;
 }
+
+/* Worker threads of the parallel loops (timing on a given number of cores). */
+void ocl_set_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : 1); }
+int32_t ocl_get_threads() { return (int32_t)omp_get_max_threads(); }
 
 /* FP32 depth keys of every Gaussian in one view (ordering quantity). */
 void ocl_depth_keys(const ocl_map* m, const ocl_camera* cam, float* keys) {

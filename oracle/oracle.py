@@ -71,6 +71,8 @@ def _load():
                                          + [C.c_int32] * 4 + [P] * 8)
             lib.ocl_pose_jacobian.argtypes = [P, P, P, P, C.c_int32, P, P]
             lib.ocl_depth_keys.argtypes = [P, P, P]
+            lib.ocl_set_threads.argtypes = [C.c_int32]
+            lib.ocl_get_threads.restype = C.c_int32
             _lib = lib
     return _lib
 
@@ -239,3 +241,12 @@ def pose_jacobian(m, cam, pix, cfg=None):
     rgb = np.zeros((len(pix), 3))
     lib.ocl_pose_jacobian(C.byref(mh.s), C.byref(c), C.byref(k), _p(pix), len(pix), _p(J), _p(rgb))
     return J, rgb
+
+
+def set_threads(n: int) -> None:
+    """Number of threads the oracle's parallel loops use from now on."""
+    _load().ocl_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().ocl_get_threads())
