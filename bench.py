@@ -714,6 +714,19 @@ def run_ours(args):
                 "peak_source": ("FP32 FMA issue: %d SMs x 128 lanes x 2 FLOP x %.0f MHz median SM clock" %
                                 (n_sm, sm_mhz)) if bound == "alu" else f"{peaks['source']} HBM copy bandwidth"}
 
+    # every kernel with an algorithmic count against its own roof
+    per_kernel_roof = {}
+    for k, (bd, amt) in alg.items():
+        if k not in kernels or not amt:
+            continue
+        t_s = kernels[k]["ms_avg"] / 1e3
+        if bd == "hbm":
+            a_, p_, u_ = amt / t_s / 1e9, peaks["hbm_gbs"], "GB/s"
+        else:
+            a_, p_, u_ = amt / t_s / 1e12, fp32_peak, "TFLOP/s"
+        per_kernel_roof[k] = {"bound": bd, "achieved": round(a_, 3), "peak": round(p_, 2), "unit": u_,
+                              "frac": round(a_ / p_, 4), "traffic": traffic_for(k)}
+
     # end to end: host keyframes -> device, fwd+bwd, loss back to host
     e2e = None if args.no_e2e else run_e2e(args, d, rast, gm, w, px_step)
     total_px = d.sum(px_step * args.steps)
@@ -765,6 +778,7 @@ def run_ours(args):
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": roofline,
+                "roofline_per_kernel": per_kernel_roof,
                 "cpu_baseline": cpu,
                 "mapping_iteration": mapping_iter,
                 "bucket_backward": bucket,
