@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-bucket", action="store_true", help="skip the per-Gaussian (bucket) backward leg")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target length of the CPU baseline sample")
-    p.add_argument("--cpu-seconds-one-core", type=float, default=12.0,
+    p.add_argument("--cpu-seconds-one-core", type=float, default=4.0,
                    help="length of the one-core oracle sample beside the CPU baseline (0 skips it)")
     p.add_argument("--reference-seconds", type=float, default=150.0,
                    help="--impl reference: oracle time spread over the warm-up and timed steps")
