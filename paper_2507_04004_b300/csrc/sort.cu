@@ -343,7 +343,7 @@ __device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT,
 // persistent kMediumThreads-thread CTA over the medium list (filled from the
 // end of long_tiles), longer ones by k_sort_long.
 constexpr int kSmallThreads = 128, kSmallCap = 768;
-constexpr int kMediumThreads = 256, kMediumCap = 2048;
+constexpr int kMediumThreads = 512, kMediumCap = 2048;
 
 __global__ void __launch_bounds__(kSmallThreads) k_sort_small(Ws ws) {
   __shared__ RadixSmem<kSmallThreads, kSmallCap> sm;
@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(Ws ws) {
 }
 
 __global__ void __launch_bounds__(kMediumThreads) k_sort_medium(Ws ws) {
-  __shared__ RadixSmem<kMediumThreads, kMediumCap> sm;
+  // over 48 KB: dynamic shared memory (the launch raises the limit)
+  extern __shared__ __align__(16) unsigned char s_medium[];
+  auto& sm = *reinterpret_cast<RadixSmem<kMediumThreads, kMediumCap>*>(s_medium);
   if (ws.counters[kStatus] != 0) return;
   const int64_t ntiles = (int64_t)ws.views * ws.tiles_per_view;
   const uint32_t nm = ws.counters[kMediumCount];
@@ -467,8 +469,11 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   k_sort_small<<<ntiles, kSmallThreads, 0, st>>>(ws);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const int medium_smem = (int)sizeof(RadixSmem<kMediumThreads, kMediumCap>);
+  err = cudaFuncSetAttribute(k_sort_medium, cudaFuncAttributeMaxDynamicSharedMemorySize, medium_smem);
+  if (err != cudaSuccess) return err;
   trace_begin(kKSortMedium, st);
-  k_sort_medium<<<sm_count() * 4, kMediumThreads, 0, st>>>(ws);
+  k_sort_medium<<<sm_count() * 4, kMediumThreads, medium_smem, st>>>(ws);
   trace_end(st);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
