@@ -645,11 +645,15 @@ def run_ours(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     d.barrier()
     torch.cuda.synchronize()
+    # one event per step boundary as well, for the spread of the step times
+    bounds = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     N.gs_trace_start([e.cuda_event for e in evs], ids)
     t_wall0 = time.time()
     start.record()
-    for _ in range(args.steps):
+    bounds[0].record()
+    for i in range(args.steps):
         step()
+        bounds[i + 1].record()
     end.record()
     end.synchronize()
     launches = N.gs_trace_stop()
@@ -662,6 +666,9 @@ def run_ours(args):
     code, needed = rast.status()
     if code != 0:
         raise SystemExit(f"workspace status {code} in the timed region")
+
+    step_times = np.array([bounds[i].elapsed_time(bounds[i + 1]) for i in range(args.steps)])
+    step_pct = {q: round(float(np.percentile(step_times, int(q[1:]))), 4) for q in ("p10", "p50", "p90")}
 
     # per-kernel durations
     rec = min(launches, cap)
@@ -775,6 +782,7 @@ def run_ours(args):
                                parallelism=f"replicas x{d.world}" if d.world > 1 else "single GPU",
                                l2="inputs larger than L2: 236 MB of Gaussian parameters, 192 MB of projected records"),
                 "clocks": clocks,
+                "step_ms_percentiles": step_pct,
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": roofline,
