@@ -23,7 +23,9 @@ constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
 struct Win {
-  float w[2 * kR + 1];  // normalised 1D Gaussian; the 2D window is its outer product
+  // normalised 1D Gaussian (the 2D window is its outer product), each weight
+  // twice so that the packed FP32 pair instructions take it as it stands
+  float2 w[2 * kR + 1];
 };
 
 // Stage one plane over the tile and its 5-pixel halo (zero outside the
@@ -61,7 +63,7 @@ __device__ __forceinline__ void row_filter(const Win& win, F map_of, float (*out
       for (int o = 0; o < 4; ++o) {
         const int k = j - o;
         if (k >= 0 && k <= 2 * kR) {
-          const float2 wk = f2(win.w[k]);
+          const float2 wk = win.w[k];
 #pragma unroll
           for (int m = 0; m < NM; ++m) a[o][m] = fma2(wk, v[m], a[o][m]);
         }
@@ -95,7 +97,7 @@ __device__ __forceinline__ void col_filter(const Win& win, float (*in)[kS][kT], 
     for (int o = 0; o < 2; ++o) {
       const int k = i - o;
       if (k >= 0 && k <= 2 * kR) {
-        const float2 wk = f2(win.w[k]);
+        const float2 wk = win.w[k];
 #pragma unroll
         for (int m = 0; m < NM; ++m) res[o][m] = fma2(wk, v[m], res[o][m]);
       }
@@ -226,7 +228,7 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
     g[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
     sum += g[k];
   }
-  for (int k = 0; k <= 2 * kR; ++k) win.w[k] = (float)(g[k] / sum);
+  for (int k = 0; k <= 2 * kR; ++k) win.w[k] = make_float2((float)(g[k] / sum), (float)(g[k] / sum));
   float* dmaps = static_cast<float*>(scratch);
   float* ssim_sum = reinterpret_cast<float*>(static_cast<char*>(scratch) +
                                              (((size_t)V * 9 * H * W * sizeof(float) + 255) / 256) * 256);
