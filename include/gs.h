@@ -131,7 +131,9 @@ typedef struct {
 } gs_layout;
 
 /* Workspace bytes and layout for n Gaussians, a batch geometry and a pair
- * capacity.  Return 0 / GS_ERR_ARG on invalid sizes. */
+ * capacity.  Valid sizes: 1 <= n < 2^31, 1 <= pair_capacity < 2^31 (an empty
+ * map has nothing to project: its image is the background, which the caller
+ * fills without the library).  Return 0 / GS_ERR_ARG on invalid sizes. */
 size_t gs_workspace_size(int64_t n, const gs_frame* frame, int64_t pair_capacity);
 gs_status gs_workspace_layout(int64_t n, const gs_frame* frame, int64_t pair_capacity, gs_layout* out);
 
