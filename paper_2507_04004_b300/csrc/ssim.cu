@@ -28,18 +28,28 @@ struct Win {
   float2 w[2 * kR + 1];
 };
 
+// 4-byte asynchronous copy into shared memory, zero-filled when `in` is
+// false (no global byte is read then; `src` must still be a valid address).
+__device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool in) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+}
+
 // Stage one plane over the tile and its 5-pixel halo (zero outside the
 // image) with rows paired, s[i][c] = (v[2i][c], v[2i + 1][c]), so that the
-// row filter handles two rows per packed FP32x2 instruction.
+// row filter handles two rows per packed FP32x2 instruction.  The copies are
+// asynchronous (all of a thread's loads in flight at once); the caller waits
+// with cp_async_wait_all() and a barrier.
 __device__ __forceinline__ void stage_pairs(const float* __restrict__ plane, int H, int W, int x0, int y0,
                                             float2 (*s)[kS]) {
   for (int i = threadIdx.x; i < kS2 * kS; i += blockDim.x) {
     const int rp = i / kS, c = i - rp * kS;
     const int gx = x0 + c, gy = y0 + 2 * rp;
     const bool cx = gx >= 0 && gx < W;
-    const float a = (cx && gy >= 0 && gy < H) ? plane[(int64_t)gy * W + gx] : 0.f;
-    const float b = (cx && gy + 1 >= 0 && gy + 1 < H) ? plane[(int64_t)(gy + 1) * W + gx] : 0.f;
-    s[rp][c] = make_float2(a, b);
+    const bool ia = cx && gy >= 0 && gy < H, ib = cx && gy + 1 >= 0 && gy + 1 < H;
+    float* dst = reinterpret_cast<float*>(&s[rp][c]);
+    cp_async4_zfill(dst, ia ? plane + (int64_t)gy * W + gx : plane, ia);
+    cp_async4_zfill(dst + 1, ib ? plane + (int64_t)(gy + 1) * W + gx : plane, ib);
   }
 }
 
@@ -124,6 +134,8 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ i
   const int x0 = tx * kT - kR, y0 = ty * kT - kR;
   stage_pairs(img + plane * HW, H, W, x0, y0, s_x);
   stage_pairs(tgt + plane * HW, H, W, x0, y0, s_y);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   // window sums of x, y, x^2, y^2, x y
   row_filter<5>(win, [&](int rp, int c, float2* v) {
@@ -185,6 +197,8 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float* __restrict__ img,
   const int x0 = tx * kT - kR, y0 = ty * kT - kR;
 #pragma unroll
   for (int q = 0; q < 3; ++q) stage_pairs(d + q * HW, H, W, x0, y0, s_d[q]);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   row_filter<3>(win, [&](int rp, int c, float2* v) {
     v[0] = s_d[0][rp][c]; v[1] = s_d[1][rp][c]; v[2] = s_d[2][rp][c];
