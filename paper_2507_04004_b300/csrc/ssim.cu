@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ i
                                                   int H, int W, Win win, float* __restrict__ dmaps,
                                                   float* __restrict__ ssim_sum) {
   __shared__ float2 s_x[kS2][kS], s_y[kS2][kS];
-  __shared__ __align__(16) float s_h[5][kS][kT];
+  __shared__ __align__(16) float s_h[4][kS][kT];
   __shared__ float s_red[8];
   const int tiles_x = (W + kT - 1) / kT;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
@@ -137,14 +137,15 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ i
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  // window sums of x, y, x^2, y^2, x y
-  row_filter<5>(win, [&](int rp, int c, float2* v) {
+  // window sums of x, y, x^2 + y^2, x y: SSIM takes the two variances only as
+  // their sum, so their second moments are filtered together
+  row_filter<4>(win, [&](int rp, int c, float2* v) {
     const float2 xv = s_x[rp][c], yv = s_y[rp][c];
-    v[0] = xv; v[1] = yv; v[2] = mul2(xv, xv); v[3] = mul2(yv, yv); v[4] = mul2(xv, yv);
+    v[0] = xv; v[1] = yv; v[2] = fma2(xv, xv, mul2(yv, yv)); v[3] = mul2(xv, yv);
   }, s_h);
   __syncthreads();
-  float2 m[2][5];
-  col_filter<5>(win, s_h, m);
+  float2 m[2][4];
+  col_filter<4>(win, s_h, m);
   float local = 0.f;
   const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
   float* d = dmaps + (int64_t)plane * 3 * HW;
@@ -155,11 +156,11 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ i
       const int gy = ty * kT + r0 + o, gx = tx * kT + c + hx;
       if (gy >= H || gx >= W) continue;
       const float mx = hx ? m[o][0].y : m[o][0].x, my = hx ? m[o][1].y : m[o][1].x;
-      const float exx = hx ? m[o][2].y : m[o][2].x, eyy = hx ? m[o][3].y : m[o][3].x;
-      const float exy = hx ? m[o][4].y : m[o][4].x;
-      const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+      const float ess = hx ? m[o][2].y : m[o][2].x;  // window sum of x^2 + y^2
+      const float exy = hx ? m[o][3].y : m[o][3].x;
+      const float sxy = exy - mx * my;
       const float a1 = 2.f * mx * my + kC1, a2 = 2.f * sxy + kC2;
-      const float b1 = mx * mx + my * my + kC1, b2 = sxx + syy + kC2;
+      const float b1 = mx * mx + my * my + kC1, b2 = ess - mx * mx - my * my + kC2;  // s_xx + s_yy + C2
       const float ib = 1.f / (b1 * b2);
       const float sv = a1 * a2 * ib;
       const float ds_dmx = 2.f * my * a2 * ib - sv * 2.f * mx / b1;
