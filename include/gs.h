@@ -241,8 +241,11 @@ gs_status gs_pose_jacobian(const gs_map* map, const gs_camera* cams_dev, const g
  * dl_dimg [V][3][H][W] (may be NULL; e.g. the buffer later passed to
  * gs_render_bwd as dl_drgb).  scratch: caller-owned device buffer of
  * gs_dssim_scratch_bytes(V, H, W) bytes, 256-byte aligned, overwritten.
+ * With W % 4 == 0 and 16-byte aligned img, tgt and dl_dimg the tiles are
+ * staged by TMA, otherwise element by element (same results, bit for bit).
  * GS_ERR_ARG for missing pointers or sizes, GS_ERR_UNSUPPORTED for more than
- * 21845 views. */
+ * 21845 views.  A tile copy whose bounded (1 s) wait runs out, which is not
+ * expected, leaves NaN in the view's loss or the tile's dl_dimg. */
 size_t gs_dssim_scratch_bytes(int32_t n_views, int32_t height, int32_t width);
 gs_status gs_dssim(const float* img, const float* tgt, int32_t n_views, int32_t height, int32_t width, float weight,
                    float* loss, float* dl_dimg, void* scratch, gs_stream_t stream);

@@ -4,10 +4,21 @@
 // under an 11 x 11 Gaussian window (sigma 1.5, zero padding at the borders,
 // C1 = 0.01^2, C2 = 0.03^2) and D = 1 - mean SSIM over a view.  Sec.
 // "Additional Strategies" (c) computes it with separable Gaussian filters;
-// so does this file: each 32 x 32 output tile stages its inputs with a 5-pixel
-// halo in shared memory, filters rows then columns, and the backward pass
-// filters the three per-pixel derivative maps the forward pass leaves behind.
+// so does this file.  Each CTA owns a 48-wide, 32-tall output tile of one
+// channel plane:
+//   1. the tile's inputs with their 5-pixel halo arrive in shared memory as
+//      one TMA box per plane (zero outside the image, filled by the copy
+//      engine), or by cp.async where the image rows are not 16-byte strided;
+//   2. the vertical filter runs down the staged columns on horizontal pixel
+//      pairs (packed FP32x2) and leaves its sums interleaved by row pairs;
+//   3. the horizontal filter runs along those on vertical pixel pairs, and
+//      the same thread finishes its 8 pixels (SSIM and its derivative maps
+//      in the forward pass, the image gradient in the backward pass, whose
+//      per-pixel operands a second TMA copy brings in meanwhile).
 #include <cmath>
+#include <cstring>
+
+#include <cuda.h>
 
 #include "gs_internal.h"
 
@@ -15,12 +26,50 @@ namespace gsb {
 
 namespace {
 
-constexpr int kT = 32;             // output tile edge
+constexpr int kTW = 48;            // output tile width
+constexpr int kTH = 32;            // output tile height
 constexpr int kR = 5;              // window radius
-constexpr int kS = kT + 2 * kR;    // staged edge (42)
-constexpr int kS2 = kS / 2;        // staged row pairs (21)
+constexpr int kThreads = 256;
+// Staged box: columns tx*48 - 8 .. tx*48 + 55 (the left edge on a 16-byte
+// boundary, as TMA requires; the filters use columns 3 .. 60 of the box),
+// rows ty*32 - 5 .. ty*32 + 36.
+constexpr int kBX = 64;
+constexpr int kBY = kTH + 2 * kR;  // 42
+constexpr int kBXOff = 8;
+// Vertical filter: lanes 0..29 of warp w take the column pair (2 + 2 lane,
+// 3 + 2 lane) of the box and output rows 4w .. 4w + 3.
+constexpr int kVPairs = 30;
+constexpr int kVRows = kTH / (kThreads / 32);  // 4
+// Its sums: hp[m][i][k] = (row 2i, row 2i + 1) at box column k + 2; the odd
+// row stride keeps the horizontal filter's loads free of bank conflicts.
+constexpr int kHP = 61;
+// Horizontal filter: thread it < 192 takes row pair it % 16 and columns
+// 4 (it / 16) .. 4 (it / 16) + 3.
+constexpr int kHItems = (kTH / 2) * (kTW / 4);  // 192
+// Backward operand boxes (x, y, dl_dimg over the output tile), 52 columns
+// wide so that the epilogue's row reads fall on distinct banks.
+constexpr int kEX = 52;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
+constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a TMA wait (1 s)
+
+static_assert(kVRows == 4 && kTH == 32 && kTW == 48, "tile shape");
+static_assert(kBX >= kBXOff + kTW + kR && 2 + 2 * kVPairs <= kBX, "box covers the window");
+static_assert(kHP >= 2 * kVPairs && 4 * (kTW / 4 - 1) + 1 + 13 < 2 * kVPairs, "horizontal filter reads");
+
+constexpr size_t kPlaneBytes = (size_t)kBX * kBY * sizeof(float);  // 10752, a multiple of 128
+constexpr size_t kHpBytes = (size_t)(kTH / 2) * kHP * sizeof(float2);
+constexpr size_t kEpBytes = (size_t)kTH * kEX * sizeof(float);
+// forward: staged x, y | hp[4] | reduction | barrier
+constexpr size_t kFwdHp = 2 * kPlaneBytes;
+constexpr size_t kFwdRed = kFwdHp + 4 * kHpBytes;
+constexpr size_t kFwdBar = (kFwdRed + 8 * sizeof(float) + 15) / 16 * 16;
+constexpr size_t kFwdSmem = kFwdBar + 16 + 128;  // + alignment slack of the dynamic base
+// backward: staged D1, D2, D3 (then x, y, dl_dimg in their place) | hp[3] | barriers
+constexpr size_t kBwdHp = 3 * kPlaneBytes;
+constexpr size_t kBwdBar = kBwdHp + 3 * kHpBytes;
+constexpr size_t kBwdSmem = kBwdBar + 16 + 128;
+static_assert(kPlaneBytes % 128 == 0 && kEpBytes % 128 == 0 && 3 * kEpBytes <= 3 * kPlaneBytes, "staging layout");
 
 struct Win {
   // normalised 1D Gaussian (the 2D window is its outer product), each weight
@@ -28,84 +77,169 @@ struct Win {
   float2 w[2 * kR + 1];
 };
 
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for phase `parity` of the barrier; false once kWaitNs has passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// One box of a [planes][H][W] FP32 tensor map at (x, y, plane) into shared
+// memory, completing its bytes on the barrier (out-of-image elements read 0).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Order the block's earlier shared-memory accesses (this thread's, and after
+// a barrier everyone's) before later async-proxy (TMA) writes to the same bytes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // 4-byte asynchronous copy into shared memory, zero-filled when `in` is
 // false (no global byte is read then; `src` must still be a valid address).
 __device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool in) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(in ? 4 : 0)
+               : "memory");
 }
 
-// Stage one plane over the tile and its 5-pixel halo (zero outside the
-// image) with rows paired, s[i][c] = (v[2i][c], v[2i + 1][c]), so that the
-// row filter handles two rows per packed FP32x2 instruction.  The copies are
-// asynchronous (all of a thread's loads in flight at once); the caller waits
-// with cp_async_wait_all() and a barrier.
-__device__ __forceinline__ void stage_pairs(const float* __restrict__ plane, int H, int W, int x0, int y0,
-                                            float2 (*s)[kS]) {
-  for (int i = threadIdx.x; i < kS2 * kS; i += blockDim.x) {
-    const int rp = i / kS, c = i - rp * kS;
-    const int gx = x0 + c, gy = y0 + 2 * rp;
-    const bool cx = gx >= 0 && gx < W;
-    const bool ia = cx && gy >= 0 && gy < H, ib = cx && gy + 1 >= 0 && gy + 1 < H;
-    float* dst = reinterpret_cast<float*>(&s[rp][c]);
-    cp_async4_zfill(dst, ia ? plane + (int64_t)gy * W + gx : plane, ia);
-    cp_async4_zfill(dst + 1, ib ? plane + (int64_t)(gy + 1) * W + gx : plane, ib);
+// The same box as tma_load_3d, element by element (rows of any stride).
+template <int BX, int BY>
+__device__ __forceinline__ void copy_box(const float* __restrict__ plane, int H, int W, int gx0, int gy0, float* dst) {
+  for (int e = threadIdx.x; e < BX * BY; e += kThreads) {
+    const int r = e / BX, s = e - r * BX;
+    const int gx = gx0 + s, gy = gy0 + r;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    cp_async4_zfill(dst + e, in ? plane + (int64_t)gy * W + gx : plane, in);
   }
 }
 
-// Row filter of NM maps formed from the staged planes by map_of (two rows and
-// four output columns per thread: each of the 14 inputs is loaded and its
-// products formed once), into out[m][row][col] for the kS rows and kT columns.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// Reciprocal of each half by the hardware approximation (within a few units
+// in the last place; the arguments here are at least C1 C2, far from the
+// denormal range).
+__device__ __forceinline__ float2 rcp2_approx(float2 a) {
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(a.y));
+  return r;
+}
+
+__device__ __forceinline__ bool aligned16(const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Four consecutive pixels of a row from column gx: one 16-byte store where
+// all lie in the image and the address allows it, else one by one.
+__device__ __forceinline__ void store_row4(float* row, int gx, int W, float a, float b, float c, float d) {
+  if (gx + 3 < W && aligned16(row + gx)) {
+    *reinterpret_cast<float4*>(row + gx) = make_float4(a, b, c, d);
+  } else {
+    if (gx < W) row[gx] = a;
+    if (gx + 1 < W) row[gx + 1] = b;
+    if (gx + 2 < W) row[gx + 2] = c;
+    if (gx + 3 < W) row[gx + 3] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The two filter passes
+
+// Vertical filter of NM maps formed from the staged planes by map_of(row,
+// column, v) (v[m] = the maps at that box row for the thread's column pair):
+// output rows 4w .. 4w + 3 from box rows 4w .. 4w + 13, into hp.
 template <int NM, class F>
-__device__ __forceinline__ void row_filter(const Win& win, F map_of, float (*out)[kS][kT]) {
-  for (int it = threadIdx.x; it < kS2 * (kT / 4); it += blockDim.x) {
-    const int rp = it / (kT / 4), c0 = (it - rp * (kT / 4)) * 4;
-    float2 a[4][NM];
+__device__ __forceinline__ void vertical_filter(const Win& win, F map_of, float2* __restrict__ hp) {
+  const int w = threadIdx.x >> 5, j = threadIdx.x & 31;
+  if (j >= kVPairs) return;
+  const int col = 2 + 2 * j, r0 = kVRows * w;
+  float2 acc[kVRows][NM];
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
+  for (int o = 0; o < kVRows; ++o)
 #pragma unroll
-      for (int m = 0; m < NM; ++m) a[o][m] = f2(0.f);
+    for (int m = 0; m < NM; ++m) acc[o][m] = f2(0.f);
 #pragma unroll
-    for (int j = 0; j < 4 + 2 * kR; ++j) {
-      float2 v[NM];
-      map_of(rp, c0 + j, v);
+  for (int i = 0; i < kVRows + 2 * kR; ++i) {
+    float2 v[NM];
+    map_of(r0 + i, col, v);
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const int k = j - o;
-        if (k >= 0 && k <= 2 * kR) {
-          const float2 wk = win.w[k];
+    for (int o = 0; o < kVRows; ++o) {
+      const int k = i - o;
+      if (k >= 0 && k <= 2 * kR) {
+        const float2 wk = win.w[k];
 #pragma unroll
-          for (int m = 0; m < NM; ++m) a[o][m] = fma2(wk, v[m], a[o][m]);
-        }
+        for (int m = 0; m < NM; ++m) acc[o][m] = fma2(wk, v[m], acc[o][m]);
       }
     }
+  }
+  // (rows 4w, 4w + 1) -> row pair 2w, (4w + 2, 4w + 3) -> 2w + 1.  Of the
+  // thread's two columns, lanes with bit 3 clear store the left one first and
+  // the others the right one, so each half-warp's stores cover all 32 banks
+  // once per instruction.
+  const bool swap = (j >> 3) & 1;
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
+  for (int m = 0; m < NM; ++m) {
+    float2* h = hp + (size_t)m * (kTH / 2) * kHP + (size_t)(2 * w) * kHP + 2 * j;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        out[m][2 * rp][c0 + o] = a[o][m].x;
-        out[m][2 * rp + 1][c0 + o] = a[o][m].y;
-      }
+    for (int rp = 0; rp < 2; ++rp) {
+      const float2 left = make_float2(acc[2 * rp][m].x, acc[2 * rp + 1][m].x);
+      const float2 right = make_float2(acc[2 * rp][m].y, acc[2 * rp + 1][m].y);
+      h[rp * kHP + (swap ? 1 : 0)] = swap ? right : left;
+      h[rp * kHP + (swap ? 0 : 1)] = swap ? left : right;
+    }
   }
 }
 
-// Column filter: thread t covers columns (2 cp, 2 cp + 1) as one packed pair
-// and rows 2 rg, 2 rg + 1 of the tile (cp = t % 16, rg = t / 16).
+// Horizontal filter of the NM interleaved maps for row pair i and output
+// columns 4q .. 4q + 3: res[o][m] = (row 2i, row 2i + 1) at column 4q + o.
 template <int NM>
-__device__ __forceinline__ void col_filter(const Win& win, float (*in)[kS][kT], float2 (*res)[NM]) {
-  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
+__device__ __forceinline__ void horizontal_filter(const Win& win, const float2* __restrict__ hp, int i, int q,
+                                                  float2 (*res)[NM]) {
 #pragma unroll
-  for (int o = 0; o < 2; ++o)
+  for (int o = 0; o < 4; ++o)
 #pragma unroll
     for (int m = 0; m < NM; ++m) res[o][m] = f2(0.f);
+  const float2* h = hp + (size_t)i * kHP + 4 * q + 1;
 #pragma unroll
-  for (int i = 0; i < 2 + 2 * kR; ++i) {
+  for (int jj = 0; jj < 4 + 2 * kR; ++jj) {
     float2 v[NM];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) v[m] = *reinterpret_cast<const float2*>(&in[m][r0 + i][c]);
+    for (int m = 0; m < NM; ++m) v[m] = h[(size_t)m * (kTH / 2) * kHP + jj];
 #pragma unroll
-    for (int o = 0; o < 2; ++o) {
-      const int k = i - o;
+    for (int o = 0; o < 4; ++o) {
+      const int k = jj - o;
       if (k >= 0 && k <= 2 * kR) {
         const float2 wk = win.w[k];
 #pragma unroll
@@ -115,119 +249,269 @@ __device__ __forceinline__ void col_filter(const Win& win, float (*in)[kS][kT], 
   }
 }
 
+__device__ __forceinline__ unsigned char* smem_base(unsigned char* raw) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+}
+
 }  // namespace
 
 // Forward: SSIM at every pixel, the view's loss, and the derivative maps
 //   D1 = dS/dmu_x - 2 mu_x dS/ds_xx - mu_y dS/ds_xy, D2 = dS/ds_xx, D3 = dS/ds_xy
 // (S depends on x through the window sums G*x, G*x^2 and G*(x y)).
-// 256 threads per 32 x 32 tile.
-__global__ void __launch_bounds__(256, 4) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  int H, int W, Win win, float* __restrict__ dmaps,
-                                                  float* __restrict__ ssim_sum) {
-  __shared__ float2 s_x[kS2][kS], s_y[kS2][kS];
-  __shared__ __align__(16) float s_h[4][kS][kT];
-  __shared__ float s_red[8];
-  const int tiles_x = (W + kT - 1) / kT;
+// A TMA wait that runs out (never expected) adds NaN to the view's SSIM sum.
+template <bool TMA>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_ssim_fwd(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y,
+               const float* __restrict__ img, const float* __restrict__ tgt, int H, int W, Win win,
+               float* __restrict__ dmaps, float* __restrict__ ssim_sum) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sb = smem_base(smem_raw);
+  float* sx = reinterpret_cast<float*>(sb);
+  float* sy = reinterpret_cast<float*>(sb + kPlaneBytes);
+  float2* hp = reinterpret_cast<float2*>(sb + kFwdHp);
+  float* red = reinterpret_cast<float*>(sb + kFwdRed);
+  const uint32_t bar = smem_u32(sb + kFwdBar);
+  const int tiles_x = (W + kTW - 1) / kTW;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int plane = blockIdx.y;  // view * 3 + channel
   const int64_t HW = (int64_t)H * W;
-  const int x0 = tx * kT - kR, y0 = ty * kT - kR;
-  stage_pairs(img + plane * HW, H, W, x0, y0, s_x);
-  stage_pairs(tgt + plane * HW, H, W, x0, y0, s_y);
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
+  const int gx0 = tx * kTW - kBXOff, gy0 = ty * kTH - kR;
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar);
+      mbar_init_fence();
+      mbar_expect_tx(bar, 2 * (uint32_t)kPlaneBytes);
+      tma_load_3d(smem_u32(sx), &map_x, gx0, gy0, plane, bar);
+      tma_load_3d(smem_u32(sy), &map_y, gx0, gy0, plane, bar);
+    }
+    __syncthreads();  // the barrier's initialisation before anyone waits on it
+    if (!__syncthreads_and(mbar_wait(bar, 0))) {
+      mbar_wait(bar, 0);  // let copies still in flight land before the block exits
+      if (threadIdx.x == 0) atomicAdd(ssim_sum + plane / 3, __int_as_float(0x7fc00000));
+      return;
+    }
+  } else {
+    copy_box<kBX, kBY>(img + plane * HW, H, W, gx0, gy0, sx);
+    copy_box<kBX, kBY>(tgt + plane * HW, H, W, gx0, gy0, sy);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+  }
   // window sums of x, y, x^2 + y^2, x y: SSIM takes the two variances only as
   // their sum, so their second moments are filtered together
-  row_filter<4>(win, [&](int rp, int c, float2* v) {
-    const float2 xv = s_x[rp][c], yv = s_y[rp][c];
+  vertical_filter<4>(win, [&](int r, int c, float2* v) {
+    const float2 xv = *reinterpret_cast<const float2*>(sx + r * kBX + c);
+    const float2 yv = *reinterpret_cast<const float2*>(sy + r * kBX + c);
     v[0] = xv; v[1] = yv; v[2] = fma2(xv, xv, mul2(yv, yv)); v[3] = mul2(xv, yv);
-  }, s_h);
+  }, hp);
   __syncthreads();
-  float2 m[2][4];
-  col_filter<4>(win, s_h, m);
   float local = 0.f;
-  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
-  float* d = dmaps + (int64_t)plane * 3 * HW;
+  if (threadIdx.x < kHItems) {
+    const int i = threadIdx.x & 15, q = threadIdx.x >> 4;
+    float2 m[4][4];
+    horizontal_filter<4>(win, hp, i, q, m);
+    const float2 C1 = f2(kC1), C2 = f2(kC2), two = f2(2.f);
+    float2 d1[4], d2[4], d3[4];
+    const int gy = ty * kTH + 2 * i, gx = tx * kTW + 4 * q;
 #pragma unroll
-  for (int o = 0; o < 2; ++o)
-#pragma unroll
-    for (int hx = 0; hx < 2; ++hx) {
-      const int gy = ty * kT + r0 + o, gx = tx * kT + c + hx;
-      if (gy >= H || gx >= W) continue;
-      const float mx = hx ? m[o][0].y : m[o][0].x, my = hx ? m[o][1].y : m[o][1].x;
-      const float ess = hx ? m[o][2].y : m[o][2].x;  // window sum of x^2 + y^2
-      const float exy = hx ? m[o][3].y : m[o][3].x;
-      const float sxy = exy - mx * my;
-      const float a1 = 2.f * mx * my + kC1, a2 = 2.f * sxy + kC2;
-      const float b1 = mx * mx + my * my + kC1, b2 = ess - mx * mx - my * my + kC2;  // s_xx + s_yy + C2
-      const float ib = 1.f / (b1 * b2);
-      const float sv = a1 * a2 * ib;
-      const float ds_dmx = 2.f * my * a2 * ib - sv * 2.f * mx / b1;
-      const float ds_dsxx = -sv / b2;
-      const float ds_dsxy = 2.f * a1 * ib;
-      const int64_t p = (int64_t)gy * W + gx;
-      d[p] = ds_dmx - 2.f * mx * ds_dsxx - my * ds_dsxy;
-      d[HW + p] = ds_dsxx;
-      d[2 * HW + p] = ds_dsxy;
-      local += sv;
+    for (int o = 0; o < 4; ++o) {
+      // (row 2i, row 2i + 1) at column 4q + o
+      const float2 mx = m[o][0], my = m[o][1], ess = m[o][2], exy = m[o][3];  // ess: window sum of x^2 + y^2
+      const float2 mxy = mul2(mx, my), mm = fma2(mx, mx, mul2(my, my));
+      const float2 a1 = fma2(two, mxy, C1), a2 = fma2(two, sub2(exy, mxy), C2);  // 2 mu_x mu_y + C1, 2 s_xy + C2
+      const float2 b1 = add2(mm, C1), b2 = add2(sub2(ess, mm), C2);  // mu_x^2 + mu_y^2 + C1, s_xx + s_yy + C2
+      const float2 ib = rcp2_approx(mul2(b1, b2));
+      const float2 a2ib = mul2(a2, ib);
+      const float2 sv = mul2(a1, a2ib);
+      const float2 ds_dsxy = mul2(two, mul2(a1, ib));
+      const float2 sv_b2 = mul2(sv, mul2(b1, ib));  // S / b2 = -dS/ds_xx
+      // dS/dmu_x = 2 mu_y a2 / (b1 b2) - 2 mu_x S / b1, with 1 / b1 = b2 ib
+      const float2 ds_dmx = mul2(two, sub2(mul2(my, a2ib), mul2(mx, mul2(sv, mul2(b2, ib)))));
+      d1[o] = sub2(fma2(mul2(two, mx), sv_b2, ds_dmx), mul2(my, ds_dsxy));
+      d2[o] = make_float2(-sv_b2.x, -sv_b2.y);
+      d3[o] = ds_dsxy;
+      if (gx + o < W) local += (gy < H ? sv.x : 0.f) + (gy + 1 < H ? sv.y : 0.f);
     }
+    float* d = dmaps + (int64_t)plane * 3 * HW;
+    if (gy < H) {
+      float* row = d + (int64_t)gy * W;
+      store_row4(row, gx, W, d1[0].x, d1[1].x, d1[2].x, d1[3].x);
+      store_row4(row + HW, gx, W, d2[0].x, d2[1].x, d2[2].x, d2[3].x);
+      store_row4(row + 2 * HW, gx, W, d3[0].x, d3[1].x, d3[2].x, d3[3].x);
+    }
+    if (gy + 1 < H) {
+      float* row = d + (int64_t)(gy + 1) * W;
+      store_row4(row, gx, W, d1[0].y, d1[1].y, d1[2].y, d1[3].y);
+      store_row4(row + HW, gx, W, d2[0].y, d2[1].y, d2[2].y, d2[3].y);
+      store_row4(row + 2 * HW, gx, W, d3[0].y, d3[1].y, d3[2].y, d3[3].y);
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
   __syncthreads();
   if (threadIdx.x == 0) {
     float t = 0.f;
-    for (int w = 0; w < 8; ++w) t += s_red[w];
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
     atomicAdd(ssim_sum + plane / 3, t);
   }
 }
 
 // Backward: dD/dx = -(G*D1 + 2 x G*D2 + y G*D3) / (3 H W), added (times the
 // weight) to dl_dimg; the window is symmetric, so the adjoint filter is the
-// same filter.
-__global__ void __launch_bounds__(256) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  int H, int W, Win win, const float* __restrict__ dmaps,
-                                                  float scale, float* __restrict__ dl_dimg) {
-  __shared__ float2 s_d[3][kS2][kS];
-  __shared__ __align__(16) float s_h[3][kS][kT];
-  const int tiles_x = (W + kT - 1) / kT;
+// same filter.  A TMA wait that runs out (never expected) leaves NaN in the
+// tile's dl_dimg.
+template <bool TMA>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_ssim_bwd(const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_x,
+               const __grid_constant__ CUtensorMap map_y, const __grid_constant__ CUtensorMap map_dl,
+               const float* __restrict__ img, const float* __restrict__ tgt, int H, int W, Win win,
+               const float* __restrict__ dmaps, float scale, float* __restrict__ dl_dimg) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sb = smem_base(smem_raw);
+  float* sd = reinterpret_cast<float*>(sb);  // D1, D2, D3 boxes; then x, y, dl_dimg over the tile
+  float2* hp = reinterpret_cast<float2*>(sb + kBwdHp);
+  const uint32_t bar0 = smem_u32(sb + kBwdBar), bar1 = bar0 + 8;
+  const int tiles_x = (W + kTW - 1) / kTW;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int plane = blockIdx.y;
   const int64_t HW = (int64_t)H * W;
   const float* d = dmaps + (int64_t)plane * 3 * HW;
-  const int x0 = tx * kT - kR, y0 = ty * kT - kR;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) stage_pairs(d + q * HW, H, W, x0, y0, s_d[q]);
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
-  row_filter<3>(win, [&](int rp, int c, float2* v) {
-    v[0] = s_d[0][rp][c]; v[1] = s_d[1][rp][c]; v[2] = s_d[2][rp][c];
-  }, s_h);
-  __syncthreads();
-  float2 m[2][3];
-  col_filter<3>(win, s_h, m);
-  const float* x = img + plane * HW;
-  const float* y = tgt + plane * HW;
   float* out = dl_dimg + plane * HW;
-  const int c = 2 * (threadIdx.x & 15), r0 = 2 * (threadIdx.x >> 4);
+  const int gx0 = tx * kTW - kBXOff, gy0 = ty * kTH - kR;
+  const int ex0 = tx * kTW, ey0 = ty * kTH;  // output tile origin
+  float* ep = sd;                            // operand boxes [3][kTH][kEX]
+  constexpr int kPlaneFloats = (int)(kPlaneBytes / sizeof(float));
+  bool ok = true;
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar0);
+      mbar_init(bar1);
+      mbar_init_fence();
+      mbar_expect_tx(bar0, 3 * (uint32_t)kPlaneBytes);
 #pragma unroll
-  for (int o = 0; o < 2; ++o)
-#pragma unroll
-    for (int hx = 0; hx < 2; ++hx) {
-      const int gy = ty * kT + r0 + o, gx = tx * kT + c + hx;
-      if (gy >= H || gx >= W) continue;
-      const int64_t p = (int64_t)gy * W + gx;
-      const float s0 = hx ? m[o][0].y : m[o][0].x, s1 = hx ? m[o][1].y : m[o][1].x;
-      const float s2 = hx ? m[o][2].y : m[o][2].x;
-      out[p] += scale * (s0 + 2.f * x[p] * s1 + y[p] * s2);
+      for (int k = 0; k < 3; ++k) tma_load_3d(smem_u32(sd + k * kPlaneFloats), &map_d, gx0, gy0, 3 * plane + k, bar0);
     }
+    __syncthreads();
+    ok = __syncthreads_and(mbar_wait(bar0, 0));
+    if (!ok) mbar_wait(bar0, 0);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) copy_box<kBX, kBY>(d + k * HW, H, W, gx0, gy0, sd + k * kPlaneFloats);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  if (ok) {
+    vertical_filter<3>(win, [&](int r, int c, float2* v) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = *reinterpret_cast<const float2*>(sd + k * kPlaneFloats + r * kBX + c);
+    }, hp);
+  }
+  __syncthreads();
+  // the staged maps are dead: fetch x, y and dl_dimg over the output tile
+  // into their place while the horizontal filter runs
+  if (TMA) {
+    if (ok && threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar1, 3 * (uint32_t)kEpBytes);
+      tma_load_3d(smem_u32(ep), &map_x, ex0, ey0, plane, bar1);
+      tma_load_3d(smem_u32(ep + kTH * kEX), &map_y, ex0, ey0, plane, bar1);
+      tma_load_3d(smem_u32(ep + 2 * kTH * kEX), &map_dl, ex0, ey0, plane, bar1);
+    }
+  } else {
+    copy_box<kEX, kTH>(img + plane * HW, H, W, ex0, ey0, ep);
+    copy_box<kEX, kTH>(tgt + plane * HW, H, W, ex0, ey0, ep + kTH * kEX);
+    copy_box<kEX, kTH>(out, H, W, ex0, ey0, ep + 2 * kTH * kEX);
+    cp_async_commit();
+  }
+  const int i = threadIdx.x & 15, q = threadIdx.x >> 4;
+  float2 m[4][3];
+  if (threadIdx.x < kHItems && ok) horizontal_filter<3>(win, hp, i, q, m);
+  if (TMA) {
+    if (ok) {
+      ok = __syncthreads_and(mbar_wait(bar1, 0));
+      if (!ok) mbar_wait(bar1, 0);
+    }
+  } else {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  if (threadIdx.x >= kHItems) return;
+  const int gy = ey0 + 2 * i, gx = ex0 + 4 * q;
+  if (!ok) {
+    const float nan = __int_as_float(0x7fc00000);
+    if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, nan, nan, nan, nan);
+    if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, nan, nan, nan, nan);
+    return;
+  }
+  // operands of rows 2i, 2i + 1, columns 4q .. 4q + 3 (zero outside the image)
+  float4 xr[2], yr[2], lr[2];
+#pragma unroll
+  for (int hy = 0; hy < 2; ++hy) {
+    const int e = (2 * i + hy) * kEX + 4 * q;
+    xr[hy] = *reinterpret_cast<const float4*>(ep + e);
+    yr[hy] = *reinterpret_cast<const float4*>(ep + kTH * kEX + e);
+    lr[hy] = *reinterpret_cast<const float4*>(ep + 2 * kTH * kEX + e);
+  }
+  const float xs[2][4] = {{xr[0].x, xr[0].y, xr[0].z, xr[0].w}, {xr[1].x, xr[1].y, xr[1].z, xr[1].w}};
+  const float ys[2][4] = {{yr[0].x, yr[0].y, yr[0].z, yr[0].w}, {yr[1].x, yr[1].y, yr[1].z, yr[1].w}};
+  const float ls[2][4] = {{lr[0].x, lr[0].y, lr[0].z, lr[0].w}, {lr[1].x, lr[1].y, lr[1].z, lr[1].w}};
+  const float2 sc = f2(scale);
+  float g[2][4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const float2 xv = make_float2(xs[0][o], xs[1][o]), yv = make_float2(ys[0][o], ys[1][o]);
+    const float2 r = fma2(sc, fma2(add2(xv, xv), m[o][1], fma2(yv, m[o][2], m[o][0])),
+                          make_float2(ls[0][o], ls[1][o]));
+    g[0][o] = r.x;
+    g[1][o] = r.y;
+  }
+  if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, g[0][0], g[0][1], g[0][2], g[0][3]);
+  if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, g[1][0], g[1][1], g[1][2], g[1][3]);
 }
 
 __global__ void k_ssim_loss(const float* __restrict__ ssim_sum, int V, float n, float weight, float* __restrict__ loss) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v < V) loss[v] += weight * (1.f - ssim_sum[v] / n);
 }
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null when unavailable.
+EncodeTiled encoder() {
+  static const EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<EncodeTiled>(nullptr);
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of `planes` FP32 planes of H x W at `base`, boxes of bx x by x 1
+// (zero fill outside).  Needs W % 4 == 0 and a 16-byte aligned base.
+bool encode_planes(CUtensorMap* map, const float* base, int planes, int H, int W, int bx, int by) {
+  const EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * sizeof(float), (cuuint64_t)W * H * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16_host(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
 
 size_t dssim_scratch_bytes(int V, int H, int W) {
   // three derivative maps per channel plane, then one float per view (SSIM sums)
@@ -249,10 +533,32 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
                                              (((size_t)V * 9 * H * W * sizeof(float) + 255) / 256) * 256);
   cudaError_t err = cudaMemsetAsync(ssim_sum, 0, (size_t)V * sizeof(float), st);
   if (err != cudaSuccess) return err;
-  const int tiles = ((W + kT - 1) / kT) * ((H + kT - 1) / kT);
+  // TMA needs 16-byte row strides and bases; other shapes stage by cp.async
+  CUtensorMap mx, my, md, ex, ey, el;
+  std::memset(&mx, 0, sizeof mx);
+  std::memset(&my, 0, sizeof my);
+  std::memset(&md, 0, sizeof md);
+  std::memset(&ex, 0, sizeof ex);
+  std::memset(&ey, 0, sizeof ey);
+  std::memset(&el, 0, sizeof el);
+  const bool tma = W % 4 == 0 && aligned16_host(img) && aligned16_host(tgt) && aligned16_host(dmaps) &&
+                   (!dl_dimg || aligned16_host(dl_dimg)) && encode_planes(&mx, img, 3 * V, H, W, kBX, kBY) &&
+                   encode_planes(&my, tgt, 3 * V, H, W, kBX, kBY) && encode_planes(&md, dmaps, 9 * V, H, W, kBX, kBY) &&
+                   encode_planes(&ex, img, 3 * V, H, W, kEX, kTH) && encode_planes(&ey, tgt, 3 * V, H, W, kEX, kTH) &&
+                   (!dl_dimg || encode_planes(&el, dl_dimg, 3 * V, H, W, kEX, kTH));
+  const int tiles = ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
   const dim3 grid((unsigned)tiles, (unsigned)(3 * V));
+  auto fwd = tma ? k_ssim_fwd<true> : k_ssim_fwd<false>;
+  auto bwd = tma ? k_ssim_bwd<true> : k_ssim_bwd<false>;
+  if ((err = cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem)) != cudaSuccess)
+    return err;
+  if ((err = cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem)) != cudaSuccess)
+    return err;
+  // four CTAs per SM need the largest shared-memory carveout
+  if ((err = cudaFuncSetAttribute(fwd, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return err;
+  if ((err = cudaFuncSetAttribute(bwd, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return err;
   trace_begin(kKSsimFwd, st);
-  k_ssim_fwd<<<grid, 256, 0, st>>>(img, tgt, H, W, win, dmaps, ssim_sum);
+  fwd<<<grid, kThreads, kFwdSmem, st>>>(mx, my, img, tgt, H, W, win, dmaps, ssim_sum);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (loss) {
@@ -261,7 +567,8 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
   }
   if (dl_dimg) {
     trace_begin(kKSsimBwd, st);
-    k_ssim_bwd<<<grid, 256, 0, st>>>(img, tgt, H, W, win, dmaps, -weight / (3.f * (float)H * (float)W), dl_dimg);
+    bwd<<<grid, kThreads, kBwdSmem, st>>>(md, ex, ey, el, img, tgt, H, W, win, dmaps,
+                                          -weight / (3.f * (float)H * (float)W), dl_dimg);
     trace_end(st);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
