@@ -43,12 +43,12 @@ constexpr int kVRows = kTH / (kThreads / 32);  // 4
 // Its sums: hp[m][i][k] = (row 2i, row 2i + 1) at box column k + 2; the odd
 // row stride keeps the horizontal filter's loads free of bank conflicts.
 constexpr int kHP = 61;
-// Horizontal filter: thread it < 192 takes row pair it % 16 and columns
-// 4 (it / 16) .. 4 (it / 16) + 3.
+// Horizontal filter: threads 0..191, each one row pair i and the output
+// columns 4q .. 4q + 3 (see hitem).
 constexpr int kHItems = (kTH / 2) * (kTW / 4);  // 192
-// Backward operand boxes (x, y, dl_dimg over the output tile), 52 columns
-// wide so that the epilogue's row reads fall on distinct banks.
-constexpr int kEX = 52;
+// Output tiles ([kTH][kTW] per map, dense: the TMA store box) and the
+// backward's operand tiles (x, y, dl_dimg over the output tile).
+constexpr int kOutFloats = kTH * kTW;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 constexpr uint64_t kWaitNs = 1000000000ull;  // bound on a TMA wait (1 s)
@@ -59,7 +59,7 @@ static_assert(kHP >= 2 * kVPairs && 4 * (kTW / 4 - 1) + 1 + 13 < 2 * kVPairs, "h
 
 constexpr size_t kPlaneBytes = (size_t)kBX * kBY * sizeof(float);  // 10752, a multiple of 128
 constexpr size_t kHpBytes = (size_t)(kTH / 2) * kHP * sizeof(float2);
-constexpr size_t kEpBytes = (size_t)kTH * kEX * sizeof(float);
+constexpr size_t kEpBytes = (size_t)kOutFloats * sizeof(float);
 // forward: staged x, y | hp[4] | reduction | barrier
 constexpr size_t kFwdHp = 2 * kPlaneBytes;
 constexpr size_t kFwdRed = kFwdHp + 4 * kHpBytes;
@@ -69,7 +69,7 @@ constexpr size_t kFwdSmem = kFwdBar + 16 + 128;  // + alignment slack of the dyn
 constexpr size_t kBwdHp = 3 * kPlaneBytes;
 constexpr size_t kBwdBar = kBwdHp + 3 * kHpBytes;
 constexpr size_t kBwdSmem = kBwdBar + 16 + 128;
-static_assert(kPlaneBytes % 128 == 0 && kEpBytes % 128 == 0 && 3 * kEpBytes <= 3 * kPlaneBytes, "staging layout");
+static_assert(kPlaneBytes % 128 == 0 && kEpBytes % 128 == 0 && 3 * kEpBytes <= 2 * kPlaneBytes, "staging layout");
 
 struct Win {
   // normalised 1D Gaussian (the 2D window is its outer product), each weight
@@ -129,6 +129,20 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 // a barrier everyone's) before later async-proxy (TMA) writes to the same bytes.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Shared memory -> one box of a [planes][H][W] FP32 tensor map at (x, y,
+// plane) (elements outside the tensor are not written); the issuing thread
+// then waits until the copy has read shared memory.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit_and_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // 4-byte asynchronous copy into shared memory, zero-filled when `in` is
 // false (no global byte is read then; `src` must still be a valid address).
 __device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool in) {
@@ -157,6 +171,25 @@ __device__ __forceinline__ float2 rcp2_approx(float2 a) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(a.x));
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(a.y));
   return r;
+}
+
+// Horizontal-filter thread t < 192: row pair i and column quad q.  A warp
+// takes 8 row pairs x 4 quads, the lane bits (3, 0, 4) giving the row pair
+// and (1, 2) the quad; with hp's row stride of 61 its hp loads, and its
+// 16-byte accesses to a dense [32][48] tile in the order of tile_rows, are
+// free of bank conflicts.
+__device__ __forceinline__ void hitem(int t, int& i, int& q) {
+  const int w = t >> 5, l = t & 31;
+  i = (w & 1) * 8 + (((l >> 3) & 1) | ((l & 1) << 1) | (((l >> 4) & 1) << 2));
+  q = (w >> 1) * 4 + ((l >> 1) & 3);
+}
+
+// The two rows of row pair i in the order the thread accesses a dense tile:
+// lanes with bit 1 of i set take the odd row first.
+__device__ __forceinline__ void tile_rows(int i, int& first, int& second) {
+  const int sel = (i >> 1) & 1;
+  first = 2 * i + sel;
+  second = 2 * i + 1 - sel;
 }
 
 __device__ __forceinline__ bool aligned16(const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -257,17 +290,20 @@ __device__ __forceinline__ unsigned char* smem_base(unsigned char* raw) {
 
 // Forward: SSIM at every pixel, the view's loss, and the derivative maps
 //   D1 = dS/dmu_x - 2 mu_x dS/ds_xx - mu_y dS/ds_xy, D2 = dS/ds_xx, D3 = dS/ds_xy
-// (S depends on x through the window sums G*x, G*x^2 and G*(x y)).
-// A TMA wait that runs out (never expected) adds NaN to the view's SSIM sum.
+// (S depends on x through the window sums G*x, G*x^2 and G*(x y)), written
+// by TMA from output tiles in the dead staging space.  A TMA wait that runs
+// out (never expected) adds NaN to the view's SSIM sum.
 template <bool TMA>
 __global__ void __launch_bounds__(kThreads, 4)
     k_ssim_fwd(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y,
-               const float* __restrict__ img, const float* __restrict__ tgt, int H, int W, Win win,
-               float* __restrict__ dmaps, float* __restrict__ ssim_sum) {
+               const __grid_constant__ CUtensorMap map_d, const float* __restrict__ img,
+               const float* __restrict__ tgt, int H, int W, Win win, float* __restrict__ dmaps,
+               float* __restrict__ ssim_sum) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sb = smem_base(smem_raw);
   float* sx = reinterpret_cast<float*>(sb);
   float* sy = reinterpret_cast<float*>(sb + kPlaneBytes);
+  float* so = sx;  // output tiles D1, D2, D3 once the staged planes are dead
   float2* hp = reinterpret_cast<float2*>(sb + kFwdHp);
   float* red = reinterpret_cast<float*>(sb + kFwdRed);
   const uint32_t bar = smem_u32(sb + kFwdBar);
@@ -306,16 +342,17 @@ __global__ void __launch_bounds__(kThreads, 4)
   }, hp);
   __syncthreads();
   float local = 0.f;
+  const int ex0 = tx * kTW, ey0 = ty * kTH;  // output tile origin
   if (threadIdx.x < kHItems) {
-    const int i = threadIdx.x & 15, q = threadIdx.x >> 4;
+    int i, q;
+    hitem(threadIdx.x, i, q);
     float2 m[4][4];
     horizontal_filter<4>(win, hp, i, q, m);
     const float2 C1 = f2(kC1), C2 = f2(kC2), two = f2(2.f);
-    float2 d1[4], d2[4], d3[4];
-    const int gy = ty * kTH + 2 * i, gx = tx * kTW + 4 * q;
+    float2 dd[3][4];  // D1, D2, D3 at (row 2i, row 2i + 1), column 4q + o
+    const int gy = ey0 + 2 * i, gx = ex0 + 4 * q;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      // (row 2i, row 2i + 1) at column 4q + o
       const float2 mx = m[o][0], my = m[o][1], ess = m[o][2], exy = m[o][3];  // ess: window sum of x^2 + y^2
       const float2 mxy = mul2(mx, my), mm = fma2(mx, mx, mul2(my, my));
       const float2 a1 = fma2(two, mxy, C1), a2 = fma2(two, sub2(exy, mxy), C2);  // 2 mu_x mu_y + C1, 2 s_xy + C2
@@ -327,39 +364,53 @@ __global__ void __launch_bounds__(kThreads, 4)
       const float2 sv_b2 = mul2(sv, mul2(b1, ib));  // S / b2 = -dS/ds_xx
       // dS/dmu_x = 2 mu_y a2 / (b1 b2) - 2 mu_x S / b1, with 1 / b1 = b2 ib
       const float2 ds_dmx = mul2(two, sub2(mul2(my, a2ib), mul2(mx, mul2(sv, mul2(b2, ib)))));
-      d1[o] = sub2(fma2(mul2(two, mx), sv_b2, ds_dmx), mul2(my, ds_dsxy));
-      d2[o] = make_float2(-sv_b2.x, -sv_b2.y);
-      d3[o] = ds_dsxy;
+      dd[0][o] = sub2(fma2(mul2(two, mx), sv_b2, ds_dmx), mul2(my, ds_dsxy));
+      dd[1][o] = make_float2(-sv_b2.x, -sv_b2.y);
+      dd[2][o] = ds_dsxy;
       if (gx + o < W) local += (gy < H ? sv.x : 0.f) + (gy + 1 < H ? sv.y : 0.f);
     }
-    float* d = dmaps + (int64_t)plane * 3 * HW;
-    if (gy < H) {
-      float* row = d + (int64_t)gy * W;
-      store_row4(row, gx, W, d1[0].x, d1[1].x, d1[2].x, d1[3].x);
-      store_row4(row + HW, gx, W, d2[0].x, d2[1].x, d2[2].x, d2[3].x);
-      store_row4(row + 2 * HW, gx, W, d3[0].x, d3[1].x, d3[2].x, d3[3].x);
-    }
-    if (gy + 1 < H) {
-      float* row = d + (int64_t)(gy + 1) * W;
-      store_row4(row, gx, W, d1[0].y, d1[1].y, d1[2].y, d1[3].y);
-      store_row4(row + HW, gx, W, d2[0].y, d2[1].y, d2[2].y, d2[3].y);
-      store_row4(row + 2 * HW, gx, W, d3[0].y, d3[1].y, d3[2].y, d3[3].y);
+    if (TMA) {
+      int ra, rb;
+      tile_rows(i, ra, rb);
+      const bool odd_first = ra & 1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float4 ev = make_float4(dd[k][0].x, dd[k][1].x, dd[k][2].x, dd[k][3].x);
+        const float4 od = make_float4(dd[k][0].y, dd[k][1].y, dd[k][2].y, dd[k][3].y);
+        *reinterpret_cast<float4*>(so + k * kOutFloats + ra * kTW + 4 * q) = odd_first ? od : ev;
+        *reinterpret_cast<float4*>(so + k * kOutFloats + rb * kTW + 4 * q) = odd_first ? ev : od;
+      }
+    } else {
+      float* d = dmaps + (int64_t)plane * 3 * HW;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (gy < H) store_row4(d + k * HW + (int64_t)gy * W, gx, W, dd[k][0].x, dd[k][1].x, dd[k][2].x, dd[k][3].x);
+        if (gy + 1 < H)
+          store_row4(d + k * HW + (int64_t)(gy + 1) * W, gx, W, dd[k][0].y, dd[k][1].y, dd[k][2].y, dd[k][3].y);
+      }
     }
   }
+  if (TMA) fence_proxy_async();  // the output tiles, to the copy engine
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (TMA) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tma_store_3d(&map_d, smem_u32(so + k * kOutFloats), ex0, ey0, 3 * plane + k);
+    }
     float t = 0.f;
     for (int w = 0; w < kThreads / 32; ++w) t += red[w];
     atomicAdd(ssim_sum + plane / 3, t);
+    if (TMA) tma_store_commit_and_wait_read();
   }
 }
 
 // Backward: dD/dx = -(G*D1 + 2 x G*D2 + y G*D3) / (3 H W), added (times the
 // weight) to dl_dimg; the window is symmetric, so the adjoint filter is the
-// same filter.  A TMA wait that runs out (never expected) leaves NaN in the
-// tile's dl_dimg.
+// same filter.  x, y and dl_dimg over the tile come in by TMA, the updated
+// dl_dimg goes out by TMA from the same shared memory.  A TMA wait that runs
+// out (never expected) leaves NaN in the tile's dl_dimg.
 template <bool TMA>
 __global__ void __launch_bounds__(kThreads, 4)
     k_ssim_bwd(const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_x,
@@ -379,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   float* out = dl_dimg + plane * HW;
   const int gx0 = tx * kTW - kBXOff, gy0 = ty * kTH - kR;
   const int ex0 = tx * kTW, ey0 = ty * kTH;  // output tile origin
-  float* ep = sd;                            // operand boxes [3][kTH][kEX]
+  float* ep = sd;                            // operand tiles [3][kTH][kTW]
   constexpr int kPlaneFloats = (int)(kPlaneBytes / sizeof(float));
   bool ok = true;
   if (TMA) {
@@ -415,16 +466,17 @@ __global__ void __launch_bounds__(kThreads, 4)
       fence_proxy_async();
       mbar_expect_tx(bar1, 3 * (uint32_t)kEpBytes);
       tma_load_3d(smem_u32(ep), &map_x, ex0, ey0, plane, bar1);
-      tma_load_3d(smem_u32(ep + kTH * kEX), &map_y, ex0, ey0, plane, bar1);
-      tma_load_3d(smem_u32(ep + 2 * kTH * kEX), &map_dl, ex0, ey0, plane, bar1);
+      tma_load_3d(smem_u32(ep + kOutFloats), &map_y, ex0, ey0, plane, bar1);
+      tma_load_3d(smem_u32(ep + 2 * kOutFloats), &map_dl, ex0, ey0, plane, bar1);
     }
   } else {
-    copy_box<kEX, kTH>(img + plane * HW, H, W, ex0, ey0, ep);
-    copy_box<kEX, kTH>(tgt + plane * HW, H, W, ex0, ey0, ep + kTH * kEX);
-    copy_box<kEX, kTH>(out, H, W, ex0, ey0, ep + 2 * kTH * kEX);
+    copy_box<kTW, kTH>(img + plane * HW, H, W, ex0, ey0, ep);
+    copy_box<kTW, kTH>(tgt + plane * HW, H, W, ex0, ey0, ep + kOutFloats);
+    copy_box<kTW, kTH>(out, H, W, ex0, ey0, ep + 2 * kOutFloats);
     cp_async_commit();
   }
-  const int i = threadIdx.x & 15, q = threadIdx.x >> 4;
+  int i, q;
+  hitem(threadIdx.x, i, q);
   float2 m[4][3];
   if (threadIdx.x < kHItems && ok) horizontal_filter<3>(win, hp, i, q, m);
   if (TMA) {
@@ -436,38 +488,59 @@ __global__ void __launch_bounds__(kThreads, 4)
     cp_async_wait_all();
     __syncthreads();
   }
-  if (threadIdx.x >= kHItems) return;
   const int gy = ey0 + 2 * i, gx = ex0 + 4 * q;
   if (!ok) {
-    const float nan = __int_as_float(0x7fc00000);
-    if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, nan, nan, nan, nan);
-    if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, nan, nan, nan, nan);
+    if (threadIdx.x < kHItems) {
+      const float nan = __int_as_float(0x7fc00000);
+      if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, nan, nan, nan, nan);
+      if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, nan, nan, nan, nan);
+    }
     return;
   }
-  // operands of rows 2i, 2i + 1, columns 4q .. 4q + 3 (zero outside the image)
-  float4 xr[2], yr[2], lr[2];
+  if (threadIdx.x < kHItems) {
+    // operands of rows 2i, 2i + 1, columns 4q .. 4q + 3 (zero outside the image)
+    int ra, rb;
+    tile_rows(i, ra, rb);
+    const bool odd_first = ra & 1;
+    float4 v[3][2];
 #pragma unroll
-  for (int hy = 0; hy < 2; ++hy) {
-    const int e = (2 * i + hy) * kEX + 4 * q;
-    xr[hy] = *reinterpret_cast<const float4*>(ep + e);
-    yr[hy] = *reinterpret_cast<const float4*>(ep + kTH * kEX + e);
-    lr[hy] = *reinterpret_cast<const float4*>(ep + 2 * kTH * kEX + e);
-  }
-  const float xs[2][4] = {{xr[0].x, xr[0].y, xr[0].z, xr[0].w}, {xr[1].x, xr[1].y, xr[1].z, xr[1].w}};
-  const float ys[2][4] = {{yr[0].x, yr[0].y, yr[0].z, yr[0].w}, {yr[1].x, yr[1].y, yr[1].z, yr[1].w}};
-  const float ls[2][4] = {{lr[0].x, lr[0].y, lr[0].z, lr[0].w}, {lr[1].x, lr[1].y, lr[1].z, lr[1].w}};
-  const float2 sc = f2(scale);
-  float g[2][4];
+    for (int k = 0; k < 3; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(ep + k * kOutFloats + ra * kTW + 4 * q);
+      const float4 b = *reinterpret_cast<const float4*>(ep + k * kOutFloats + rb * kTW + 4 * q);
+      v[k][0] = odd_first ? b : a;  // row 2i
+      v[k][1] = odd_first ? a : b;  // row 2i + 1
+    }
+    const float2 sc = f2(scale);
+    float g[2][4];
 #pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    const float2 xv = make_float2(xs[0][o], xs[1][o]), yv = make_float2(ys[0][o], ys[1][o]);
-    const float2 r = fma2(sc, fma2(add2(xv, xv), m[o][1], fma2(yv, m[o][2], m[o][0])),
-                          make_float2(ls[0][o], ls[1][o]));
-    g[0][o] = r.x;
-    g[1][o] = r.y;
+    for (int o = 0; o < 4; ++o) {
+      auto col = [&](const float4& r) { return o == 0 ? r.x : o == 1 ? r.y : o == 2 ? r.z : r.w; };
+      const float2 xv = make_float2(col(v[0][0]), col(v[0][1])), yv = make_float2(col(v[1][0]), col(v[1][1]));
+      const float2 r = fma2(sc, fma2(add2(xv, xv), m[o][1], fma2(yv, m[o][2], m[o][0])),
+                            make_float2(col(v[2][0]), col(v[2][1])));
+      g[0][o] = r.x;
+      g[1][o] = r.y;
+    }
+    if (TMA) {
+      // the updated dl_dimg in place of the loaded one (each element read and
+      // written by this thread only), rows in the same order
+      const float4 ev = make_float4(g[0][0], g[0][1], g[0][2], g[0][3]);
+      const float4 od = make_float4(g[1][0], g[1][1], g[1][2], g[1][3]);
+      *reinterpret_cast<float4*>(ep + 2 * kOutFloats + ra * kTW + 4 * q) = odd_first ? od : ev;
+      *reinterpret_cast<float4*>(ep + 2 * kOutFloats + rb * kTW + 4 * q) = odd_first ? ev : od;
+    } else {
+      if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, g[0][0], g[0][1], g[0][2], g[0][3]);
+      if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, g[1][0], g[1][1], g[1][2], g[1][3]);
+    }
   }
-  if (gy < H) store_row4(out + (int64_t)gy * W, gx, W, g[0][0], g[0][1], g[0][2], g[0][3]);
-  if (gy + 1 < H) store_row4(out + (int64_t)(gy + 1) * W, gx, W, g[1][0], g[1][1], g[1][2], g[1][3]);
+  if (TMA) {
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma_store_3d(&map_dl, smem_u32(ep + 2 * kOutFloats), ex0, ey0, plane);
+      tma_store_commit_and_wait_read();
+    }
+  }
 }
 
 __global__ void k_ssim_loss(const float* __restrict__ ssim_sum, int V, float n, float weight, float* __restrict__ loss) {
@@ -534,18 +607,15 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
   cudaError_t err = cudaMemsetAsync(ssim_sum, 0, (size_t)V * sizeof(float), st);
   if (err != cudaSuccess) return err;
   // TMA needs 16-byte row strides and bases; other shapes stage by cp.async
-  CUtensorMap mx, my, md, ex, ey, el;
-  std::memset(&mx, 0, sizeof mx);
-  std::memset(&my, 0, sizeof my);
-  std::memset(&md, 0, sizeof md);
-  std::memset(&ex, 0, sizeof ex);
-  std::memset(&ey, 0, sizeof ey);
-  std::memset(&el, 0, sizeof el);
+  // and store directly
+  CUtensorMap mx, my, md, mdo, ex, ey, el;
+  for (CUtensorMap* mp : {&mx, &my, &md, &mdo, &ex, &ey, &el}) std::memset(mp, 0, sizeof(CUtensorMap));
   const bool tma = W % 4 == 0 && aligned16_host(img) && aligned16_host(tgt) && aligned16_host(dmaps) &&
                    (!dl_dimg || aligned16_host(dl_dimg)) && encode_planes(&mx, img, 3 * V, H, W, kBX, kBY) &&
                    encode_planes(&my, tgt, 3 * V, H, W, kBX, kBY) && encode_planes(&md, dmaps, 9 * V, H, W, kBX, kBY) &&
-                   encode_planes(&ex, img, 3 * V, H, W, kEX, kTH) && encode_planes(&ey, tgt, 3 * V, H, W, kEX, kTH) &&
-                   (!dl_dimg || encode_planes(&el, dl_dimg, 3 * V, H, W, kEX, kTH));
+                   encode_planes(&mdo, dmaps, 9 * V, H, W, kTW, kTH) &&
+                   encode_planes(&ex, img, 3 * V, H, W, kTW, kTH) && encode_planes(&ey, tgt, 3 * V, H, W, kTW, kTH) &&
+                   (!dl_dimg || encode_planes(&el, dl_dimg, 3 * V, H, W, kTW, kTH));
   const int tiles = ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
   const dim3 grid((unsigned)tiles, (unsigned)(3 * V));
   auto fwd = tma ? k_ssim_fwd<true> : k_ssim_fwd<false>;
@@ -558,7 +628,7 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
   if ((err = cudaFuncSetAttribute(fwd, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return err;
   if ((err = cudaFuncSetAttribute(bwd, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return err;
   trace_begin(kKSsimFwd, st);
-  fwd<<<grid, kThreads, kFwdSmem, st>>>(mx, my, img, tgt, H, W, win, dmaps, ssim_sum);
+  fwd<<<grid, kThreads, kFwdSmem, st>>>(mx, my, mdo, img, tgt, H, W, win, dmaps, ssim_sum);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (loss) {
