@@ -289,7 +289,7 @@ __device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT,
     ++pass;
   };
   // Two passes order the bin by the top 16 bits of the depth key; runs that
-  // share those bits are then finished by insertion on (key, index).  A run
+  // share those bits are then finished by ranking on (key, index).  A run
   // longer than 32 keys (near-constant depth) sends the bin through all four
   // passes instead, so the fix-up stays short.
   radix_pass(16);
@@ -314,27 +314,23 @@ __device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT,
     radix_pass(24);
   }
   const uint32_t mask = full ? 0xffffffffu : 0xffff0000u;
-  // runs of equal (masked) keys: insertion sort on (key, Gaussian index)
+  // Runs of equal (masked) keys are finished in parallel: each key's place in
+  // its run is the number of the run's keys below it in (key, Gaussian
+  // index) order (all distinct), so it is written straight to its sorted slot.
   for (int i = threadIdx.x; i < n; i += NT) {
-    const uint32_t k = s_key[src][i] & mask;
-    if ((i == 0 || (s_key[src][i - 1] & mask) != k) && i + 1 < n && (s_key[src][i + 1] & mask) == k) {
-      int e = i + 1;
-      while (e < n && (s_key[src][e] & mask) == k) ++e;
-      for (int a = i + 1; a < e; ++a) {
-        const uint32_t ka = s_key[src][a], va = s_val[src][a];
-        int b = a - 1;
-        while (b >= i && (s_key[src][b] > ka || (s_key[src][b] == ka && s_val[src][b] > va))) {
-          s_key[src][b + 1] = s_key[src][b];
-          s_val[src][b + 1] = s_val[src][b];
-          --b;
-        }
-        s_key[src][b + 1] = ka;
-        s_val[src][b + 1] = va;
+    const uint32_t ka = s_key[src][i], va = s_val[src][i];
+    const uint32_t k = ka & mask;
+    int s0 = i, e = i + 1;
+    while (s0 > 0 && (s_key[src][s0 - 1] & mask) == k) --s0;
+    while (e < n && (s_key[src][e] & mask) == k) ++e;
+    int rank = 0;
+    if (e - s0 > 1)
+      for (int b = s0; b < e; ++b) {
+        const uint32_t kb = s_key[src][b];
+        rank += (kb < ka || (kb == ka && s_val[src][b] < va)) ? 1 : 0;
       }
-    }
+    ws.sorted_ids[start + s0 + rank] = va;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += NT) ws.sorted_ids[start + i] = s_val[src][i];
 }
 
 // Bins are sorted by size class: up to 64 keys by one warp (register bitonic
