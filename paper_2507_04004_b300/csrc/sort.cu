@@ -339,7 +339,8 @@ __device__ void cta_radix_bin(const Ws& ws, uint32_t start, int n, RadixSmem<NT,
 // persistent kMediumThreads-thread CTA over the medium list (filled from the
 // end of long_tiles), longer ones by k_sort_long.
 constexpr int kSmallThreads = 128, kSmallCap = 768;
-constexpr int kMediumThreads = 512, kMediumCap = 2048;
+constexpr int kMediumThreads = 256, kMediumCap = 2048;
+constexpr int kMediumPerSm = 5;  // resident CTAs per SM (shared memory: 41 KB each)
 
 __global__ void __launch_bounds__(kSmallThreads) k_sort_small(Ws ws) {
   __shared__ RadixSmem<kSmallThreads, kSmallCap> sm;
@@ -469,7 +470,7 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   err = cudaFuncSetAttribute(k_sort_medium, cudaFuncAttributeMaxDynamicSharedMemorySize, medium_smem);
   if (err != cudaSuccess) return err;
   trace_begin(kKSortMedium, st);
-  k_sort_medium<<<sm_count() * 4, kMediumThreads, medium_smem, st>>>(ws);
+  k_sort_medium<<<sm_count() * kMediumPerSm, kMediumThreads, medium_smem, st>>>(ws);
   trace_end(st);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
