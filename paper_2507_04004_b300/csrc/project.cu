@@ -29,6 +29,40 @@
 namespace gsb {
 
 constexpr int kMaxBuckets = 4096;  // buckets counted in shared memory (else global atomics)
+constexpr int kCamChunk = 32;      // views whose cameras k_project holds in shared memory at a time
+constexpr int kCamF4 = 7;          // float4 per staged camera
+
+// A view's camera as k_project reads it, with the per-view constants of its
+// tests precomputed once per CTA instead of once per (Gaussian, view):
+//   [0..2] rows of R with t, [3] fx fy cx cy, [4] the clamp limits of x/z and
+//   y/z and |fx| |r0|, |fx| |r2|, [5] |fy| |r1|, |fy| |r2|, [6] the centre -R^T t.
+__device__ __forceinline__ void stage_cam(const gs_camera* cams, int v, const gs_config& cfg, int width, int height,
+                                          float4* dst) {
+  const Cam c = load_cam(cams, v);
+  const float limx = cfg.fov_clamp * 0.5f * (float)width / c.fx;
+  const float limy = cfg.fov_clamp * 0.5f * (float)height / c.fy;
+  const float n0 = sqrtf(c.R[0] * c.R[0] + c.R[1] * c.R[1] + c.R[2] * c.R[2]);
+  const float n1 = sqrtf(c.R[3] * c.R[3] + c.R[4] * c.R[4] + c.R[5] * c.R[5]);
+  const float n2 = sqrtf(c.R[6] * c.R[6] + c.R[7] * c.R[7] + c.R[8] * c.R[8]);
+  const float3 cw = camera_centre(c);
+  dst[0] = make_float4(c.R[0], c.R[1], c.R[2], c.t[0]);
+  dst[1] = make_float4(c.R[3], c.R[4], c.R[5], c.t[1]);
+  dst[2] = make_float4(c.R[6], c.R[7], c.R[8], c.t[2]);
+  dst[3] = make_float4(c.fx, c.fy, c.cx, c.cy);
+  dst[4] = make_float4(limx, limy, fabsf(c.fx) * n0, fabsf(c.fx) * n2);
+  dst[5] = make_float4(fabsf(c.fy) * n1, fabsf(c.fy) * n2, 0.f, 0.f);
+  dst[6] = make_float4(cw.x, cw.y, cw.z, 0.f);
+}
+
+__device__ __forceinline__ Cam staged_cam(const float4* p) {
+  Cam c;
+  const float4 a = p[0], b = p[1], d = p[2], f = p[3];
+  c.R[0] = a.x; c.R[1] = a.y; c.R[2] = a.z; c.t[0] = a.w;
+  c.R[3] = b.x; c.R[4] = b.y; c.R[5] = b.z; c.t[1] = b.w;
+  c.R[6] = d.x; c.R[7] = d.y; c.R[8] = d.z; c.t[2] = d.w;
+  c.fx = f.x; c.fy = f.y; c.cx = f.z; c.cy = f.w;
+  return c;
+}
 constexpr int kMaxWindow = 2048;
 constexpr int kScatterThreads = 512;   // tiles of one CTA's row window kept in shared memory (two rows of 8K pixels)
 
@@ -39,13 +73,25 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
   // FP32 SH: each thread's 3K coefficients are copied asynchronously into its
   // own shared-memory column when it starts a Gaussian, so the DRAM latency
   // overlaps the first view's projection (dynamic shared memory, 3K x 256 floats)
-  extern __shared__ float s_shc[];
+  extern __shared__ float4 s_dyn[];
   constexpr int K = (DEG + 1) * (DEG + 1);
+  float* s_shc = reinterpret_cast<float*>(s_dyn);
+  // cameras of the current chunk of views, after the SH columns; then the
+  // CTA's visible entries of the current batch and chunk (256 x chunk slots),
+  // appended with shared atomics and written out with one global reservation
+  float4* s_cam = s_dyn + (BF16 ? 0 : 3 * K * 256 / 4);
+  uint32_t* s_vis = reinterpret_cast<uint32_t*>(s_cam + kCamChunk * kCamF4);
+  __shared__ uint32_t s_vis_n, s_vis_cnt, s_vis_base;
+  if (threadIdx.x == 0) s_vis_n = 0;
   const int64_t n = ws.n;
   const int nb = ws.views * ws.tiles_y;
   const bool smem_buckets = nb <= kMaxBuckets;
   if (smem_buckets)
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s_bucket[i] = 0;
+  const bool one_chunk = ws.views <= kCamChunk;  // staged once; else per chunk between barriers
+  if (one_chunk)
+    for (int i = threadIdx.x; i < ws.views; i += blockDim.x)
+      stage_cam(cams, i, cfg, ws.width, ws.height, s_cam + kCamF4 * i);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   // One thread per Gaussian, all views in turn: the parameters are read and
@@ -96,27 +142,31 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
     // lanes are not left idle when a Gaussian is outside most views.
     const float s2max = fmaxf(sc[0], fmaxf(sc[1], sc[2])) * fmaxf(sc[0], fmaxf(sc[1], sc[2]));
     const float Wf = (float)(ws.width - 1), Hf = (float)(ws.height - 1);
-    for (int v0 = 0; v0 < ws.views; v0 += 32) {
-      const int nv = min(32, ws.views - v0);
+    for (int v0 = 0; v0 < ws.views; v0 += kCamChunk) {
+      const int nv = min(kCamChunk, ws.views - v0);
+      if (!one_chunk) {
+        __syncthreads();  // everyone is done with the previous chunk's cameras
+        for (int i = threadIdx.x; i < nv; i += blockDim.x)
+          stage_cam(cams, v0 + i, cfg, ws.width, ws.height, s_cam + kCamF4 * i);
+        __syncthreads();
+      }
       uint32_t cand = 0;
       for (int j = 0; j < nv; ++j) {
         const int v = v0 + j;
-        const Cam cam = load_cam(cams, v);
+        const float4* cp = s_cam + kCamF4 * j;
+        const Cam cam = staged_cam(cp);
         const float3 mh = to_camera(cam, mw[0], mw[1], mw[2]);
         bool c = g_ok && q_thr > 0.f && mh.z > cfg.near_z;
         if (c) {
           const float iz = 1.f / mh.z;
           const float mx = __fmaf_rn(cam.fx * mh.x, iz, cam.cx);
           const float my = __fmaf_rn(cam.fy * mh.y, iz, cam.cy);
-          const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
-          const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
-          const float txc = fminf(limx, fmaxf(-limx, mh.x * iz));
-          const float tyc = fminf(limy, fmaxf(-limy, mh.y * iz));
-          const float n0 = sqrtf(cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2]);
-          const float n1 = sqrtf(cam.R[3] * cam.R[3] + cam.R[4] * cam.R[4] + cam.R[5] * cam.R[5]);
-          const float n2 = sqrtf(cam.R[6] * cam.R[6] + cam.R[7] * cam.R[7] + cam.R[8] * cam.R[8]);
-          const float a0 = fabsf(cam.fx * iz) * n0 + fabsf(cam.fx * txc * iz) * n2;
-          const float a1 = fabsf(cam.fy * iz) * n1 + fabsf(cam.fy * tyc * iz) * n2;
+          const float4 k4 = cp[4], k5 = cp[5];
+          const float txc = fminf(k4.x, fmaxf(-k4.x, mh.x * iz));
+          const float tyc = fminf(k4.y, fmaxf(-k4.y, mh.y * iz));
+          // |fx / z| |r0| + |fx x/z / z| |r2| (z > 0), and the same in y
+          const float a0 = iz * (k4.z + fabsf(txc) * k4.w);
+          const float a1 = iz * (k5.x + fabsf(tyc) * k5.y);
           const float hxb = 1.001f * sqrtf(q_thr * (1.001f * s2max * a0 * a0 + cfg.dilation)) + 1.f;
           const float hyb = 1.001f * sqrtf(q_thr * (1.001f * s2max * a1 * a1 + cfg.dilation)) + 1.f;
           if (mx - hxb - 1.5f > Wf + 1.f || mx + hxb + 0.5f < -1.f || my - hyb - 1.5f > Hf + 1.f ||
@@ -132,7 +182,8 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         const int v = act ? v0 + __ffs(cand) - 1 : v0;
         cand &= cand - 1;
         const int64_t e = (int64_t)v * n + g;
-        const Cam cam = load_cam(cams, v);
+        const float4* cp = s_cam + kCamF4 * (v - v0);
+        const Cam cam = staged_cam(cp);
         const float3 mh = to_camera(cam, mw[0], mw[1], mw[2]);
         bool ok = act && g_ok && (mh.z > cfg.near_z);
         const float z = ok ? mh.z : 1.f;
@@ -140,8 +191,8 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         const float mx = __fmaf_rn(cam.fx * mh.x, iz, cam.cx);
         const float my = __fmaf_rn(cam.fy * mh.y, iz, cam.cy);
         // affine Jacobian of the projection with x/z, y/z clamped
-        const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
-        const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
+        const float4 k4 = cp[4];
+        const float limx = k4.x, limy = k4.y;
         const float txc = fminf(limx, fmaxf(-limx, mh.x * iz));
         const float tyc = fminf(limy, fmaxf(-limy, mh.y * iz));
         const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz;
@@ -194,7 +245,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         // View-dependent colour: dir = (mu - c_w) / |mu - c_w|.
         float rgb[3] = {0.f, 0.f, 0.f};
         if (ok) {
-          const float3 cw = camera_centre(cam);
+          const float4 cw = cp[6];
           float dx = mw[0] - cw.x, dy = mw[1] - cw.y, dz = mw[2] - cw.z;
           const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
           dx *= inv; dy *= inv; dz *= inv;
@@ -222,24 +273,37 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
           rec[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
           float4* adj = ws.adjoints + 3 * e;
           adj[0] = adj[1] = adj[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-          const int b0 = v * ws.tiles_y;
-          for (int ty = ty0; ty <= ty1; ++ty) {
-            if (smem_buckets) atomicAdd(s_bucket + b0 + ty, 1u);
-            else atomicAdd(ws.bucket_count + b0 + ty, 1u);
-          }
+          // the entry's tile rows ty0..ty1 counted as a difference, +1 at ty0
+          // and -1 after ty1 (k_scan_buckets sums them per view): two atomics
+          // however many rows the box spans
+          uint32_t* bc = (smem_buckets ? s_bucket : ws.bucket_count) + v * ws.tiles_y;
+          atomicAdd(bc + ty0, 1u);
+          if (ty1 + 1 < ws.tiles_y) atomicAdd(bc + ty1 + 1, 0xffffffffu);
         }
         if (act) ws.rects[e] = ok ? pack_rect(tx0, ty0, tx1, ty1) : empty_rect();
-        // Append visible entries to the compact list, one atomic per warp.
+        // Append visible entries to the CTA's list, one shared atomic per warp.
         const unsigned vis = __ballot_sync(kFull, ok);
         if (vis) {
           const int leader = __ffs(vis) - 1;
           uint32_t slot = 0;
-          if (lane == leader) slot = atomicAdd(ws.counters + kVisibleCount, (uint32_t)__popc(vis));
+          if (lane == leader) slot = atomicAdd(&s_vis_n, (uint32_t)__popc(vis));
           slot = __shfl_sync(kFull, slot, leader);
-          if (ok) ws.visible[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
+          if (ok) s_vis[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
         }
         seen |= ok;
       }
+      // The CTA's visible entries of this batch and chunk go to the compact
+      // list under one global reservation (one hot counter otherwise takes an
+      // atomic per warp step from every SM).
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_vis_cnt = s_vis_n;
+        s_vis_base = s_vis_n ? atomicAdd(ws.counters + kVisibleCount, s_vis_n) : 0u;
+        s_vis_n = 0;
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < s_vis_cnt; i += blockDim.x) ws.visible[s_vis_base + i] = s_vis[i];
+      __syncthreads();  // the list is refilled by the next chunk
     }
     // Gaussians seen by some view, for the backward projection pass (one
     // atomic per warp; a warp's Gaussians stay consecutive in the list)
@@ -441,7 +505,9 @@ static cudaError_t launch_project_t(const gs_map& map, const gs_camera* cams, co
   const int64_t need = (ws.n + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 6;
   const unsigned grid = (unsigned)(need < cap ? need : cap);
-  const size_t smem = BF16 ? 0 : (size_t)3 * (DEG + 1) * (DEG + 1) * 256 * sizeof(float);
+  const size_t smem = (BF16 ? 0 : (size_t)3 * (DEG + 1) * (DEG + 1) * 256 * sizeof(float)) +
+                      (size_t)kCamChunk * kCamF4 * sizeof(float4) +
+                      (size_t)256 * (ws.views < kCamChunk ? ws.views : kCamChunk) * sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(k_project<DEG, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   trace_begin(kKProject, st);

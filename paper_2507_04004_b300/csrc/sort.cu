@@ -72,6 +72,29 @@ __device__ unsigned long long block_scan(const uint32_t* count, uint32_t* start,
 
 // Bucket (view, tile row) ranges of the row items; capacity check.
 __global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
+  // The projection leaves each view's row-item counts as differences over the
+  // tile rows (+1 at an entry's first row, -1 after its last, modulo 2^32):
+  // a running sum per view, one warp per view, turns them into counts.
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int v = warp; v < ws.views; v += kScanThreads / 32) {
+      uint32_t* c = ws.bucket_count + (int64_t)v * ws.tiles_y;
+      uint32_t carry = 0;
+      for (int t0 = 0; t0 < ws.tiles_y; t0 += 32) {
+        const int ty = t0 + lane;
+        uint32_t x = ty < ws.tiles_y ? c[ty] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, x, o);
+          if (lane >= o) x += y;
+        }
+        x += carry;
+        if (ty < ws.tiles_y) c[ty] = x;
+        carry = __shfl_sync(kFull, x, 31);
+      }
+    }
+    __syncthreads();
+  }
   const unsigned long long total =
       block_scan(ws.bucket_count, ws.bucket_start, ws.bucket_cursor, (int64_t)ws.views * ws.tiles_y);
   if (threadIdx.x == 0) {
