@@ -76,13 +76,12 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
   extern __shared__ float4 s_dyn[];
   constexpr int K = (DEG + 1) * (DEG + 1);
   float* s_shc = reinterpret_cast<float*>(s_dyn);
-  // cameras of the current chunk of views, after the SH columns; then the
-  // CTA's visible entries of the current batch and chunk (256 x chunk slots),
-  // appended with shared atomics and written out with one global reservation
+  // cameras of the current chunk of views, after the SH columns; then each
+  // warp's visible entries of its current batch and chunk (32 x chunk slots
+  // per warp), written out under one global reservation per warp and chunk
   float4* s_cam = s_dyn + (BF16 ? 0 : 3 * K * 256 / 4);
-  uint32_t* s_vis = reinterpret_cast<uint32_t*>(s_cam + kCamChunk * kCamF4);
-  __shared__ uint32_t s_vis_n, s_vis_cnt, s_vis_base;
-  if (threadIdx.x == 0) s_vis_n = 0;
+  const int wcap = 32 * min(ws.views, kCamChunk);
+  uint32_t* w_vis = reinterpret_cast<uint32_t*>(s_cam + kCamChunk * kCamF4) + (threadIdx.x >> 5) * wcap;
   const int64_t n = ws.n;
   const int nb = ws.views * ws.tiles_y;
   const bool smem_buckets = nb <= kMaxBuckets;
@@ -151,6 +150,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         __syncthreads();
       }
       uint32_t cand = 0;
+      int wn = 0;  // entries in this warp's list (warp-uniform)
       for (int j = 0; j < nv; ++j) {
         const int v = v0 + j;
         const float4* cp = s_cam + kCamF4 * j;
@@ -281,29 +281,23 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
           if (ty1 + 1 < ws.tiles_y) atomicAdd(bc + ty1 + 1, 0xffffffffu);
         }
         if (act) ws.rects[e] = ok ? pack_rect(tx0, ty0, tx1, ty1) : empty_rect();
-        // Append visible entries to the CTA's list, one shared atomic per warp.
+        // Append visible entries to the warp's list (positions by ballot).
         const unsigned vis = __ballot_sync(kFull, ok);
-        if (vis) {
-          const int leader = __ffs(vis) - 1;
-          uint32_t slot = 0;
-          if (lane == leader) slot = atomicAdd(&s_vis_n, (uint32_t)__popc(vis));
-          slot = __shfl_sync(kFull, slot, leader);
-          if (ok) s_vis[slot + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
-        }
+        if (ok) w_vis[wn + __popc(vis & ((1u << lane) - 1u))] = (uint32_t)e;
+        wn += __popc(vis);
         seen |= ok;
       }
-      // The CTA's visible entries of this batch and chunk go to the compact
+      // The warp's visible entries of this batch and chunk go to the compact
       // list under one global reservation (one hot counter otherwise takes an
       // atomic per warp step from every SM).
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_vis_cnt = s_vis_n;
-        s_vis_base = s_vis_n ? atomicAdd(ws.counters + kVisibleCount, s_vis_n) : 0u;
-        s_vis_n = 0;
+      if (wn) {
+        uint32_t gb = 0;
+        if (lane == 0) gb = atomicAdd(ws.counters + kVisibleCount, (uint32_t)wn);
+        gb = __shfl_sync(kFull, gb, 0);
+        __syncwarp();  // every lane's list entries before the reads below
+        for (int i = lane; i < wn; i += 32) ws.visible[gb + i] = w_vis[i];
+        __syncwarp();  // read before the next chunk refills the list
       }
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < s_vis_cnt; i += blockDim.x) ws.visible[s_vis_base + i] = s_vis[i];
-      __syncthreads();  // the list is refilled by the next chunk
     }
     // Gaussians seen by some view, for the backward projection pass (one
     // atomic per warp; a warp's Gaussians stay consecutive in the list)
