@@ -125,6 +125,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// One box of a [planes][H][W] FP32 tensor map into L2 (no shared memory, no
+// completion to wait for: a hint).
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
 // Order the block's earlier shared-memory accesses (this thread's, and after
 // a barrier everyone's) before later async-proxy (TMA) writes to the same bytes.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -441,6 +450,11 @@ __global__ void __launch_bounds__(kThreads, 4)
       mbar_expect_tx(bar0, 3 * (uint32_t)kPlaneBytes);
 #pragma unroll
       for (int k = 0; k < 3; ++k) tma_load_3d(smem_u32(sd + k * kPlaneFloats), &map_d, gx0, gy0, 3 * plane + k, bar0);
+      // the epilogue's x, y and dl_dimg tiles, loaded after the vertical
+      // filter, are pulled into L2 now
+      tma_prefetch_l2_3d(&map_x, ex0, ey0, plane);
+      tma_prefetch_l2_3d(&map_y, ex0, ey0, plane);
+      tma_prefetch_l2_3d(&map_dl, ex0, ey0, plane);
     }
     __syncthreads();
     ok = __syncthreads_and(mbar_wait(bar0, 0));
