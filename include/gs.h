@@ -346,18 +346,29 @@ gs_status gs_expand_init(const float* points_dev, const float* rgb_dev, int64_t 
  * array of GS_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
  * library holds until the process exits.  The caller passes the map, the
  * device cameras, the batch geometry and every output; status_dev (device
- * int32) receives GS_OK or GS_ERR_CAPACITY (the pair buffer left in the array
- * was too small; the images are then background only).  Requests whose
- * per-Gaussian and per-tile parts do not fit in the array are rejected with
- * GS_ERR_UNSUPPORTED before anything is enqueued (about V*N*108 bytes plus
- * V*T*16 bytes must stay well below 64 MiB; the rest holds 32 bytes per pair).
- * No cudaMalloc, cudaFree or allocating library routine is called.
+ * int32) receives the batch's device status: GS_OK; GS_ERR_CAPACITY when the
+ * pair buffer left in the array was too small (the images are then
+ * background only: t_final 1, n_contrib 0); or GS_ERR_CUDA if the binning
+ * found its per-tile counts inconsistent (an internal error, not expected).
+ * Requests whose per-Gaussian and per-tile parts do not fit in the array are
+ * rejected with GS_ERR_UNSUPPORTED before anything is enqueued.  Those parts
+ * take V*N*108 bytes (projected records, tile boxes, 2D adjoints, visible
+ * list) + N*4 bytes (Gaussian list) + V*T*16 bytes (per-tile counts, starts,
+ * cursors, bin lists; T tiles per view) + V*ceil(H/16)*12 bytes (per tile-row
+ * counts) + 2048*2*ceil(W/16)*4 bytes (the binning CTAs' count slots, about
+ * 2 MB at 1920 wide), each part rounded up to 256 bytes; whatever is left
+ * holds 32 bytes per (Gaussian, tile) pair.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
  *
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents (each call clears what must start at zero): calls that
- * overlap on the GPU - on two streams, or from two host threads - race. */
+ * cudaGetSymbolAddress (with that device current) and caches it with the id
+ * of the device's CUDA context; a call in another context (after
+ * cudaDeviceReset, or once the primary context was released and created
+ * again) looks it up anew.  Make the first call on a device, and the first
+ * after such a reset, before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (each call clears what must
+ * start at zero): calls that overlap on the GPU - on two streams, or from two
+ * host threads - race. */
 #define GS_NOALLOC_SCRATCH_BYTES (64u << 20)
 gs_status gs_render_fwd_noalloc(const gs_map* map, const gs_camera* cams_dev, const gs_frame* frame,
                                 const gs_config* cfg, float* rgb, float* depth, float* opac, float* t_final,

@@ -12,6 +12,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgsb300.so")
 
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = range(7)
+GS_NOALLOC_SCRATCH_BYTES = 64 << 20  # size of gs_render_fwd_noalloc's device array
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",

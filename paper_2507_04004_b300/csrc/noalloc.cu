@@ -15,25 +15,74 @@
 namespace gsb {
 
 // The scratch workspace.  In host code this name is only a stand-in: the
-// device address is fetched once per device with cudaGetSymbolAddress.
+// device address is fetched once per device (and again after the device's
+// context changed) with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[kMaxDevices] = {};
+// Per device: the scratch address and the id of the CUDA context it was
+// looked up in.  A device reset (cudaDeviceReset) or a new primary context
+// loads the module again, possibly at another address, so the address is
+// looked up again whenever the current context's id differs from the cached one.
+struct NoallocSlot {
+  void* addr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+static NoallocSlot g_noalloc_slot[kMaxDevices];
 
-// Device address of the scratch array on the current device; the first call
-// per device looks it up (with that device current) and caches it.
-static gs_status noalloc_scratch(void** out) {
+// Id of the current CUDA context (cuCtxGetCurrent + cuCtxGetId, reached
+// through the runtime's driver entry-point query so that the library needs
+// no link to the driver library); false if it cannot be read.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+static bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {  // under g_noalloc_mu
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+        q0 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+      get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+    resolved = true;
+  }
+  if (!get_current || !get_id) return false;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current device's context.  The
+// first call per device (and the first after its context changed) looks it
+// up with cudaGetSymbolAddress, with that device current, and caches it.  If
+// the context id cannot be read, every call outside stream capture looks the
+// address up again.
+static gs_status noalloc_scratch(cudaStream_t st, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GS_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return GS_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  NoallocSlot& slot = g_noalloc_slot[dev];
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  const bool fresh = slot.addr && (have_id ? slot.ctx_id == id : cap != cudaStreamCaptureStatusNone);
+  if (!fresh) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
-    g_noalloc_addr[dev] = p;
+    // the symbol lookup made the device's primary context current if it was not
+    if (!have_id) current_context_id(&id);
+    slot.addr = p;
+    slot.ctx_id = id;
   }
-  *out = g_noalloc_addr[dev];
+  *out = slot.addr;
   return GS_OK;
 }
 
@@ -73,8 +122,9 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_map* map, const gs_camera* c
   }
   const int64_t cap = lo;
   if (gs_workspace_layout(map->n, frame, cap, &L) != GS_OK || L.total > limit) return GS_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   void* base = nullptr;
-  gs_status s = noalloc_scratch(&base);
+  gs_status s = noalloc_scratch(st, &base);
   if (s != GS_OK) return s;
   gs_workspace ws;
   ws.ptr = base;
@@ -82,7 +132,6 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_map* map, const gs_camera* c
   ws.pair_capacity = cap;
   ws.frame = *frame;
   const Ws w = resolve_ws(&ws, L);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // launch_project clears the counters and the per-tile counts that the
   // later kernels start from; every other part is written before it is read.
   if (launch_project(*map, cams_dev, *cfg, w, st) != cudaSuccess) return GS_ERR_CUDA;

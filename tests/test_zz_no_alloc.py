@@ -48,6 +48,75 @@ def test_noalloc_matches_workspace_path_on_two_calls():
         assert torch.equal(nc, ref.n_contrib)
 
 
+def _noalloc(N, gm, ct, V, W, H, cfg, with_planes=True):
+    f = dict(device="cuda", dtype=torch.float32)
+    planes = ((torch.full((V, 3, H, W), -1.0, **f), torch.full((V, H, W), -1.0, **f),
+               torch.full((V, H, W), -1.0, **f)) if with_planes else (None, None, None))
+    tf = torch.full((V, H, W), -1.0, **f)
+    nc = torch.full((V, H, W), -1, device="cuda", dtype=torch.int32)
+    status = torch.full((1,), -1, device="cuda", dtype=torch.int32)
+    code = N.gs_render_fwd_noalloc(gm.struct(), ct, N.gs_frame(V, W, H), cfg, *planes, tf, nc, status,
+                                   torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return code, int(status.item()), planes, tf, nc
+
+
+@pytest.mark.gpu
+def test_noalloc_without_colour_depth_and_opacity_planes():
+    """rgb, depth and opac may be NULL: t_final and n_contrib still match the
+    workspace path."""
+    from paper_2507_04004_b300 import _native as N
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor, make_config
+    w = synth.tiny(n=1500, width=96, height=72)
+    gm = GaussianMap.from_host(w.gmap)
+    ct = cameras_tensor(w.cams)
+    ref = Rasterizer(gm.n, 1, 96, 72).render(gm, ct)
+    code, status, _, tf, nc = _noalloc(N, gm, ct, 1, 96, 72, make_config(), with_planes=False)
+    assert code == N.GS_OK and status == N.GS_OK
+    assert float((tf - ref.t_final).abs().max()) <= IMG_TOL
+    assert torch.equal(nc, ref.n_contrib)
+
+
+@pytest.mark.gpu
+def test_noalloc_pair_overflow_reports_capacity_and_background():
+    """A batch whose (Gaussian, tile) pairs exceed what the array leaves after
+    the per-Gaussian parts: the device status is GS_ERR_CAPACITY and the images
+    are background only; a following call that fits is correct again."""
+    import numpy as np
+    from paper_2507_04004_b300 import _native as N
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor, make_config
+    rng = np.random.default_rng(synth.SEED_BASE + 77)
+    # 200k large Gaussians at 256x256: 23 MB of per-Gaussian workspace leave
+    # room for about 1.4M pairs; the scene has several million
+    g = synth.random_map(rng, 200_000, (-4, -4, 2), (4, 4, 12), 0, log_scale_mean=-0.5, log_scale_std=0.2)
+    W = H = 256
+    cam = synth.camera(np.eye(3), np.zeros(3), 100.0, 100.0, W / 2, H / 2, W, H)
+    gm = GaussianMap.from_host(g)
+    ct = cameras_tensor([cam])
+    cfg = make_config()
+    L = N.gs_workspace_layout(g.n, N.gs_frame(1, W, H), 1)
+    cap = (N.GS_NOALLOC_SCRATCH_BYTES - L.total) // 32
+    code, status, (rgb, depth, opac), tf, nc = _noalloc(N, gm, ct, 1, W, H, cfg)
+    assert code == N.GS_OK
+    assert status == N.GS_ERR_CAPACITY, status
+    assert bool((tf == 1.0).all()) and bool((nc == 0).all())
+    assert float(rgb.abs().max()) == 0.0 and float(depth.abs().max()) == 0.0 and float(opac.abs().max()) == 0.0
+    # the workspace path needs more pairs than the array could hold
+    rast = Rasterizer(gm.n, 1, W, H)
+    rast.render(gm, ct)
+    code, needed = rast.status()
+    assert code == N.GS_OK and needed > cap, (needed, cap)
+    # the next call that fits starts from a clean status
+    w = synth.tiny(n=1500, width=96, height=72)
+    gs = GaussianMap.from_host(w.gmap)
+    cs = cameras_tensor(w.cams)
+    ref = Rasterizer(gs.n, 1, 96, 72).render(gs, cs)
+    code, status, (rgb, _, _), tf, nc = _noalloc(N, gs, cs, 1, 96, 72, cfg)
+    assert code == N.GS_OK and status == N.GS_OK
+    assert float((rgb - ref.rgb).abs().max()) <= IMG_TOL
+    assert torch.equal(nc, ref.n_contrib)
+
+
 def test_noalloc_rejects_requests_larger_than_its_array():
     from paper_2507_04004_b300 import build as B
     B.build()
