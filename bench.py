@@ -469,6 +469,10 @@ def run_tracking(args, dev):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # camera factor option 2's residual r = Log(T(t) T~^-1) per frame, with T(t) the poses tracking
+    # started from (the trajectory's prediction) and, for reference, the true poses
+    res = tr.residual(q).cpu().numpy().astype(np.float64)
+    res_gt = tr.residual(cameras_tensor(w.meta["gt_cams"], device=dev)).cpu().numpy().astype(np.float64)
     xi = xi.cpu().numpy().astype(np.float64)
     true = -w.meta["xi"]
     rot0 = np.degrees(np.linalg.norm(true[:, 3:], axis=1))
@@ -481,6 +485,11 @@ def run_tracking(args, dev):
             "ms_per_iteration": round(ms / 30, 4),
             "rot_err_deg_median": [round(float(np.median(rot0)), 4), round(float(np.median(rot1)), 4)],
             "trans_err_m_median": [round(float(np.median(tr0)), 4), round(float(np.median(tr1)), 4)],
+            "residual_log_median": {
+                "vs_start_pose": {"rho_m": round(float(np.median(np.linalg.norm(res[:, :3], axis=1))), 4),
+                                  "theta_deg": round(float(np.degrees(np.median(np.linalg.norm(res[:, 3:], axis=1)))), 4)},
+                "vs_true_pose": {"rho_m": round(float(np.median(np.linalg.norm(res_gt[:, :3], axis=1))), 4),
+                                 "theta_deg": round(float(np.degrees(np.median(np.linalg.norm(res_gt[:, 3:], axis=1)))), 4)}},
             "note": "errors [before, after]; timed: the captured 30-iteration graph incl. the status read-back"}
 
 

@@ -274,6 +274,20 @@ gs_status gs_adam_pose(float* xi_dev, float* grad_dev, float* m_dev, float* v_de
                        int32_t n_views, const gs_adam_config* cfg, const float* loss_dev, float* best_loss_dev,
                        float* best_xi_dev, gs_stream_t stream);
 
+/* Photometric residual of camera factor option 2 (Sec. "Camera Factor
+ * (Option 2)", Eq. map_optimize_pose): r = Log(T(t) T~^-1), with T(t) the
+ * camera-to-world pose of the continuous-time trajectory at the frame's time
+ * and T~ the pose the tracker optimised.  The library's cameras are
+ * world-to-camera (A = T(t)^-1 in cams_traj_dev, B = T~^-1 in cams_opt_dev,
+ * device arrays of n_views), so r_v = Log(A_v^-1 B_v): the twist (rho, theta),
+ * translation first, with B_v = A_v Exp(r_v) under gs_pose_apply's Exp (for
+ * B = gs_pose_apply(A, xi), r = xi).  Rotation angles are returned in [0, pi];
+ * r_dev [V][6] FP32 device.  Only R and t of the cameras are read (not the
+ * intrinsics).  GS_ERR_ARG for missing pointers or
+ * n_views < 1. */
+gs_status gs_pose_residual(const gs_camera* cams_traj_dev, const gs_camera* cams_opt_dev, int32_t n_views,
+                           float* r_dev, gs_stream_t stream);
+
 /* Sparse Adam over the map (Sec. "Additional Strategies" (a)): one Adam step
  * (Kingma and Ba, bias corrected with the device step counter step_dev,
  * advanced by one) on the Gaussians that took part in the workspace's last

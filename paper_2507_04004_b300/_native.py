@@ -17,7 +17,7 @@ GS_NOALLOC_SCRATCH_BYTES = 64 << 20  # size of gs_render_fwd_noalloc's device ar
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
             "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
-            "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
+            "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
@@ -108,6 +108,7 @@ def lib():
         L.gs_dssim_scratch_bytes.restype = C.c_size_t
         L.gs_dssim.argtypes = [P, P, I32, I32, I32, F, P, P, P, P]
         L.gs_pose_apply.argtypes = [P, P, I32, P, P]
+        L.gs_pose_residual.argtypes = [P, P, I32, P, P]
         L.gs_unpack_keyframes.argtypes = [P, I32, I32, I32, P, P, P, P, P, P]
         L.gs_expand_scratch_bytes.argtypes = [I64]
         L.gs_expand_scratch_bytes.restype = C.c_size_t
@@ -127,7 +128,7 @@ def lib():
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
                      "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
-                     "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_adam_pose",
+                     "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose",
                      "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes"):
             getattr(L, name).restype = I32
         _lib = L
@@ -227,6 +228,11 @@ def gs_dssim(img, tgt, n_views: int, height: int, width: int, weight: float, los
 def gs_pose_apply(cams0, xi, n_views: int, cams_out, stream: int) -> None:
     check("gs_pose_apply", lib().gs_pose_apply(_ptr(cams0), _ptr(xi), int(n_views), _ptr(cams_out),
                                                C.c_void_p(stream)))
+
+
+def gs_pose_residual(cams_traj, cams_opt, n_views: int, r, stream: int) -> None:
+    check("gs_pose_residual", lib().gs_pose_residual(_ptr(cams_traj), _ptr(cams_opt), int(n_views), _ptr(r),
+                                                     C.c_void_p(stream)))
 
 
 def gs_adam_pose(xi, grad, m, v, step, n_views: int, cfg: "gs_adam_config", stream: int, loss=None,

@@ -367,6 +367,13 @@ gs_status gs_pose_apply(const gs_camera* cams0_dev, const float* xi_dev, int32_t
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_pose_residual(const gs_camera* cams_traj_dev, const gs_camera* cams_opt_dev, int32_t n_views,
+                           float* r_dev, gs_stream_t stream) {
+  if (!cams_traj_dev || !cams_opt_dev || !r_dev || n_views < 1) return GS_ERR_ARG;
+  return cuda_status(launch_pose_residual(cams_traj_dev, cams_opt_dev, n_views, r_dev,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
 gs_status gs_adam_pose(float* xi_dev, float* grad_dev, float* m_dev, float* v_dev, int32_t* step_dev,
                        int32_t n_views, const gs_adam_config* cfg, const float* loss_dev, float* best_loss_dev,
                        float* best_xi_dev, gs_stream_t stream) {

@@ -39,6 +39,7 @@ cudaError_t launch_expand_init(const float* pts, const float* rgb, int64_t P, co
                                const uint32_t* count, const gs_camera* cam, int64_t first, int64_t n_dst,
                                int32_t sh_degree, float logit_init, const gs_param_set& dst, cudaStream_t st);
 cudaError_t launch_pose_apply(const gs_camera* cams0, const float* xi, int V, gs_camera* cams_out, cudaStream_t st);
+cudaError_t launch_pose_residual(const gs_camera* cams_a, const gs_camera* cams_b, int V, float* r, cudaStream_t st);
 cudaError_t launch_adam_pose(float* xi, float* grad, float* m, float* s, int32_t* step, int V,
                              const gs_adam_config& hp, const float* loss, float* best_loss, float* best_xi,
                              cudaStream_t st);

@@ -93,6 +93,77 @@ __global__ void k_adam_pose(float* __restrict__ xi, float* __restrict__ grad, fl
   if (threadIdx.x == 0) *step = t;
 }
 
+// Photometric residual of camera factor option 2 (Eq. map_optimize_pose):
+// r = Log(T(t) T~^-1) with T(t) and T~ camera-to-world.  The library's
+// cameras are world-to-camera, A = T(t)^-1 and B = T~^-1, so r = Log(A^-1 B),
+// the twist (rho, theta) with Exp(r) = A^-1 B: B = A Exp(r), the convention of
+// k_pose_apply (for B = T0 Exp(xi) and A = T0, r = xi).
+//   rotation: theta = p u from the unit quaternion (w, v) of R = R_A^T R_B
+//     (largest-pivot extraction), p = 2 atan2(|v|, w) in [0, pi] with w >= 0
+//     (well conditioned at 0 and at pi, unlike acos of the trace);
+//   translation: rho = V^-1 t, t = R_A^T (t_B - t_A),
+//     V^-1 = I - 1/2 [theta]x + c [theta]x^2,
+//     c = (1 - (p/2) cot(p/2)) / p^2, by its series 1/12 + p^2/720 + p^4/30240
+//     below p = 0.5 (the closed form cancels there).
+__global__ void k_pose_residual(const gs_camera* __restrict__ cams_a, const gs_camera* __restrict__ cams_b, int V,
+                                float* __restrict__ r) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const gs_camera A = cams_a[v], B = cams_b[v];
+  float R[3][3], t[3];
+  const float dt[3] = {B.t[0] - A.t[0], B.t[1] - A.t[1], B.t[2] - A.t[2]};
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j)
+      R[i][j] = A.R[0 * 3 + i] * B.R[0 * 3 + j] + A.R[1 * 3 + i] * B.R[1 * 3 + j] + A.R[2 * 3 + i] * B.R[2 * 3 + j];
+    t[i] = A.R[0 * 3 + i] * dt[0] + A.R[1 * 3 + i] * dt[1] + A.R[2 * 3 + i] * dt[2];
+  }
+  // quaternion (qw, qx, qy, qz) of R, pivot on the largest of 4 qw^2, 4 qx^2, 4 qy^2, 4 qz^2
+  const float tr = R[0][0] + R[1][1] + R[2][2];
+  float qw, qx, qy, qz;
+  if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + tr, 1e-30f));  // 4 qw
+    qw = 0.25f * s; qx = (R[2][1] - R[1][2]) / s; qy = (R[0][2] - R[2][0]) / s; qz = (R[1][0] - R[0][1]) / s;
+  } else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[0][0] - R[1][1] - R[2][2], 1e-30f));  // 4 qx
+    qw = (R[2][1] - R[1][2]) / s; qx = 0.25f * s; qy = (R[0][1] + R[1][0]) / s; qz = (R[0][2] + R[2][0]) / s;
+  } else if (R[1][1] >= R[2][2]) {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[1][1] - R[0][0] - R[2][2], 1e-30f));  // 4 qy
+    qw = (R[0][2] - R[2][0]) / s; qx = (R[0][1] + R[1][0]) / s; qy = 0.25f * s; qz = (R[1][2] + R[2][1]) / s;
+  } else {
+    const float s = 2.f * sqrtf(fmaxf(1.f + R[2][2] - R[0][0] - R[1][1], 1e-30f));  // 4 qz
+    qw = (R[1][0] - R[0][1]) / s; qx = (R[0][2] + R[2][0]) / s; qy = (R[1][2] + R[2][1]) / s; qz = 0.25f * s;
+  }
+  if (qw < 0.f) { qw = -qw; qx = -qx; qy = -qy; qz = -qz; }
+  const float sv = sqrtf(qx * qx + qy * qy + qz * qz);
+  const float p = 2.f * atan2f(sv, qw);
+  // theta = p v / |v|; as |v| -> 0, p / |v| -> 2 / qw
+  const float k = sv > 0.f ? p / sv : 2.f / fmaxf(qw, 1e-30f);
+  const float w0 = k * qx, w1 = k * qy, w2 = k * qz;
+  const float p2 = w0 * w0 + w1 * w1 + w2 * w2;
+  float c;
+  if (p2 < 0.25f) {
+    c = 1.f / 12.f + p2 * (1.f / 720.f + p2 * (1.f / 30240.f));
+  } else {
+    const float hp = 0.5f * sqrtf(p2);
+    c = (1.f - hp * cosf(hp) / sinf(hp)) / p2;
+  }
+  // V^-1 t = t - 1/2 theta x t + c theta x (theta x t)
+  const float cx0 = w1 * t[2] - w2 * t[1], cx1 = w2 * t[0] - w0 * t[2], cx2 = w0 * t[1] - w1 * t[0];
+  const float dx0 = w1 * cx2 - w2 * cx1, dx1 = w2 * cx0 - w0 * cx2, dx2 = w0 * cx1 - w1 * cx0;
+  float* o = r + 6 * v;
+  o[0] = t[0] - 0.5f * cx0 + c * dx0;
+  o[1] = t[1] - 0.5f * cx1 + c * dx1;
+  o[2] = t[2] - 0.5f * cx2 + c * dx2;
+  o[3] = w0;
+  o[4] = w1;
+  o[5] = w2;
+}
+
+cudaError_t launch_pose_residual(const gs_camera* cams_a, const gs_camera* cams_b, int V, float* r, cudaStream_t st) {
+  k_pose_residual<<<(V + 63) / 64, 64, 0, st>>>(cams_a, cams_b, V, r);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pose_apply(const gs_camera* cams0, const float* xi, int V, gs_camera* cams_out, cudaStream_t st) {
   k_pose_apply<<<(V + 63) / 64, 64, 0, st>>>(cams0, xi, V, cams_out);
   return cudaGetLastError();

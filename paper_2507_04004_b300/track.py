@@ -15,7 +15,9 @@ theta)); one iteration is
     Adam step on xi                           gs_adam_pose
 
 and the N_t iterations are captured once as a CUDA graph and replayed per
-batch.  All of it runs in the library's kernels.
+batch.  After tracking, :meth:`PoseTracker.residual` forms the photometric
+residual r = Log(T(t) T~^-1) of Eq. map_optimize_pose that the factor graph
+consumes (gs_pose_residual).  All of it runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -138,3 +140,20 @@ class PoseTracker:
             if code != N.GS_OK:
                 raise N.GsError("track", code)
         return self.best_xi, self.loss_hist
+
+    def optimised_cameras(self) -> torch.Tensor:
+        """[V][16] cameras at the tracked poses cams0_v Exp(xi_v) of the last
+        :meth:`track` call (the best iterate per frame)."""
+        out = torch.empty_like(self.cams0)
+        N.gs_pose_apply(self.cams0, self.best_xi, self.V, out, self._stream())
+        return out
+
+    def residual(self, cams_traj: torch.Tensor | None = None) -> torch.Tensor:
+        """r [V][6] = Log(T(t) T~^-1) (Eq. map_optimize_pose, camera-to-world
+        T(t), T~) as (rho, theta): ``cams_traj`` [V][16] holds the trajectory's
+        poses T(t) as world-to-camera cameras (default: the initial poses of the
+        last :meth:`track` call), T~ is the tracked pose."""
+        a = self.cams0 if cams_traj is None else cams_traj.contiguous()
+        r = torch.empty(self.V, 6, device=self.device, dtype=torch.float32)
+        N.gs_pose_residual(a, self.optimised_cameras(), self.V, r, self._stream())
+        return r

@@ -52,6 +52,65 @@ def test_pose_apply_matches_matrix_exponential():
         np.testing.assert_array_equal(got[v, 12:], c0.cpu().numpy()[v, 12:])
 
 
+def _se3(R, t):
+    T = np.eye(4)
+    T[:3, :3] = np.asarray(R, np.float64).reshape(3, 3)
+    T[:3, 3] = np.asarray(t, np.float64).reshape(3)
+    return T
+
+
+def test_pose_residual_matches_matrix_logarithm():
+    """gs_pose_residual against scipy's matrix logarithm of A^-1 B (A, B the
+    world-to-camera poses, i.e. Log(T(t) T~^-1) with camera-to-world T), at
+    relative rotations of 0, 1e-6, 0.3, pi/2, 2.5 and 3.1 rad; Exp(Log(.))
+    through gs_pose_apply gives B back, and B = A Exp(xi) gives xi back."""
+    from scipy.linalg import logm
+    from paper_2507_04004_b300 import _native as N
+    from paper_2507_04004_b300.raster import cameras_tensor
+    rng = np.random.default_rng(23)
+    angles = [0.0, 1e-6, 0.3, np.pi / 2, 2.5, 3.1, 1e-3, 1.0]
+    A, B = [], []
+    for k, ang in enumerate(angles):
+        Ra = Rotation.random(random_state=100 + k).as_matrix()
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        Rrel = Rotation.from_rotvec(ang * axis).as_matrix()
+        ta = rng.normal(0, 5.0, 3)
+        trel = rng.normal(0, 0.5, 3)
+        A.append(synth.camera(Ra, ta, 500.0, 500.0, 320.0, 256.0, 640, 512))
+        Tb = _se3(Ra, ta) @ _se3(Rrel, trel)
+        B.append(synth.camera(Tb[:3, :3], Tb[:3, 3], 500.0, 500.0, 320.0, 256.0, 640, 512))
+    V = len(angles)
+    ca, cb = cameras_tensor(A), cameras_tensor(B)
+    r = torch.empty(V, 6, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    N.gs_pose_residual(ca, cb, V, r, st)
+    got = r.cpu().numpy().astype(np.float64)
+    for v in range(V):
+        Ta = _se3(A[v]["R"], A[v]["t"])  # the float32 values, in float64
+        Tb = _se3(B[v]["R"], B[v]["t"])
+        X = np.real(logm(np.linalg.inv(Ta) @ Tb))
+        want = np.array([X[0, 3], X[1, 3], X[2, 3], X[2, 1], X[0, 2], X[1, 0]])
+        scale = max(1.0, np.abs(want[:3]).max())
+        np.testing.assert_allclose(got[v, 3:], want[3:], atol=2e-5, err_msg=f"theta, angle {angles[v]}")
+        np.testing.assert_allclose(got[v, :3], want[:3], atol=2e-5 * scale, err_msg=f"rho, angle {angles[v]}")
+        assert abs(np.linalg.norm(got[v, 3:]) - angles[v]) < 2e-5
+    # Exp(Log(A^-1 B)) = A^-1 B: A Exp(r) reproduces B
+    back = torch.empty_like(ca)
+    N.gs_pose_apply(ca, r, V, back, st)
+    np.testing.assert_allclose(back.cpu().numpy()[:, :12], cb.cpu().numpy()[:, :12], atol=5e-5)
+    # B = A Exp(xi): the residual is xi (rotation angles below pi)
+    xi = rng.normal(0, 0.3, (V, 6)).astype(np.float32)
+    xi[0] = 0.0
+    xi[1, 3:] = [2e-7, -1e-7, 3e-7]
+    xi[2, 3:] = [1.2, -2.0, 1.5]  # |theta| = 2.77 rad
+    xt = torch.as_tensor(xi, device="cuda")
+    cx = torch.empty_like(ca)
+    N.gs_pose_apply(ca, xt, V, cx, st)
+    N.gs_pose_residual(ca, cx, V, r, st)
+    np.testing.assert_allclose(r.cpu().numpy(), xi, atol=3e-5)
+
+
 def test_adam_step_matches_definition():
     from paper_2507_04004_b300 import _native as N
     rng = np.random.default_rng(21)
@@ -150,6 +209,12 @@ def test_tracker_reduces_pose_error_on_the_tracking_workload():
     assert np.mean(e1_rot < e0_rot) >= 0.8
     assert np.median(e1_rot) < 0.8 * np.median(e0_rot)
     assert np.median(e1_tr) <= 1.1 * np.median(e0_tr)
+    # the factor-graph residual Log(T(t) T~^-1) against the poses tracking started from is the kept xi;
+    # against the true poses it is the remaining pose error, smaller in rotation than at the start
+    r = tr.residual().cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(r, xi, atol=3e-5)
+    r_gt = tr.residual(gt).cpu().numpy().astype(np.float64)
+    assert np.median(np.linalg.norm(r_gt[:, 3:], axis=1)) < 0.8 * np.median(e0_rot)
     # a second batch replays the captured graph and gives the same result
     xi2, _ = tr.track(cameras_tensor(w.cams), targets)
     np.testing.assert_allclose(xi2.cpu().numpy(), xi, rtol=0, atol=1e-5)
