@@ -514,27 +514,94 @@ class Server:
 
 class PlainRenderer:
     """One request at a time, one launch sequence per request, no graphs: the
-    reference point for the server."""
+    reference point for the server.
 
-    def __init__(self, gmap: GaussianMap, device="cuda"):
+    By default (``checked=False``) a request runs the way the server runs a
+    batch, minus the batching and the graphs: the camera (and pixel list) go
+    up from pinned host memory, nothing is read back between sort and blend,
+    the results are copied asynchronously into pinned host tensors, and the
+    status is read once, when the request's work has finished (a pair-buffer
+    overflow is then retried with a larger buffer).  ``checked=True`` is the
+    simplest plain loop: the status is read back after the sort (a full
+    synchronisation before the blend) and results come back with ``.cpu()``
+    (pageable copies)."""
+
+    def __init__(self, gmap: GaussianMap, device="cuda", checked: bool = False):
         self.gmap = gmap
         self.device = torch.device(device)
+        self.checked = bool(checked)
         self.rasts = {}
+        self.outs = {}
+        self.retries = 0
+        self.cams = torch.zeros(1, 16, device=self.device)
+        self.host_cams = torch.empty(1, 16, pin_memory=True)
+        self.status = torch.zeros(2, dtype=torch.int32, device=self.device)
+        self.host_status = torch.zeros(2, dtype=torch.int32, pin_memory=True)
+        self.event = torch.cuda.Event()
+        self.pix = {}
 
-    def run(self, req: Request):
+    def _setup(self, req):
         kind, W, H, npix = req.key
         key = (W, H)
         if key not in self.rasts:
             self.rasts[key] = Rasterizer(self.gmap.n, 1, W, H, device=self.device)
-        rast = self.rasts[key]
-        cams = cameras_tensor([req.camera], device=self.device)
-        out = rast.render(self.gmap, cams, check=True)
+            f = dict(device=self.device, dtype=torch.float32)
+            self.outs[key] = RenderOut(torch.empty(1, 3, H, W, **f), torch.empty(1, H, W, **f),
+                                       torch.empty(1, H, W, **f), torch.empty(1, H, W, **f),
+                                       torch.empty(1, H, W, dtype=torch.int32, device=self.device))
+        return kind, key, self.rasts[key]
+
+    def run(self, req: Request):
+        kind, key, rast = self._setup(req)
+        if self.checked:
+            cams = cameras_tensor([req.camera], device=self.device)
+            out = rast.render(self.gmap, cams, check=True)
+            if kind == "jacobian":
+                pix = torch.as_tensor(req.pix, device=self.device).view(1, -1)
+                J, rgb = rast.pose_jacobian(self.gmap, cams, pix)
+                J, rgb = J[0].cpu().numpy(), rgb[0].cpu().numpy()
+                return dict(J=J, rgb=rgb, residual=rgb - (req.target if req.target is not None else 0.0))
+            return dict(rgb=out.rgb[0].cpu().numpy(), depth=out.depth[0].cpu().numpy())
+        self.host_cams[0] = torch.as_tensor(cameras_tensor([req.camera], device="cpu")[0])
+        self.cams.copy_(self.host_cams, non_blocking=True)
         if kind == "jacobian":
-            pix = torch.as_tensor(req.pix, device=self.device).view(1, -1)
-            J, rgb = rast.pose_jacobian(self.gmap, cams, pix)
-            J, rgb = J[0].cpu().numpy(), rgb[0].cpu().numpy()
-            return dict(J=J, rgb=rgb, residual=rgb - (req.target if req.target is not None else 0.0))
-        return dict(rgb=out.rgb[0].cpu().numpy(), depth=out.depth[0].cpu().numpy())
+            npix = len(req.pix)
+            if npix not in self.pix:
+                self.pix[npix] = (torch.zeros(1, npix, dtype=torch.int32, device=self.device),
+                                  torch.empty(1, npix, dtype=torch.int32, pin_memory=True))
+            pix, host_pix = self.pix[npix]
+            host_pix[0] = torch.as_tensor(req.pix)
+            pix.copy_(host_pix, non_blocking=True)
+        out = self.outs[key]
+        while True:
+            rast.render(self.gmap, self.cams, check=False, out=out)
+            if kind == "jacobian":
+                J, jrgb = rast.pose_jacobian(self.gmap, self.cams, pix)
+                a = torch.empty(J.shape[1:], pin_memory=True)
+                b = torch.empty(jrgb.shape[1:], pin_memory=True)
+                a.copy_(J[0], non_blocking=True)
+                b.copy_(jrgb[0], non_blocking=True)
+            else:
+                a = torch.empty(out.rgb.shape[1:], pin_memory=True)
+                b = torch.empty(out.depth.shape[1:], pin_memory=True)
+                a.copy_(out.rgb[0], non_blocking=True)
+                b.copy_(out.depth[0], non_blocking=True)
+            self.status.copy_(rast._view(rast.layout.counters, 2, torch.int32))
+            self.host_status.copy_(self.status, non_blocking=True)
+            self.event.record()
+            self.event.synchronize()
+            code, needed = int(self.host_status[0]), int(self.host_status[1])
+            if code == N.GS_OK:
+                break
+            if code != N.GS_ERR_CAPACITY:
+                raise N.GsError("plain render", code)
+            self.retries += 1
+            rast.capacity = int(1.25 * needed) + 1024
+            rast._alloc()
+        if kind == "jacobian":
+            rgb = b.numpy()
+            return dict(J=a.numpy(), rgb=rgb, residual=rgb - (req.target if req.target is not None else 0.0))
+        return dict(rgb=a.numpy(), depth=b.numpy())
 
 
 def latency_stats(reqs):

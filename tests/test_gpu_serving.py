@@ -49,8 +49,12 @@ def test_results_alone_equal_results_in_the_mix(use_graphs):
     assert srv.batches < len(reqs)
     assert srv.max_inflight_bytes <= max(budget, max(r.bytes for rs in srv.runners.values() for r in rs))
     plain = PlainRenderer(gm)
+    checked = PlainRenderer(gm, checked=True)
     for r, got in zip(reqs, res):
         alone = plain.run(r)
+        simple = checked.run(r)  # the plain loop with a status read-back between sort and blend
+        for k in alone:
+            assert np.array_equal(alone[k], simple[k])
         if r.kind == "render":
             assert np.array_equal(got["rgb"], alone["rgb"]) and np.array_equal(got["depth"], alone["depth"])
         else:
