@@ -17,3 +17,15 @@ def oracle():
     from oracle import oracle as O
     O.build()
     return O
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print what the parity tests measured (pair counts, error figures)."""
+    try:
+        from tests.gpu_cases import REPORT
+    except ImportError:
+        return
+    if REPORT:
+        terminalreporter.section("parity report")
+        for line in REPORT:
+            terminalreporter.write_line(line)

@@ -94,7 +94,7 @@ def test_mapping_benchmark_workload_sampled(oracle):
     t = lambda a: torch.as_tensor(a, device="cuda")
     g = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
     o = _oracle_rect_grads(oracle, m, w.cams, (0, 3), RECTS_1080, er, ed, eo)
-    assert_grads_close(g, o, GRAD_KEYS)
+    assert_grads_close(g, o, GRAD_KEYS, label="1M SH3 4x1080p, sampled rectangles")
     for v in (0, 3):
         assert rel_err(g["pose"][v], o["pose"][v]) <= GRAD_TOL, v
     assert np.abs(g["pose"][1]).max() == 0 and np.abs(g["pose"][2]).max() == 0
@@ -122,7 +122,7 @@ def test_mapping_500k_4x720p_sampled(oracle):
     t = lambda a: torch.as_tensor(a, device="cuda")
     g = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
     o = _oracle_rect_grads(oracle, m, w.cams, (0, 3), RECTS_720, er, ed, eo)
-    assert_grads_close(g, o, GRAD_KEYS)
+    assert_grads_close(g, o, GRAD_KEYS, label="500k SH3 4x720p, sampled rectangles")
     for v in (0, 3):
         assert rel_err(g["pose"][v], o["pose"][v]) <= GRAD_TOL, v
 
@@ -171,6 +171,7 @@ def test_precision_2m_gaussians_8_views_sampled(oracle, sh_bf16, capsys):
     g = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
     o = _oracle_rect_grads(oracle, m, w.cams, (5,), RECTS_1080, er, ed, eo)
     gerr = {k: rel_err(g[k], o[k]) for k in GRAD_KEYS}
+    assert_grads_close(g, o, GRAD_KEYS, label=f"2M SH3 8x1080p {'BF16' if sh_bf16 else 'FP32'} SH, sampled rectangles")
     with capsys.disabled():
         print(f"\nprecision {'BF16' if sh_bf16 else 'FP32'} SH: max abs rgb {worst['rgb']:.2e} opac {worst['opac']:.2e} "
               f"depth/scale {worst['depth']:.2e}; mean abs rgb {np.mean(means['rgb']):.2e} "

@@ -71,13 +71,32 @@ def test_tiny_forward_tiles_and_images(oracle):
     m = host_map(w.gmap)
     rast, gm, ct, out = gpu_render(w.gmap, w.cams)
     assert rast.status()[0] == 0
-    n_margin = compare_tiles(oracle, m, w.cams[0], rast, 0)
-    assert n_margin <= 5
+    n_margin = compare_tiles(oracle, m, w.cams[0], rast, 0, label="tiny scene 2k Gaussians 128x96")
+    assert n_margin == 0  # no pair of this scene lies within the threshold margin
     o_r = oracle.render(m, w.cams[0])
     _check_images(o_r, out, 0, "tiny")
     np.testing.assert_allclose(out.t_final[0].cpu().numpy()[o_r["flags"] == 0], o_r["t_final"][o_r["flags"] == 0],
                                atol=IMG_TOL)
     _check_last_contributor(rast, out, o_r, 0)
+
+
+def test_blend_counts_split_evaluations(oracle):
+    """gs_blend_counts: per view, the evaluations up to each pixel's last
+    contributor (= sum of n_contrib) and how many of them were blended
+    (= the oracle's count of blended Gaussians per pixel, summed)."""
+    from paper_2507_04004_b300 import _native as N
+    g, cams = _mapping_small(n=8000)
+    m = host_map(g)
+    rast, gm, ct, out = gpu_render(g, cams)
+    counts = torch.zeros(len(cams), 2, dtype=torch.int64, device="cuda")
+    N.gs_blend_counts(rast.cfg, rast.ws, counts, torch.cuda.current_stream().cuda_stream)
+    c = counts.cpu().numpy()
+    for v, cam in enumerate(cams):
+        assert c[v, 0] == int(out.n_contrib[v].to(torch.int64).sum())
+        o = oracle.render(m, cam)
+        nflag = int((o["flags"] != 0).sum())
+        assert abs(int(c[v, 1]) - int(o["n_contrib"].sum())) <= 8 * nflag, (v, c[v], int(o["n_contrib"].sum()), nflag)
+        assert 0 < c[v, 1] <= c[v, 0]
 
 
 def test_projection_records_match_oracle(oracle):
@@ -125,7 +144,7 @@ def test_offscreen_gaussians_reaching_into_the_image(oracle):
     ot, og, _ = oracle.tiles(m, cams[0])
     assert np.isin(np.nonzero(outside)[0], og).sum() > 300  # many off-screen centres do reach in
     for view, cam in enumerate(cams):
-        compare_tiles(oracle, m, cam, rast, view)
+        compare_tiles(oracle, m, cam, rast, view, label=f"off-screen centres view {view}")
 
 
 @pytest.mark.parametrize("sh_bf16,degenerate", [(False, 0.0), (True, 0.01)])
@@ -134,7 +153,7 @@ def test_multiview_ragged_sh3(oracle, sh_bf16, degenerate):
     m = host_map(g, sh_bf16)
     rast, gm, ct, out = gpu_render(g, cams, sh_bf16=sh_bf16)
     for v, cam in enumerate(cams):
-        compare_tiles(oracle, m, cam, rast, v)
+        compare_tiles(oracle, m, cam, rast, v, label=f"20k SH3 200x120 bf16={sh_bf16} view {v}")
         o_r = oracle.render(m, cam)
         _check_images(o_r, out, v, f"view {v}")
         _check_last_contributor(rast, out, o_r, v)
@@ -150,7 +169,7 @@ def test_long_tiles_and_merge_path(oracle):
     rast, gm, ct, out = gpu_render(g, [cam])
     _, count, _ = rast.tile_lists()
     assert int(count.max()) > 16384
-    compare_tiles(oracle, m, cam, rast, 0)
+    compare_tiles(oracle, m, cam, rast, 0, label="bins > 16,384 keys (merge path)")
     o_r = oracle.render(m, cam)
     _check_images(o_r, out, 0, "long tiles")
 
@@ -168,7 +187,7 @@ def test_bin_size_classes(oracle, n, lo, hi):
     _, count, _ = rast.tile_lists()
     c = count.cpu().numpy()
     assert ((c >= lo) & (c <= hi)).any(), c
-    compare_tiles(oracle, m, cam, rast, 0)
+    compare_tiles(oracle, m, cam, rast, 0, label=f"bins of {lo}..{hi} keys")
     _check_images(oracle.render(m, cam), out, 0, f"bins of {lo}..{hi} keys")
 
 
@@ -237,7 +256,7 @@ def test_tiny_fused_loss_gradients(oracle, backward):
     g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth))
     o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=tgt_d, w_rgb=w.w_rgb, w_depth=w.w_depth)
     assert g["loss"][0] == pytest.approx(o["loss"][0], rel=1e-4)
-    assert_grads_close(g, o, GRAD_KEYS)
+    assert_grads_close(g, o, GRAD_KEYS, label=f"tiny fused loss, {backward} backward")
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
 
 
@@ -293,7 +312,7 @@ def test_alpha_clamp_path(oracle, backward):
     td = torch.as_tensor(tgt_d, device="cuda")
     g = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=tr, tgt_depth=td, w_rgb=w.w_rgb, w_depth=w.w_depth))
     o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=tgt_d, w_rgb=w.w_rgb, w_depth=w.w_depth)
-    assert_grads_close(g, o, GRAD_KEYS)
+    assert_grads_close(g, o, GRAD_KEYS, label=f"clamped alpha, {backward} backward")
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
     pix = np.sort(rng.choice(96 * 128, 400, replace=False)).astype(np.int32)[None]
     J, rgb = rast.pose_jacobian(gm, ct, torch.as_tensor(pix, device="cuda"))
@@ -317,7 +336,7 @@ def test_multiview_external_adjoint_gradients(oracle, sh_bf16, backward):
     t = lambda a: torch.as_tensor(a, device="cuda")
     gg = grads_to_numpy(rast.backward(gm, ct, out, dl_drgb=t(er), dl_ddepth=t(ed), dl_dopac=t(eo)))
     o = oracle.backward(m, cams, ext_rgb=er, ext_depth=ed, ext_opac=eo)
-    assert_grads_close(gg, o, GRAD_KEYS)
+    assert_grads_close(gg, o, GRAD_KEYS, label=f"3 views SH3 external adjoints bf16={sh_bf16}, {backward} backward")
     for v in range(V):
         assert rel_err(gg["pose"][v], o["pose"][v]) <= GRAD_TOL, v
 
@@ -333,7 +352,7 @@ def test_mapping_fused_loss_with_lidar_depth(oracle, backward):
                                      w_depth=w.w_depth))
     o = oracle.backward(m, w.cams, tgt_rgb=w.tgt_rgb, tgt_depth=w.tgt_depth, w_rgb=w.w_rgb, w_depth=w.w_depth)
     np.testing.assert_allclose(g["loss"], o["loss"], rtol=1e-4)
-    assert_grads_close(g, o, GRAD_KEYS)
+    assert_grads_close(g, o, GRAD_KEYS, label=f"small mapping copy with LiDAR depth, {backward} backward")
     assert rel_err(g["pose"], o["pose"]) <= GRAD_TOL
 
 
@@ -403,7 +422,7 @@ def test_equal_depth_keys_sort_by_index(oracle, n):
     cam = synth.camera(np.eye(3), np.zeros(3), 60.0, 60.0, 24.0, 24.0, 48, 48)
     rast, gm, ct, out = gpu_render(g, [cam])
     assert len(set(oracle.depth_keys(host_map(g), cam).tolist())) == 1
-    compare_tiles(oracle, host_map(g), cam, rast, 0)
+    compare_tiles(oracle, host_map(g), cam, rast, 0, label=f"{n} equal depth keys")
     _check_images(oracle.render(host_map(g), cam), out, 0, "equal depths")
 
 
@@ -426,7 +445,7 @@ def test_bucket_backward_long_contributor_lists(oracle):
         assert int(out.n_contrib.max()) > 8 * 32
         res[backward] = grads_to_numpy(rast.backward(gm, ct, out, tgt_rgb=torch.as_tensor(tgt, device="cuda")))
     o = oracle.backward(m, [cam], tgt_rgb=tgt, w_rgb=1.0)
-    assert_grads_close(res["bucket"], o, GRAD_KEYS)
+    assert_grads_close(res["bucket"], o, GRAD_KEYS, label="569-deep lists, bucket backward")
     assert rel_err(res["bucket"]["pose"], o["pose"]) <= GRAD_TOL
     for k in GRAD_KEYS + ("pose", "loss"):
         assert rel_err(res["bucket"][k], res["pixel"][k]) <= 2e-4, k
