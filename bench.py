@@ -378,7 +378,81 @@ def run_mapping_iteration(args, rast, gm, cams, w, tgt_rgb, tgt_depth):
             "ms_per_iteration": round(ms, 4), "mpix_per_s": round(V * H * W / (ms / 1e3) / 1e6, 1)}
 
 
-def run_bucket_backward(args, rast0, gm, cams, tgt_rgb, tgt_depth, w, k_eval):
+# Algorithmic lane operations per (pixel, list position) evaluation of the
+# blend kernels, as the method computes it (one per scalar operation, an FMA
+# counts one; per-column terms shared by a thread's pixels amortised), for a
+# blended evaluation and one skipped below alpha_min; then the same in FP32
+# FLOP with an FMA counted twice.
+#   forward, skipped: power 3 (dy, two FMA) + column terms 1 + alpha_min test 1 = 5
+#   forward, blended: + ex2 1, clamp 1, 1 - alpha 1, T (1 - alpha) 1, stop test 1,
+#                     w = alpha T 1, colour and depth 4, last index 1 = 16
+#   backward, skipped: 5 (as forward)
+#   backward, blended: + ex2 1, clamp 1, 1 - alpha 1, T recovery (reciprocal, product) 2,
+#                      w 1, adjoint dot (gC.c + gD d + gO) 4, minus behind-sum 1, dL/dalpha 1,
+#                      behind-sum update 1, dL/dc and dL/dd sums 4, dL/dpower 1, moment sums 3,
+#                      per-thread moment finish 1.5 (12 per 8 pixels) = 28.5
+BLEND_OPS = {  # kernel: (blended ops, skipped ops, blended FLOP, skipped FLOP)
+    "render_fwd": (16.0, 5.0, 23.0, 8.0),
+    "render_bwd": (28.5, 5.0, 45.0, 8.0),
+}
+
+
+def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip, sh_degree=None):
+    """Algorithmic (bytes, lane operations) per launch of every kernel of the
+    mapping step, from the step's work counters.  Bytes: what the method must
+    move to or from HBM at least once; operations: the arithmetic the method
+    performs (see BLEND_OPS for the blend kernels).
+      project:  44 B parameters per Gaussian + SH per visible entry + 100 B
+                written per visible entry (48 record, 48 cleared adjoint,
+                4 list) + 8 B tile box per (view, Gaussian); ~300 ops per
+                visible entry (rotation, covariance, Jacobian, conic, SH 3,
+                box), 40 per (view, Gaussian) for the near/screen test
+      scatter_rows: 12 B per visible entry read, 8 B per row item written
+      rows_count: per row item 8 B item + 32 B record read, 4 B span
+                written; 16 chords x 14 ops
+      rows_emit: per row item 8 + 4 + 16 B read, 8 B key per pair written;
+                4 ops per pair + 10 per row item
+      sort_*:   8 B key read + 4 B index written per pair; 2 radix passes
+                x 8 ops per key
+      render_fwd: 52 B (record + index) per processed pair, 28 B per pixel
+                written (RGB, depth, opacity, T_final, n_contrib)
+      render_bwd: 44 B per pixel read (RGB, target RGB, depth, opacity,
+                T_final, n_contrib, target depth), 52 B per processed pair,
+                48 B of 2D adjoints added per processed pair
+      preprocess_bwd: per listed Gaussian parameters + SH read and their
+                gradients read and written ((44 + SH) x 3); per visible
+                entry 96 B (record, adjoint); ~300 ops per visible entry
+      count_depth: 4 B per pixel."""
+    deg = WORKLOAD["sh_degree"] if sh_degree is None else sh_degree
+    b_sh = 4 * 3 * (deg + 1) ** 2
+    px = views * hw
+    sort = (n_pairs * 12.0, n_pairs * 16.0)
+    return {
+        "project": (44.0 * n + b_sh * n_vis + 100.0 * n_vis + 8.0 * views * n, 300.0 * n_vis + 40.0 * views * n),
+        "scatter_rows": (12.0 * n_vis + 8.0 * n_rows, 4.0 * n_rows),
+        "rows_count": (44.0 * n_rows, 16 * 14.0 * n_rows),
+        "rows_emit": (28.0 * n_rows + 8.0 * n_pairs, 4.0 * n_pairs + 10.0 * n_rows),
+        "sort_small": sort,
+        "render_fwd": (52.0 * p_proc + 28.0 * px,
+                       k_blend * BLEND_OPS["render_fwd"][0] + k_skip * BLEND_OPS["render_fwd"][1]),
+        "count_depth": (4.0 * px, 2.0 * px),
+        "render_bwd": (44.0 * px + 100.0 * p_proc,
+                       k_blend * BLEND_OPS["render_bwd"][0] + k_skip * BLEND_OPS["render_bwd"][1]),
+        "preprocess_bwd": ((44.0 + b_sh) * 3 * n_listed + 96.0 * n_vis, 300.0 * n_vis),
+    }
+
+
+def tile_max_prefix(n_contrib) -> int:
+    """Pairs the blend kernels process: per 16x16 tile the longest
+    contributor prefix of its pixels, summed over tiles and views."""
+    import torch.nn.functional as F
+    V, H, W = n_contrib.shape
+    x = n_contrib.float().view(V, 1, H, W)  # counts far below 2^24: exact in FP32
+    x = F.pad(x, (0, (-W) % 16, 0, (-H) % 16))
+    return int(F.max_pool2d(x, 16).sum().item())
+
+
+def run_bucket_backward(args, rast0, gm, cams, tgt_rgb, tgt_depth, w, k_blend, k_skip, issue):
     """The headline step with the per-Gaussian (bucket) blend backward of
     Sec. "Per-Gaussian Backpropagation" in place of the pixel-parallel one
     (the forward then writes its bucket checkpoints): throughput and
@@ -432,7 +506,9 @@ def run_bucket_backward(args, rast0, gm, cams, tgt_rgb, tgt_depth, w, k_eval):
     kern = {k: round(v[1] / v[0], 4) for k, v in sorted(per.items(), key=lambda x: -x[1][1])}
     bwd_ms = kern.get("render_bwd_bucket", 0.0)
     res = {"ms_per_step": round(ms, 4), "mpix_per_s": round(V * H * W / (ms / 1e3) / 1e6, 1), "kernels_ms": kern,
-           "blend_bwd_tflops": round(k_eval * 43.0 / (bwd_ms / 1e3) / 1e12, 2) if bwd_ms else None,
+           # the same algorithmic instruction count as the pixel-parallel backward, against instruction issue
+           "blend_bwd_issue_frac": round((k_blend * BLEND_OPS["render_bwd"][0] + k_skip * BLEND_OPS["render_bwd"][1])
+                                         / 32.0 / (bwd_ms / 1e3) / issue, 4) if bwd_ms else None,
            "bucket_workspace_bytes": int(rast._bucket_buf.numel())}
     del rast, out, grads
     torch.cuda.empty_cache()
@@ -707,53 +783,66 @@ def run_ours(args):
 
     # work counters of one step (for the algorithmic roofline)
     counters = rast._view(rast.layout.counters, 8, torch.int32).cpu().numpy()
-    n_visible, n_pairs, n_rows = int(counters[2]), int(counters[1]), int(counters[4])
+    n_visible, n_pairs, n_rows, n_listed = int(counters[2]), int(counters[1]), int(counters[4]), int(counters[5])
     k_eval = float(out.n_contrib.to(torch.float64).sum().item())
+    bc = torch.zeros(args.views, 2, dtype=torch.int64, device=d.dev)
+    N.gs_blend_counts(rast.cfg, rast.ws, bc, torch.cuda.current_stream(d.dev).cuda_stream)
+    bc = bc.cpu().numpy().sum(0)
+    k_blend = float(bc[1])
+    k_skip = float(bc[0]) - k_blend
+    p_proc = float(tile_max_prefix(out.n_contrib))
     px_step = V * H * W
     peaks = measured_peaks()
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     n_sm = torch.cuda.get_device_properties(d.dev).multi_processor_count
+    issue = n_sm * 4 * sm_mhz * 1e6  # warp instructions per second (4 schedulers per SM)
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOP
-    # algorithmic bytes (HBM-bound kernels) or FP32 FLOP (blend kernels) per launch, from the work counters
-    sh_bytes = 4 * 3 * (WORKLOAD["sh_degree"] + 1) ** 2
-    V = args.views
-    alg = {
-        "project": ("hbm", V * args.n * 12 + n_visible * (12 + 16 + 4 + sh_bytes + 48 + 48) + V * args.n * 8),
-        "rows_emit": ("hbm", n_pairs * 8 + n_rows * (8 + 4 + 16)),
-        "rows_count": ("hbm", n_rows * (8 + 32 + 4)),
-        "sort_small": ("hbm", n_pairs * (8 + 4)),
-        # FP32 FLOP per (pixel, list position up to its last contributor), FMA = 2:
-        # forward: weight 6, exp2 1, clamp 1, transmittance 2, w 1, colour+depth 8  -> 19
-        # backward: weight 6, exp2 1, clamp 1, 1-alpha 1, T recovery 1, w 1, adjoint dot 8,
-        #           dL/dalpha 2, behind-sum 2, colour+depth sums 8, dL/dpower 1, moments 11 -> 43
-        "render_fwd": ("alu", k_eval * 19.0),
-        "render_bwd": ("alu", k_eval * 43.0),
-        "preprocess_bwd": ("hbm", n_visible * (48 + 48) + args.n * V * 8 + n_visible * (236 + 2 * 236) / V),
-    }
-    bound, amount = alg.get(dominant, ("hbm", 0))
-    kavg_s = kernels[dominant]["ms_avg"] / 1e3
-    if bound == "hbm":
-        achieved, peak, unit = amount / kavg_s / 1e9, peaks["hbm_gbs"], "GB/s"
-    else:
-        achieved, peak, unit = amount / kavg_s / 1e12, fp32_peak, "TFLOP/s"
-    traffic = traffic_for(dominant)
-    roofline = {"kernel": dominant, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": ("FP32 FMA issue: %d SMs x 128 lanes x 2 FLOP x %.0f MHz median SM clock" %
-                                (n_sm, sm_mhz)) if bound == "alu" else f"{peaks['source']} HBM copy bandwidth"}
+    model = step_model(args.n, args.views, H * W, n_visible, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip)
+    bw = peaks["hbm_gbs"] * 1e9
 
-    # every kernel with an algorithmic count against its own roof
-    per_kernel_roof = {}
-    for k, (bd, amt) in alg.items():
-        if k not in kernels or not amt:
-            continue
+    def roof(k):
+        bytes_, ops = model[k]
         t_s = kernels[k]["ms_avg"] / 1e3
-        if bd == "hbm":
-            a_, p_, u_ = amt / t_s / 1e9, peaks["hbm_gbs"], "GB/s"
+        t_mem, t_ins = bytes_ / bw, ops / 32.0 / issue
+        if t_ins > t_mem:
+            ach, pk, unit, bd = ops / 32.0 / t_s / 1e9, issue / 1e9, "Gwarp-instr/s", "alu"
         else:
-            a_, p_, u_ = amt / t_s / 1e12, fp32_peak, "TFLOP/s"
-        per_kernel_roof[k] = {"bound": bd, "achieved": round(a_, 3), "peak": round(p_, 2), "unit": u_,
-                              "frac": round(a_ / p_, 4), "traffic": traffic_for(k)}
+            ach, pk, unit, bd = bytes_ / t_s / 1e9, peaks["hbm_gbs"], "GB/s", "hbm"
+        return {"bound": bd, "achieved": round(ach, 3), "peak": round(pk, 2), "unit": unit,
+                "frac": round(ach / pk, 4), "floor_ms": round(max(t_mem, t_ins) * 1e3, 4),
+                "alg_bytes": int(bytes_), "alg_warp_instr": int(ops / 32.0), "traffic": traffic_for(k)}
+
+    per_kernel_roof = {k: roof(k) for k in model if k in kernels}
+    rf = per_kernel_roof.get(dominant)
+    roofline = {"kernel": dominant, "bound": rf["bound"], "achieved": rf["achieved"], "peak": rf["peak"],
+                "unit": rf["unit"], "frac": rf["frac"], "traffic": rf["traffic"],
+                "peak_source": (f"instruction issue: {n_sm} SMs x 4 schedulers x {sm_mhz:.0f} MHz median SM clock "
+                                "in the timed region (1 warp instruction per scheduler per clock)"
+                                if rf["bound"] == "alu" else f"{peaks['source']} HBM copy bandwidth"),
+                "numerator": ("algorithmic lane operations per evaluation (blended / skipped below alpha_min) "
+                              "x the step's evaluations, / 32 per warp instruction"
+                              if rf["bound"] == "alu" else "algorithmic bytes per launch")}
+    if dominant in ("render_bwd", "render_fwd"):
+        per_eval = BLEND_OPS[dominant]
+        roofline["per_evaluation_ops"] = {"blended": per_eval[0], "skipped": per_eval[1]}
+        # the FP32 view of the same kernel: operations x 2 for an FMA, against the FMA pipe
+        fl = (k_blend * per_eval[2] + k_skip * per_eval[3]) / (kernels[dominant]["ms_avg"] / 1e3) / 1e12
+        roofline["fp32_view"] = {"achieved_tflops": round(fl, 3), "peak_tflops": round(fp32_peak, 2),
+                                 "frac": round(fl / fp32_peak, 4),
+                                 "convention": "FLOP with FMA = 2 (blended / skipped per evaluation: "
+                                               f"{per_eval[2]} / {per_eval[3]}) against 128 FP32 lanes per SM"}
+    floors = sum(v["floor_ms"] for v in per_kernel_roof.values())
+    step_bytes = sum(v["alg_bytes"] for v in per_kernel_roof.values())
+    ms_step_local = ms_local / args.steps
+    roofline_step = {
+        "frac": round(floors / ms_step_local, 4),
+        "floor_ms": round(floors, 4), "ms_per_step": round(ms_step_local, 4),
+        "definition": "sum over the step's kernels of max(algorithmic bytes / HBM bandwidth, algorithmic "
+                      "instructions / issue rate), over the measured time per step",
+        "hbm_frac": round(step_bytes / (ms_step_local / 1e3) / bw, 4),
+        "hbm_bytes_per_step": int(step_bytes),
+        "hbm_definition": "the step's algorithmic bytes / time per step / measured HBM copy bandwidth",
+    }
 
     # end to end: host keyframes -> device, fwd+bwd, loss back to host
     e2e = None if args.no_e2e else run_e2e(args, d, rast, gm, w, px_step)
@@ -762,7 +851,7 @@ def run_ours(args):
 
     bucket = None
     if d.rank == 0 and not args.no_bucket:
-        bucket = run_bucket_backward(args, rast, gm, cams, tgt_rgb, tgt_depth, w, k_eval)
+        bucket = run_bucket_backward(args, rast, gm, cams, tgt_rgb, tgt_depth, w, k_blend, k_skip, issue)
 
     mapping_iter = None
     if d.rank == 0 and not args.no_e2e:
@@ -807,6 +896,7 @@ def run_ours(args):
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": roofline,
+                "roofline_step": roofline_step,
                 "roofline_per_kernel": per_kernel_roof,
                 "cpu_baseline": cpu,
                 "mapping_iteration": mapping_iter,
@@ -815,7 +905,9 @@ def run_ours(args):
                 "serving": serving,
                 "kernels": kernels,
                 "work": {"visible_entries": n_visible, "pairs": n_pairs, "row_items": n_rows,
-                         "blend_evaluations": k_eval,
+                         "gaussians_listed": n_listed, "pairs_processed": p_proc,
+                         "blend_evaluations": k_eval, "blend_evaluations_blended": k_blend,
+                         "blend_evaluations_skipped": k_skip,
                          "lidar_valid_frac": [round(x, 4) for x in w.meta["depth_frac"]]}}
         print(json.dumps(line), flush=True)
     d.close()

@@ -169,6 +169,16 @@ gs_status gs_bin_sort(const gs_workspace* ws, gs_stream_t stream);
 gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb, float* depth, float* opac,
                         float* t_final, uint32_t* n_contrib, gs_stream_t stream);
 
+/* Work counters of the compositing (measurement support; no counterpart in
+ * the paper): runs the front-to-back compositing of gs_render_fwd over the
+ * workspace's tile lists without writing an image and sets, per view,
+ * counts_dev[2v] = number of (pixel, tile-list position) evaluations up to
+ * each pixel's last blended Gaussian (the sum of gs_render_fwd's n_contrib)
+ * and counts_dev[2v + 1] = how many of them were blended (the others were
+ * skipped below alpha_min).  counts_dev: device uint64 [V][2], 8-byte
+ * aligned, overwritten. */
+gs_status gs_blend_counts(const gs_config* cfg, const gs_workspace* ws, uint64_t* counts_dev, gs_stream_t stream);
+
 /* Backward pass (Eq. depth_loss back through Eq. rendered_* and the
  * projection).  Pixel adjoints are the fused loss (tgt_rgb != NULL):
  *   L_v = w_rgb mean_{3HW} |C^ - C| + w_depth / |M_d| sum_{D_s>0, O^>0} |D^/O^ - D_s|,

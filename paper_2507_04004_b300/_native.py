@@ -15,7 +15,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_
 GS_NOALLOC_SCRATCH_BYTES = 64 << 20  # size of gs_render_fwd_noalloc's device array
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
+            "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
             "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
             "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_trace_start",
@@ -92,6 +92,7 @@ def lib():
         L.gs_project.argtypes = [C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace), P]
         L.gs_bin_sort.argtypes = [C.POINTER(gs_workspace), P]
         L.gs_render_fwd.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace), P, P, P, P, P, P]
+        L.gs_blend_counts.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace), P, P]
         L.gs_render_bwd.argtypes = ([C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace)]
                                     + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P])
         L.gs_bucket_workspace_size.argtypes = [C.POINTER(gs_workspace)]
@@ -126,7 +127,7 @@ def lib():
         L.gs_status_str.argtypes = [I32]
         L.gs_status_str.restype = C.c_char_p
         L.gs_version.restype = C.c_char_p
-        for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd",
+        for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_blend_counts", "gs_render_bwd",
                      "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose",
                      "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes"):
@@ -175,6 +176,10 @@ def gs_bin_sort(ws: gs_workspace, stream: int) -> None:
 def gs_render_fwd(cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib, stream: int) -> None:
     check("gs_render_fwd", lib().gs_render_fwd(C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac),
                                                _ptr(t_final), _ptr(n_contrib), C.c_void_p(stream)))
+
+
+def gs_blend_counts(cfg: gs_config, ws: gs_workspace, counts, stream: int) -> None:
+    check("gs_blend_counts", lib().gs_blend_counts(C.byref(cfg), C.byref(ws), _ptr(counts), C.c_void_p(stream)))
 
 
 def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib,

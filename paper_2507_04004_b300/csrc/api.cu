@@ -197,6 +197,16 @@ gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb
                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 
+gs_status gs_blend_counts(const gs_config* cfg, const gs_workspace* ws, uint64_t* counts_dev, gs_stream_t stream) {
+  gs_layout L;
+  gs_status s = check_ws(ws, &L);
+  if (s != GS_OK) return s;
+  if ((s = check_cfg(cfg)) != GS_OK) return s;
+  if (!counts_dev || (reinterpret_cast<uintptr_t>(counts_dev) & 7u) != 0) return GS_ERR_ARG;
+  return cuda_status(launch_blend_counts(*cfg, resolve_ws(ws, L), reinterpret_cast<unsigned long long*>(counts_dev),
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // Argument checks and marshalling shared by both blend backwards.
 static gs_status bwd_args(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
                           const float* rgb, const float* depth, const float* opac, const float* t_final,

@@ -47,6 +47,7 @@ cudaError_t launch_dssim(const float* img, const float* tgt, int V, int H, int W
                          float* dl_dimg, void* scratch, cudaStream_t st);
 cudaError_t launch_render_fwd(const gs_config& cfg, const Ws& ws, float* rgb, float* depth, float* opac,
                               float* t_final, uint32_t* n_contrib, cudaStream_t st);
+cudaError_t launch_blend_counts(const gs_config& cfg, const Ws& ws, unsigned long long* counts, cudaStream_t st);
 
 struct BwdArgs {
   const float *rgb, *depth, *opac, *t_final;

@@ -12,11 +12,16 @@
 // Sec. "Per-Gaussian Backpropagation" (bucket b of tile t is record
 // (tile_start[t] >> 5) + t + b of the checkpoint array, planes T, C_r, C_g,
 // C_b, D of 256 pixels each, pixel index y * 16 + x within the tile).
+//
+// The counting variant (STATS) composites the same way but writes no image:
+// it adds, per view, the number of (pixel, list position) evaluations up to
+// each pixel's last contributor and how many of them were blended (the rest
+// were skipped below alpha_min) into ckpt reinterpreted as uint64 [V][2].
 #include "gs_internal.h"
 
 namespace gsb {
 
-template <int PPT, bool CKPT>
+template <int PPT, bool CKPT, bool STATS = false>
 __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, float* __restrict__ rgb,
                                                           float* __restrict__ depth, float* __restrict__ opac,
                                                           float* __restrict__ t_final,
@@ -47,6 +52,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   // comparison decides whether a Gaussian takes part at the pixel
   float thr[PPT];
   uint32_t last[PPT];
+  uint32_t n_blend = 0;  // STATS only
   bool all_done = true;
   const float inf = __int_as_float(0x7f800000);
 #pragma unroll
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
         T[h] = mul2(T[h], fma2(ak, f2(-1.f), f2(1.f)));
         last[2 * h] = k0 ? nxt : last[2 * h];
         last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
+        if (STATS) n_blend += (uint32_t)k0 + (uint32_t)k1;
       }
       // the thread leaves once all its pixels are done, checked every 8
       // Gaussians (a done pixel takes no part in the ones in between)
@@ -128,6 +135,22 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     // pixels whose list ended are done only when the whole list is walked
   }
   const int64_t HW = (int64_t)ws.width * ws.height;
+  if (STATS) {
+    unsigned long long ev = 0, bl = n_blend;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) ev += last[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ev += __shfl_xor_sync(kFull, ev, o);
+      bl += __shfl_xor_sync(kFull, bl, o);
+    }
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ckpt) + 2 * v;
+    if ((threadIdx.x & 31) == 0 && ev) {
+      atomicAdd(counts, ev);
+      atomicAdd(counts + 1, bl);
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const int y = yb + k;
@@ -164,6 +187,19 @@ cudaError_t launch_render_fwd_ckpt(const gs_config& cfg, const Ws& ws, float* rg
   trace_begin(kKRenderFwdCkpt, st);
   k_render_fwd<kFwdPPT, true><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, rgb, depth, opac, t_final, n_contrib, ckpt);
   trace_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace gsb
+
+namespace gsb {
+
+cudaError_t launch_blend_counts(const gs_config& cfg, const Ws& ws, unsigned long long* counts, cudaStream_t st) {
+  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)ws.views * 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_render_fwd<kFwdPPT, false, true><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr, reinterpret_cast<float*>(counts));
   return cudaGetLastError();
 }
 

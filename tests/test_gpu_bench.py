@@ -30,6 +30,12 @@ def test_bench_prints_the_contract_line():
     roof = line["roofline"]
     assert roof["bound"] in ("hbm", "alu", "tensor") and roof["achieved"] > 0 and roof["peak"] > 0
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-3
+    step = line["roofline_step"]
+    assert 0 < step["frac"] <= 1.5 and 0 < step["hbm_frac"] <= 1.5
+    assert abs(step["floor_ms"] - sum(v["floor_ms"] for v in line["roofline_per_kernel"].values())) < 1e-3
+    work = line["work"]
+    assert 0 < work["blend_evaluations_blended"] <= work["blend_evaluations"]
+    assert work["blend_evaluations_blended"] + work["blend_evaluations_skipped"] == work["blend_evaluations"]
     e2e = line["e2e"]
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     cb = line["cpu_baseline"]
