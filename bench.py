@@ -173,10 +173,11 @@ def source_hash(*names) -> str:
 
 
 # Which source file holds each kernel (for matching ncu traffic to source).
-KERNEL_SRC = {"project": "project.cu", "scatter_rows": "project.cu", "rows_count": "project.cu",
-              "rows_emit": "project.cu", "scan_buckets": "sort.cu", "scan": "sort.cu", "sort_small": "sort.cu",
-              "sort_medium": "sort.cu",
-              "sort_long": "sort.cu", "render_fwd": "render_fwd.cu", "count_depth": "render_bwd.cu",
+KERNEL_SRC = {"project": "project.cu", "scan_buckets": "binning.cu", "depth_hist": "binning.cu",
+              "depth_scan": "binning.cu", "depth_scatter": "binning.cu", "entry_order": "binning.cu",
+              "entry_units": "binning.cu", "entry_rows": "binning.cu", "unit_scan": "binning.cu",
+              "scatter_rows": "binning.cu", "rows_count": "binning.cu", "scan": "binning.cu",
+              "rows_emit": "binning.cu", "render_fwd": "render_fwd.cu", "count_depth": "render_bwd.cu",
               "render_bwd": "render_bwd.cu", "preprocess_bwd": "render_bwd.cu", "pose_jacobian": "jacobian.cu"}
 
 
@@ -407,13 +408,17 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
                 4 list) + 8 B tile box per (view, Gaussian); ~300 ops per
                 visible entry (rotation, covariance, Jacobian, conic, SH 3,
                 box), 40 per (view, Gaussian) for the near/screen test
-      scatter_rows: 12 B per visible entry read, 8 B per row item written
-      rows_count: per row item 8 B item + 32 B record read, 4 B span
+      depth sort: depth_hist reads 8 B per visible entry once (digit counts
+                of all passes); depth_scatter (5 passes at 2..256 views)
+                reads 8 B and writes 8 B per entry per pass; ~12 ops per
+                entry per pass
+      entry_order: 8 B read, 4 B written per visible entry
+      entry_rows / scatter_rows: per visible entry 4 B list + 8 B box
+                read (twice), 4 B row item written per row item
+      rows_count: per row item 4 B item + 32 B record read, 4 B span
                 written; 16 chords x 14 ops
-      rows_emit: per row item 8 + 4 + 16 B read, 8 B key per pair written;
-                4 ops per pair + 10 per row item
-      sort_*:   8 B key read + 4 B index written per pair; 2 radix passes
-                x 8 ops per key
+      rows_emit: per row item 4 + 4 B read, 4 B Gaussian index written per
+                pair; ~10 ops per pair
       render_fwd: 52 B (record + index) per processed pair, 28 B per pixel
                 written (RGB, depth, opacity, T_final, n_contrib)
       render_bwd: 44 B per pixel read (RGB, target RGB, depth, opacity,
@@ -426,13 +431,17 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
     deg = WORKLOAD["sh_degree"] if sh_degree is None else sh_degree
     b_sh = 4 * 3 * (deg + 1) ** 2
     px = views * hw
-    sort = (n_pairs * 12.0, n_pairs * 16.0)
+    passes = 4 + (1 if views > 1 else 0)
     return {
-        "project": (44.0 * n + b_sh * n_vis + 100.0 * n_vis + 8.0 * views * n, 300.0 * n_vis + 40.0 * views * n),
-        "scatter_rows": (12.0 * n_vis + 8.0 * n_rows, 4.0 * n_rows),
-        "rows_count": (44.0 * n_rows, 16 * 14.0 * n_rows),
-        "rows_emit": (28.0 * n_rows + 8.0 * n_pairs, 4.0 * n_pairs + 10.0 * n_rows),
-        "sort_small": sort,
+        "project": (44.0 * n + b_sh * n_vis + 100.0 * n_vis + 8.0 * views * n + 8.0 * n_vis,
+                    300.0 * n_vis + 40.0 * views * n),
+        "depth_hist": (8.0 * n_vis, 4.0 * n_vis * passes),
+        "depth_scatter": (16.0 * n_vis * passes, 12.0 * n_vis * passes),
+        "entry_order": (12.0 * n_vis, 8.0 * n_vis),
+        "entry_rows": (12.0 * n_vis, 6.0 * n_vis),
+        "scatter_rows": (12.0 * n_vis + 4.0 * n_rows, 10.0 * n_rows),
+        "rows_count": (40.0 * n_rows, 16 * 14.0 * n_rows),
+        "rows_emit": (8.0 * n_rows + 4.0 * n_pairs, 10.0 * n_pairs),
         "render_fwd": (52.0 * p_proc + 28.0 * px,
                        k_blend * BLEND_OPS["render_fwd"][0] + k_skip * BLEND_OPS["render_fwd"][1]),
         "count_depth": (4.0 * px, 2.0 * px),
@@ -729,7 +738,7 @@ def run_ours(args):
         raise SystemExit(f"workspace status {code} after warm-up (pairs needed {needed})")
 
     # per-kernel trace events for the timed region
-    per_step = 16
+    per_step = 48
     cap = per_step * args.steps + 16
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * cap)]
     for e in evs:
@@ -802,7 +811,7 @@ def run_ours(args):
 
     def roof(k):
         bytes_, ops = model[k]
-        t_s = kernels[k]["ms_avg"] / 1e3
+        t_s = kernels[k]["ms_total"] / args.steps / 1e3  # all of the kernel's launches in one step
         t_mem, t_ins = bytes_ / bw, ops / 32.0 / issue
         if t_ins > t_mem:
             ach, pk, unit, bd = ops / 32.0 / t_s / 1e9, issue / 1e9, "Gwarp-instr/s", "alu"

@@ -103,28 +103,38 @@ typedef struct {
   gs_frame frame;
 } gs_workspace;
 
-/* Byte offsets of the workspace's parts (for inspection and tests). */
+/* Byte offsets of the workspace's parts (for inspection and tests).  E = V*N
+ * (view, Gaussian) entries, T tiles per view, B = V*ceil(H/16) (view, tile
+ * row) buckets, cap the pair capacity; an entry unit is up to 256 sorted
+ * visible entries of one view, a row unit up to 128 row items of one bucket. */
 typedef struct {
   size_t counters;    /* uint32[16]: [0] status, [1] pairs (or row items) needed, [2] visible entries,
-                         [3] long tiles, [4] row items, [5] Gaussians in gauss_list, [6] medium tiles */
-  size_t records;     /* float4[V*N][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
-  size_t rects;       /* uint32[V*N][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
-  size_t adjoints;    /* float4[V*N][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */
-  size_t visible;     /* uint32[V*N]: indices v*N + g of projected Gaussians with a non-empty box */
+                         [3] entry units, [4] row items, [5] Gaussians in gauss_list, [6] row units,
+                         [8..13] tile tickets of the sort's passes */
+  size_t records;     /* float4[E][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
+  size_t rects;       /* uint32[E][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
+  size_t adjoints;    /* float4[E][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */
+  size_t visible;     /* uint32[E]: entries v*N + g with a non-empty box, after binning in
+                         (view, depth key, Gaussian index) order */
+  size_t vis_key;     /* uint32[E]: depth key bits of the visible entries (projection order) */
+  size_t sort_key;    /* uint32[2][E]: radix-sort buffers (keys) */
+  size_t sort_val;    /* uint32[2][E]: radix-sort buffers (entries) */
+  size_t radix_status; /* uint32[6][256] digit counts of the sort's passes, then
+                          uint32[6][ceil(E/2048)][256] per-tile status words */
+  size_t view_start;  /* uint32[V+1]: first sorted visible entry of each view */
   size_t gauss_list;  /* uint32[N]: Gaussians g with a non-empty box in at least one view */
   size_t tile_count;  /* uint32[V*T]: pairs per tile, T = ceil(W/16) * ceil(H/16) */
   size_t tile_start;  /* uint32[V*T]: first pair of each tile in the sorted order */
-  size_t tile_cursor; /* uint32[V*T]: fill cursor used while binning */
-  size_t long_tiles;  /* uint32[V*T]: tiles for the long-bin sort (from the front) and for the
-                         medium-bin sort (from the back) */
-  size_t bucket_count;  /* uint32[V*ceil(H/16)]: row items per (view, tile row) */
-  size_t bucket_start;  /* uint32[V*ceil(H/16)] */
-  size_t bucket_cursor; /* uint32[V*ceil(H/16)] */
-  size_t row_items;   /* uint32[cap][2]: (entry v*N + g, bucket), one per (Gaussian, tile row of its box) */
+  size_t bucket_count;  /* uint32[B]: row items (Gaussian, tile row of its box) per bucket */
+  size_t bucket_start;  /* uint32[B] */
+  size_t unit_first_e;  /* uint32[V+1]: first entry unit of each view */
+  size_t unit_seg_e;    /* uint32[E/256 + V]: view of each entry unit */
+  size_t unit_cnt_e;    /* uint32[ceil(H/16)][E/256 + V]: row items per tile row of each entry unit */
+  size_t unit_first_r;  /* uint32[B+1]: first row unit of each bucket */
+  size_t unit_seg_r;    /* uint32[cap/128 + B]: bucket of each row unit */
+  size_t unit_cnt_r;    /* uint32[ceil(W/16)][cap/128 + B]: pairs per tile of each row unit */
+  size_t row_items;   /* uint32[cap]: entry of each row item, grouped by bucket, in (depth key, index) order */
   size_t row_span;    /* uint32[cap]: kept tile columns of each row item */
-  size_t cta_counts;  /* uint32[2048][2 ceil(W/16)]: pairs per tile in each binning CTA's tile-row window */
-  size_t keys;        /* uint64[cap]: (depth key bits << 32 | Gaussian index), binned by tile */
-  size_t keys_alt;    /* uint64[cap]: merge buffer for very long tiles */
   size_t sorted_ids;  /* uint32[cap]: Gaussian index of each pair, sorted by (tile, depth key, index) */
   size_t view_stats;  /* float[V][4]: per-view loss accumulators and valid-depth counts */
   size_t total;       /* bytes */
@@ -133,7 +143,8 @@ typedef struct {
 /* Workspace bytes and layout for n Gaussians, a batch geometry and a pair
  * capacity.  Valid sizes: 1 <= n < 2^31, 1 <= pair_capacity < 2^31 (an empty
  * map has nothing to project: its image is the background, which the caller
- * fills without the library).  Return 0 / GS_ERR_ARG on invalid sizes. */
+ * fills without the library).  Return 0 / GS_ERR_ARG on invalid sizes, 0 /
+ * GS_ERR_UNSUPPORTED when n_views * n >= 2^30 or n_views * T >= 2^31. */
 size_t gs_workspace_size(int64_t n, const gs_frame* frame, int64_t pair_capacity);
 gs_status gs_workspace_layout(int64_t n, const gs_frame* frame, int64_t pair_capacity, gs_layout* out);
 

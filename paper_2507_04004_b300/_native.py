@@ -48,11 +48,11 @@ class gs_workspace(C.Structure):
 
 
 class gs_layout(C.Structure):
-    _fields_ = [(k, C.c_size_t) for k in ("counters", "records", "rects", "adjoints", "visible", "gauss_list",
-                                          "tile_count",
-                                          "tile_start", "tile_cursor", "long_tiles", "bucket_count",
-                                          "bucket_start", "bucket_cursor", "row_items", "row_span", "cta_counts", "keys",
-                                          "keys_alt", "sorted_ids", "view_stats", "total")]
+    _fields_ = [(k, C.c_size_t) for k in ("counters", "records", "rects", "adjoints", "visible", "vis_key", "sort_key",
+                                          "sort_val", "radix_status", "view_start", "gauss_list", "tile_count",
+                                          "tile_start", "bucket_count", "bucket_start", "unit_first_e", "unit_seg_e",
+                                          "unit_cnt_e", "unit_first_r", "unit_seg_r", "unit_cnt_r", "row_items",
+                                          "row_span", "sorted_ids", "view_stats", "total")]
 
 
 class gs_adam_config(C.Structure):

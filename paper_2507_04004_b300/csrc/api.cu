@@ -20,30 +20,38 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
     return GS_ERR_ARG;
   const int64_t V = f->n_views;
   const int64_t E = V * n;
-  if (E >= (int64_t(1) << 32)) return GS_ERR_UNSUPPORTED;
+  if (E >= (int64_t(1) << 30)) return GS_ERR_UNSUPPORTED;  // the sort's status words hold 30-bit counts
   const int64_t T = (int64_t)((f->width + 15) / 16) * ((f->height + 15) / 16);
   if (V * T >= (int64_t(1) << 31)) return GS_ERR_UNSUPPORTED;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  const int64_t tx = (f->width + 15) / 16, ty = (f->height + 15) / 16;
+  const int64_t B = V * ty;
+  const int64_t units_e = (E + kEntryUnit - 1) / kEntryUnit + V;
+  const int64_t units_r = (cap + kRowUnit - 1) / kRowUnit + B;
   L->counters = take(16 * sizeof(uint32_t));
   L->records = take((size_t)E * 3 * sizeof(float4));
   L->rects = take((size_t)E * sizeof(uint2));
   L->adjoints = take((size_t)E * 3 * sizeof(float4));
   L->visible = take((size_t)E * sizeof(uint32_t));
+  L->vis_key = take((size_t)E * sizeof(uint32_t));
+  L->sort_key = take((size_t)2 * E * sizeof(uint32_t));
+  L->sort_val = take((size_t)2 * E * sizeof(uint32_t));
+  L->radix_status = take((size_t)6 * 256 * (1 + (E + kRadixTileEntries - 1) / kRadixTileEntries) * sizeof(uint32_t));
+  L->view_start = take((size_t)(V + 1) * sizeof(uint32_t));
   L->gauss_list = take((size_t)n * sizeof(uint32_t));
   L->tile_count = take((size_t)(V * T) * sizeof(uint32_t));
   L->tile_start = take((size_t)(V * T) * sizeof(uint32_t));
-  L->tile_cursor = take((size_t)(V * T) * sizeof(uint32_t));
-  L->long_tiles = take((size_t)(V * T) * sizeof(uint32_t));
-  const int64_t B = V * ((f->height + 15) / 16);
   L->bucket_count = take((size_t)B * sizeof(uint32_t));
   L->bucket_start = take((size_t)B * sizeof(uint32_t));
-  L->bucket_cursor = take((size_t)B * sizeof(uint32_t));
-  L->row_items = take((size_t)cap * sizeof(uint2));
+  L->unit_first_e = take((size_t)(V + 1) * sizeof(uint32_t));
+  L->unit_seg_e = take((size_t)units_e * sizeof(uint32_t));
+  L->unit_cnt_e = take((size_t)units_e * ty * sizeof(uint32_t));
+  L->unit_first_r = take((size_t)(B + 1) * sizeof(uint32_t));
+  L->unit_seg_r = take((size_t)units_r * sizeof(uint32_t));
+  L->unit_cnt_r = take((size_t)units_r * tx * sizeof(uint32_t));
+  L->row_items = take((size_t)cap * sizeof(uint32_t));
   L->row_span = take((size_t)cap * sizeof(uint32_t));
-  L->cta_counts = take((size_t)kRowsGridMax * 2 * ((f->width + 15) / 16) * sizeof(uint32_t));
-  L->keys = take((size_t)cap * sizeof(unsigned long long));
-  L->keys_alt = take((size_t)cap * sizeof(unsigned long long));
   L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
   L->view_stats = take((size_t)V * 4 * sizeof(float));
   L->total = off;
@@ -52,26 +60,32 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
 
 Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   char* b = static_cast<char*>(w->ptr);
+  auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t*>(b + off); };
   Ws ws;
-  ws.counters = reinterpret_cast<uint32_t*>(b + L.counters);
+  ws.counters = u32(L.counters);
   ws.records = reinterpret_cast<float4*>(b + L.records);
   ws.rects = reinterpret_cast<uint2*>(b + L.rects);
   ws.adjoints = reinterpret_cast<float4*>(b + L.adjoints);
-  ws.visible = reinterpret_cast<uint32_t*>(b + L.visible);
-  ws.gauss_list = reinterpret_cast<uint32_t*>(b + L.gauss_list);
-  ws.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
-  ws.tile_start = reinterpret_cast<uint32_t*>(b + L.tile_start);
-  ws.tile_cursor = reinterpret_cast<uint32_t*>(b + L.tile_cursor);
-  ws.long_tiles = reinterpret_cast<uint32_t*>(b + L.long_tiles);
-  ws.bucket_count = reinterpret_cast<uint32_t*>(b + L.bucket_count);
-  ws.bucket_start = reinterpret_cast<uint32_t*>(b + L.bucket_start);
-  ws.bucket_cursor = reinterpret_cast<uint32_t*>(b + L.bucket_cursor);
-  ws.row_items = reinterpret_cast<uint2*>(b + L.row_items);
-  ws.row_span = reinterpret_cast<uint32_t*>(b + L.row_span);
-  ws.cta_counts = reinterpret_cast<uint32_t*>(b + L.cta_counts);
-  ws.keys = reinterpret_cast<unsigned long long*>(b + L.keys);
-  ws.keys_alt = reinterpret_cast<unsigned long long*>(b + L.keys_alt);
-  ws.sorted_ids = reinterpret_cast<uint32_t*>(b + L.sorted_ids);
+  ws.visible = u32(L.visible);
+  ws.vis_key = u32(L.vis_key);
+  ws.sort_key = u32(L.sort_key);
+  ws.sort_val = u32(L.sort_val);
+  ws.radix_status = u32(L.radix_status);
+  ws.view_start = u32(L.view_start);
+  ws.gauss_list = u32(L.gauss_list);
+  ws.tile_count = u32(L.tile_count);
+  ws.tile_start = u32(L.tile_start);
+  ws.bucket_count = u32(L.bucket_count);
+  ws.bucket_start = u32(L.bucket_start);
+  ws.unit_first_e = u32(L.unit_first_e);
+  ws.unit_seg_e = u32(L.unit_seg_e);
+  ws.unit_cnt_e = u32(L.unit_cnt_e);
+  ws.unit_first_r = u32(L.unit_first_r);
+  ws.unit_seg_r = u32(L.unit_seg_r);
+  ws.unit_cnt_r = u32(L.unit_cnt_r);
+  ws.row_items = u32(L.row_items);
+  ws.row_span = u32(L.row_span);
+  ws.sorted_ids = u32(L.sorted_ids);
   ws.view_stats = reinterpret_cast<float*>(b + L.view_stats);
   ws.n = w->n;
   ws.cap = w->pair_capacity;
@@ -81,6 +95,9 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.tiles_x = (ws.width + 15) / 16;
   ws.tiles_y = (ws.height + 15) / 16;
   ws.tiles_per_view = ws.tiles_x * ws.tiles_y;
+  ws.units_e_max = ((int64_t)ws.views * ws.n + kEntryUnit - 1) / kEntryUnit + ws.views;
+  ws.units_r_max = (ws.cap + kRowUnit - 1) / kRowUnit + (int64_t)ws.views * ws.tiles_y;
+  ws.radix_tiles_max = ((int64_t)ws.views * ws.n + kRadixTileEntries - 1) / kRadixTileEntries;
   return ws;
 }
 
@@ -425,11 +442,11 @@ int32_t gs_trace_stop(void) {
 }
 
 const char* gs_kernel_name(int32_t id) {
-  static const char* names[kKNumKernels] = {"project",     "scan",           "scatter_rows",  "sort_small",
-                                            "sort_long",   "render_fwd",     "count_depth",   "render_bwd",
-                                            "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
-                                            "rows_emit",   "ssim_fwd",       "ssim_bwd",      "sparse_adam",
-                                            "sort_medium", "render_fwd_ckpt", "render_bwd_bucket"};
+  static const char* names[kKNumKernels] = {
+      "project",    "scan",           "scatter_rows",   "depth_hist",    "depth_scan",  "render_fwd",
+      "count_depth", "render_bwd",    "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
+      "rows_emit",  "ssim_fwd",       "ssim_bwd",       "sparse_adam",   "depth_scatter", "render_fwd_ckpt",
+      "render_bwd_bucket", "entry_order", "entry_units", "entry_rows",   "unit_scan"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

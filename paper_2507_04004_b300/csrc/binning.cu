@@ -1,0 +1,692 @@
+// Binning of the kept (Gaussian, tile) pairs into per-tile lists ordered by
+// (depth key, Gaussian index) - the front-to-back order the compositing of
+// Eq. rendered_rgb walks - without sorting any pair.
+//
+// The order of a tile's list is the order of its Gaussians' depth keys, and
+// every Gaussian has one depth key per view.  So the visible (view, Gaussian)
+// entries are sorted once, and everything after that is a stable scatter:
+//   1. stable LSD radix sort of the visible entries by (view, depth key) -
+//      four 8-bit passes on the key, one or two on the view, one kernel per
+//      pass - then runs of equal keys put in index order (k_radix_*,
+//      k_entry_order);
+//   2. stable scatter of the sorted entries into (view, tile row) buckets,
+//      one "row item" per tile row of an entry's box (k_entry_rows,
+//      k_unit_scan, k_rows_scatter);
+//   3. per row item the exact kept-tile span of Sec. "Fast Tile-based
+//      Culling" (16 pixel-row chords) and per-tile counts (k_rows_count,
+//      k_unit_scan), the tile ranges (k_scan_tiles);
+//   4. stable scatter of the row items' kept tiles into the tile bins, which
+//      writes each tile's Gaussian indices in order (k_rows_emit).
+// Stable scatters: the input is cut into units (up to kEntryUnit sorted
+// entries of one view, up to kRowUnit row items of one bucket), one warp per
+// unit.  A unit's counts per output bin are scanned over the units of its
+// segment in order, which gives each unit its first slot in every bin; inside
+// a unit, a warp takes 32 inputs at a time and ranks each lane among the
+// lower lanes that cover the same bin (per-warp lane masks in shared memory).
+// Pairs and row items thus keep their input order, and no bin is sorted.
+#include "gs_internal.h"
+
+namespace gsb {
+
+constexpr int kScanThreads = 1024;
+constexpr int kRadixThreads = 256;
+constexpr int kUnitWarps = 8;  // warps (units in flight) per CTA of the unit kernels
+
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive scan of count(i), i < n, by one CTA of kScanThreads: start[i] =
+// sum of counts before i; returns the 64-bit total (to every thread).  Each
+// warp owns a contiguous segment and walks it 32 counts at a time.
+template <typename F>
+__device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
+  constexpr int NW = kScanThreads / 32;
+  __shared__ unsigned long long wbase[NW + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = (n + NW - 1) / NW;
+  const int64_t b = min(n, (int64_t)warp * seg), e = min(n, b + seg);
+  unsigned long long s = 0;
+  for (int64_t i = b + lane; i < e; i += 32) s += count(i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if (lane == 0) wbase[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long v = wbase[lane];  // NW == 32
+    unsigned long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    wbase[lane] = inc - v;
+    if (lane == 31) wbase[NW] = inc;
+  }
+  __syncthreads();
+  unsigned long long run = wbase[warp];
+  for (int64_t i0 = b; i0 < e; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const unsigned long long c = i < e ? count(i) : 0u;
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (i < e) {
+      const unsigned long long ex = run + inc - c;
+      start[i] = ex > 0xffffffffull ? 0xffffffffu : (uint32_t)ex;
+    }
+    run += __shfl_sync(kFull, inc, 31);
+  }
+  const unsigned long long total = wbase[NW];
+  __syncthreads();
+  return total;
+}
+
+// Units of n_seg segments of cnt(s) items, unit_len items per unit: first[s]
+// = first unit of segment s (first[n_seg] = total), seg[u] = segment of unit
+// u, *total_out = total.  One CTA; more than max_units units (not expected:
+// the workspace is sized for the capacities checked before) flag an error.
+template <typename F>
+__device__ void build_units(F cnt, int64_t n_seg, uint32_t unit_len, int64_t max_units, uint32_t* first, uint32_t* seg,
+                            uint32_t* total_out, uint32_t* status) {
+  auto nu = [&](int64_t s) { return (uint32_t)((cnt(s) + unit_len - 1) / unit_len); };
+  const unsigned long long total = block_scan(nu, first, n_seg);
+  if (threadIdx.x == 0) {
+    first[n_seg] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    *total_out = total > (unsigned long long)max_units ? 0u : (uint32_t)total;
+    if (total > (unsigned long long)max_units) atomicExch(status, (uint32_t)GS_ERR_CUDA);
+  }
+  __syncthreads();
+  if (total > (unsigned long long)max_units) return;
+  for (int64_t s = threadIdx.x; s < n_seg; s += blockDim.x) {
+    const uint32_t f = first[s], k = nu(s);
+    for (uint32_t j = 0; j < k; ++j) seg[f + j] = (uint32_t)s;
+  }
+}
+
+// ---------------------------------------------------------------- buckets
+// Bucket (view, tile row) ranges of the row items, capacity check, row units.
+__global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
+  // The projection leaves each view's row-item counts as differences over the
+  // tile rows (+1 at an entry's first row, -1 after its last, modulo 2^32):
+  // a running sum per view, one warp per view, turns them into counts.
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int v = warp; v < ws.views; v += kScanThreads / 32) {
+      uint32_t* c = ws.bucket_count + (int64_t)v * ws.tiles_y;
+      uint32_t carry = 0;
+      for (int t0 = 0; t0 < ws.tiles_y; t0 += 32) {
+        const int ty = t0 + lane;
+        uint32_t x = warp_incl_scan(ty < ws.tiles_y ? c[ty] : 0u, lane) + carry;
+        if (ty < ws.tiles_y) c[ty] = x;
+        carry = __shfl_sync(kFull, x, 31);
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 6 * 256; i += kScanThreads) ws.radix_status[i] = 0;  // the sort's digit counts
+  const int64_t nb = (int64_t)ws.views * ws.tiles_y;
+  const uint32_t* bc = ws.bucket_count;
+  const unsigned long long total = block_scan([&](int64_t i) { return bc[i]; }, ws.bucket_start, nb);
+  if (threadIdx.x == 0) {
+    ws.counters[kRowCount] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    if (total > (unsigned long long)ws.cap) {
+      ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+      ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
+    }
+  }
+  if (total > (unsigned long long)ws.cap) return;
+  build_units([&](int64_t s) { return bc[s]; }, nb, kRowUnit, ws.units_r_max, ws.unit_first_r, ws.unit_seg_r,
+              ws.counters + kRowUnits, ws.counters + kStatus);
+}
+
+// ---------------------------------------------------------------- entry sort
+// Digit of an entry in pass p: bytes of the depth key for p < 4, then the
+// bytes of the view (entry / N).  LSD order makes the last pass the most
+// significant: (view, depth key).
+__device__ __forceinline__ uint32_t radix_digit(uint32_t key, uint32_t val, int pass, uint32_t n_per_view) {
+  if (pass < 4) return (key >> (8 * pass)) & 255u;
+  const uint32_t v = val / n_per_view;
+  return (pass == 4 ? v : v >> 8) & 255u;
+}
+
+
+// Lanes of the warp whose (active) digit equals this lane's: the AND of the
+// eight ballots of the digit's bits, each taken as is or complemented.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool act) {
+  unsigned peers = __ballot_sync(kFull, act);
+#pragma unroll
+  for (int bit = 0; bit < 8; ++bit) {
+    const bool on = (d >> bit) & 1u;
+    const unsigned m = __ballot_sync(kFull, on);
+    peers &= on ? m : ~m;
+  }
+  return peers;
+}
+
+// The sort is "onesweep": the digit counts of every pass come from one read
+// of the entries (the counts do not depend on the order), and each pass is
+// one kernel whose CTAs take tiles of kSortTile consecutive entries by
+// ticket, rank them stably, and find where their run of each digit starts by
+// looking back over the earlier tiles' published counts (decoupled
+// look-back).  A tile's status word per digit: bits 30-31 = 1 (its own count
+// in bits 0-29) or 2 (the count of all tiles up to and including it); the
+// workspace allows fewer than 2^30 (view, Gaussian) entries.  Waits on an
+// earlier tile are bounded: past kSpinLimit polls the status word of the
+// workspace becomes GS_ERR_TIMEOUT and the pass writes only in-range slots.
+constexpr int kSortItems = 8;                            // entries per thread
+constexpr int kSortTile = kRadixThreads * kSortItems;    // entries per tile (kRadixTileEntries)
+static_assert(kSortTile == kRadixTileEntries, "tile size of the sort");
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValueMask = (1u << 30) - 1u;
+constexpr int kSpinLimit = 1 << 16;
+
+__device__ __forceinline__ uint32_t* radix_counts(const Ws& ws) { return ws.radix_status; }  // [6][256]
+__device__ __forceinline__ uint32_t* radix_tiles(const Ws& ws, int pass) {
+  return ws.radix_status + 6 * 256 + (int64_t)pass * ws.radix_tiles_max * 256;
+}
+
+// Digit counts of every pass over all visible entries; clears the tile status
+// words the passes will use.  The counts were zeroed by k_scan_buckets.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_counts(Ws ws, int passes) {
+  __shared__ uint32_t h[6][256];
+  if (ws.counters[kStatus] != 0) return;
+  const uint64_t n = ws.counters[kVisibleCount];
+  const uint64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* st = radix_tiles(ws, p);
+    for (uint64_t i = tid; i < ntiles * 256; i += stride) st[i] = 0;
+  }
+  for (int i = threadIdx.x; i < 6 * 256; i += kRadixThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t N = (uint32_t)ws.n;
+  for (uint64_t i = tid; i < n; i += stride) {
+    const uint32_t k = ws.vis_key[i], v = ws.visible[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][radix_digit(k, v, p, N)], 1u);
+  }
+  __syncthreads();
+  uint32_t* g = radix_counts(ws);
+  for (int i = threadIdx.x; i < passes * 256; i += kRadixThreads) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(g + i, c);
+  }
+}
+
+// One LSD pass: stable scatter of the entries by the pass's digit.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_pass(Ws ws, int pass, const uint32_t* __restrict__ key_in,
+                                                              const uint32_t* __restrict__ val_in,
+                                                              uint32_t* __restrict__ key_out,
+                                                              uint32_t* __restrict__ val_out) {
+  constexpr int NW = kRadixThreads / 32;
+  __shared__ uint32_t s_wcnt[NW][256];  // per warp: count of each digit, then its first slot in the tile
+  __shared__ uint32_t s_base[256];      // first output slot of each digit's run of this tile
+  __shared__ uint32_t s_ticket;
+  if (ws.counters[kStatus] != 0) return;
+  const uint64_t n = ws.counters[kVisibleCount];
+  const uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt(lane);
+  const uint32_t N = (uint32_t)ws.n;
+  uint32_t* status = radix_tiles(ws, pass);
+  const uint32_t* counts = radix_counts(ws) + pass * 256;
+  for (;;) {
+    for (int i = threadIdx.x; i < NW * 256; i += kRadixThreads) (&s_wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ws.counters + kRadixTicket + pass, 1u);
+    __syncthreads();
+    const uint32_t t = s_ticket;
+    if (t >= ntiles) return;
+    // this warp's 256 entries, taken lane-minor: entry order = (j, lane) order
+    const uint64_t base = (uint64_t)t * kSortTile + (uint64_t)warp * 32 * kSortItems;
+    uint32_t k[kSortItems], v[kSortItems], d[kSortItems], r[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint64_t i = base + 32 * j + lane;
+      k[j] = i < n ? key_in[i] : 0u;
+      v[j] = i < n ? val_in[i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const bool act = base + 32 * j + lane < n;
+      d[j] = radix_digit(k[j], v[j], pass, N);
+      const unsigned peers = digit_peers(d[j], act);
+      const uint32_t prev = s_wcnt[warp][d[j]];
+      r[j] = prev + __popc(peers & lt);
+      __syncwarp();
+      if (act && (peers & lt) == 0) s_wcnt[warp][d[j]] = prev + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      const int dd = threadIdx.x;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = s_wcnt[w][dd];
+        s_wcnt[w][dd] = run;
+        run += c;
+      }
+      // publish this tile's count, then look back for the runs of earlier tiles
+      volatile uint32_t* st = status;
+      st[(int64_t)t * 256 + dd] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
+      uint32_t excl = 0;
+      if (t > 0) {
+        for (int64_t tt = (int64_t)t - 1; tt >= 0; --tt) {
+          uint32_t w = st[tt * 256 + dd];
+          for (int spin = 0; (w >> 30) == 0; ++spin) {
+            if (spin >= kSpinLimit) {
+              atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_TIMEOUT);
+              w = kFlagPrefix;
+              break;
+            }
+            __nanosleep(64);
+            w = st[tt * 256 + dd];
+          }
+          excl += w & kValueMask;
+          if ((w >> 30) == 2u) break;
+        }
+        st[(int64_t)t * 256 + dd] = kFlagPrefix | (excl + run);
+      }
+      // first slot of the digit: all entries of lower digits, then earlier tiles
+      s_base[dd] = excl;
+    }
+    __syncthreads();
+    // exclusive scan of the pass's digit counts (one warp), added to s_base
+    if (warp == 0) {
+      uint32_t c8[8], tot = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { c8[q] = counts[lane * 8 + q]; tot += c8[q]; }
+      uint32_t run = warp_incl_scan(tot, lane) - tot;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] += run; run += c8[q]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint64_t i = base + 32 * j + lane;
+      if (i >= n) continue;
+      const uint64_t pos = (uint64_t)s_base[d[j]] + s_wcnt[warp][d[j]] + r[j];
+      if (pos < n) {
+        key_out[pos] = k[j];
+        val_out[pos] = v[j];
+      }
+    }
+    __syncthreads();  // s_wcnt and s_base are reused by the next tile
+  }
+}
+
+// Runs of equal (view, depth key) put in Gaussian-index order, the sorted
+// entries written to ws.visible; first sorted entry of every view.
+__global__ void __launch_bounds__(256) k_entry_order(Ws ws, const uint32_t* __restrict__ key,
+                                                     const uint32_t* __restrict__ val) {
+  if (ws.counters[kStatus] != 0) return;
+  const uint64_t n = ws.counters[kVisibleCount];
+  const uint32_t N = (uint32_t)ws.n;
+  const int64_t V = ws.views;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  if (n == 0) {
+    for (uint64_t u = tid; u <= (uint64_t)V; u += stride) ws.view_start[u] = 0;
+    return;
+  }
+  for (uint64_t i = tid; i < n; i += stride) {
+    const uint32_t k = key[i], e = val[i], v = e / N;
+    auto same = [&](uint64_t j) { return key[j] == k && val[j] / N == v; };
+    const bool prev = i > 0 && same(i - 1), next = i + 1 < n && same(i + 1);
+    if (!prev && !next) {
+      ws.visible[i] = e;
+    } else {
+      uint64_t s = i, t = i + 1;
+      while (s > 0 && same(s - 1)) --s;
+      while (t < n && same(t)) ++t;
+      uint32_t rank = 0;
+      for (uint64_t j = s; j < t; ++j) rank += val[j] < e ? 1u : 0u;
+      ws.visible[s + rank] = e;
+    }
+    const int64_t vp = i > 0 ? (int64_t)(val[i - 1] / N) : -1;
+    for (int64_t u = vp + 1; u <= (int64_t)v; ++u) ws.view_start[u] = (uint32_t)i;
+    if (i + 1 == n)
+      for (int64_t u = (int64_t)v + 1; u <= V; ++u) ws.view_start[u] = (uint32_t)n;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_entry_units(Ws ws) {
+  if (ws.counters[kStatus] != 0) return;
+  const uint32_t* vs = ws.view_start;
+  build_units([&](int64_t s) { return vs[s + 1] - vs[s]; }, ws.views, kEntryUnit, ws.units_e_max, ws.unit_first_e,
+              ws.unit_seg_e, ws.counters + kEntryUnits, ws.counters + kStatus);
+}
+
+// ---------------------------------------------------------------- stable scatters
+// Exclusive scan of unit counts over each segment's units, per bin, one warp
+// per (segment, bin).  Tables are bin-major, table[x * stride + u], so a
+// segment's units are contiguous in each bin's row: table[x][u] becomes the
+// first slot of unit u in bin x relative to the bin's start.  totals (may be
+// NULL) receives each (segment, bin) total; expect (may be NULL) holds totals
+// to check against.
+__global__ void __launch_bounds__(256) k_unit_scan(Ws ws, uint32_t* __restrict__ table, int64_t stride,
+                                                   const uint32_t* __restrict__ first, int64_t n_seg, int bins,
+                                                   uint32_t* __restrict__ totals, const uint32_t* __restrict__ expect) {
+  if (ws.counters[kStatus] != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (idx >= n_seg * bins) return;
+  const int64_t s = idx / bins;
+  const int x = (int)(idx - s * bins);
+  const uint32_t u0 = first[s], u1 = first[s + 1];
+  uint32_t* row = table + (int64_t)x * stride;
+  uint32_t run = 0;
+  for (uint32_t c0 = u0; c0 < u1; c0 += 128) {
+    uint32_t c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = c0 + 32 * j + lane;
+      c[j] = u < u1 ? row[u] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = c0 + 32 * j + lane;
+      const uint32_t incl = warp_incl_scan(c[j], lane);
+      if (u < u1) row[u] = run + incl - c[j];
+      run += __shfl_sync(kFull, incl, 31);
+    }
+  }
+  if (lane == 0) {
+    if (totals) totals[s * bins + x] = run;
+    if (expect && expect[s * bins + x] != run) atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+  }
+}
+
+// Row items per tile row of every entry unit (differences, then a prefix).
+__global__ void __launch_bounds__(32 * kUnitWarps) k_entry_rows(Ws ws) {
+  extern __shared__ uint32_t s_dyn[];
+  if (ws.counters[kStatus] != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ny = ws.tiles_y;
+  uint32_t* cnt = s_dyn + warp * (ny + 1);
+  const uint32_t nu = ws.counters[kEntryUnits];
+  for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
+    const uint32_t v = ws.unit_seg_e[u];
+    const uint32_t i0 = ws.view_start[v] + (u - ws.unit_first_e[v]) * kEntryUnit;
+    const uint32_t i1 = min(i0 + (uint32_t)kEntryUnit, ws.view_start[v + 1]);
+    for (int t = lane; t <= ny; t += 32) cnt[t] = 0;
+    __syncwarp();
+    for (uint32_t i = i0 + lane; i < i1; i += 32) {
+      const uint2 r = ws.rects[ws.visible[i]];
+      atomicAdd(cnt + (r.x >> 16), 1u);
+      atomicSub(cnt + (r.y >> 16) + 1, 1u);
+    }
+    __syncwarp();
+    uint32_t run = 0;
+    for (int t0 = 0; t0 < ny; t0 += 32) {
+      const int t = t0 + lane;
+      const uint32_t x = warp_incl_scan(t < ny ? cnt[t] : 0u, lane) + run;
+      if (t < ny) ws.unit_cnt_e[(int64_t)t * ws.units_e_max + u] = x;
+      run = __shfl_sync(kFull, x, 31);
+    }
+    __syncwarp();
+  }
+}
+
+// Stable ranking inside a warp: the 32 lanes' inputs each cover some bins;
+// a lane marks its bit in a per-warp mask of every bin it covers, reads back
+// the masks to rank itself among the lower lanes of the same bin, and the
+// lowest lane of each bin advances the bin's base and clears its mask.
+
+// Sorted entries -> row items, grouped by (view, tile row), in entry order.
+__global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
+  extern __shared__ uint32_t s_dyn[];
+  if (ws.counters[kStatus] != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt(lane);
+  const int ny = ws.tiles_y;
+  uint32_t* base = s_dyn + warp * 3 * ny;
+  uint32_t* end = base + ny;
+  uint32_t* mask = end + ny;
+  const uint32_t nu = ws.counters[kEntryUnits];
+  for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
+    const uint32_t v = ws.unit_seg_e[u];
+    const uint32_t i0 = ws.view_start[v] + (u - ws.unit_first_e[v]) * kEntryUnit;
+    const uint32_t i1 = min(i0 + (uint32_t)kEntryUnit, ws.view_start[v + 1]);
+    for (int t = lane; t < ny; t += 32) {
+      const int64_t b = (int64_t)v * ny + t;
+      const uint32_t bs = ws.bucket_start[b];
+      base[t] = bs + ws.unit_cnt_e[(int64_t)t * ws.units_e_max + u];
+      end[t] = bs + ws.bucket_count[b];
+      mask[t] = 0;
+    }
+    __syncwarp();
+    for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
+      const uint32_t i = r0 + lane;
+      uint32_t e = 0;
+      int y0 = 0, y1 = -1;
+      if (i < i1) {
+        e = ws.visible[i];
+        const uint2 r = ws.rects[e];
+        y0 = (int)(r.x >> 16);
+        y1 = (int)(r.y >> 16);
+      }
+      for (int y = y0; y <= y1; ++y) atomicOr(mask + y, 1u << lane);
+      __syncwarp();
+      for (int y = y0; y <= y1; ++y) {
+        const uint32_t pos = base[y] + __popc(mask[y] & lt);
+        if (pos < end[y]) ws.row_items[pos] = e;
+        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+      }
+      __syncwarp();
+      for (int y = y0; y <= y1; ++y) {
+        const uint32_t m = mask[y];
+        if (m != 0 && (m & lt) == 0) {  // lowest lane of this row
+          base[y] += __popc(m);
+          mask[y] = 0;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Kept-tile span of every row item (Sec. "Fast Tile-based Culling": the
+// exact chords of the 16 pixel rows) and pairs per tile of every row unit.
+__global__ void __launch_bounds__(32 * kUnitWarps) k_rows_count(Ws ws) {
+  extern __shared__ uint32_t s_dyn[];
+  if (ws.counters[kStatus] != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nx = ws.tiles_x;
+  uint32_t* cnt = s_dyn + warp * (nx + 1);
+  const uint32_t nu = ws.counters[kRowUnits];
+  for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
+    const uint32_t b = ws.unit_seg_r[u];
+    const int ty = (int)(b % (uint32_t)ws.tiles_y);
+    const uint32_t bs = ws.bucket_start[b];
+    const uint32_t i0 = bs + (u - ws.unit_first_r[b]) * kRowUnit;
+    const uint32_t i1 = min(i0 + (uint32_t)kRowUnit, bs + ws.bucket_count[b]);
+    for (int t = lane; t <= nx; t += 32) cnt[t] = 0;
+    __syncwarp();
+    for (uint32_t i = i0 + lane; i < i1; i += 32) {
+      const int64_t e = ws.row_items[i];
+      const Ellipse el = make_ellipse(ws.records[3 * e], ws.records[3 * e + 1]);
+      const RowSpan sp = row_span(el, ty, ws.width, ws.height);
+      ws.row_span[i] = pack_span(sp);
+      if (sp.lo > sp.hi) continue;
+      if (!sp.gap) {
+        atomicAdd(cnt + sp.lo, 1u);
+        atomicSub(cnt + sp.hi + 1, 1u);
+      } else {
+        for (int tx = sp.lo; tx <= sp.hi; ++tx)
+          if (tile_kept(el, tx, ty, ws.width, ws.height)) {
+            atomicAdd(cnt + tx, 1u);
+            atomicSub(cnt + tx + 1, 1u);
+          }
+      }
+    }
+    __syncwarp();
+    uint32_t run = 0;
+    for (int t0 = 0; t0 < nx; t0 += 32) {
+      const int t = t0 + lane;
+      const uint32_t x = warp_incl_scan(t < nx ? cnt[t] : 0u, lane) + run;
+      if (t < nx) ws.unit_cnt_r[(int64_t)t * ws.units_r_max + u] = x;
+      run = __shfl_sync(kFull, x, 31);
+    }
+    __syncwarp();
+  }
+}
+
+// Tile ranges of the pairs (exclusive scan of the per-tile counts) and the
+// capacity check.  Counts fit in 32 bits; the total is checked in 64 bits.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Ws ws) {
+  if (ws.counters[kStatus] != 0) return;
+  const uint32_t* tc = ws.tile_count;
+  const unsigned long long total =
+      block_scan([&](int64_t i) { return tc[i]; }, ws.tile_start, (int64_t)ws.views * ws.tiles_per_view);
+  if (threadIdx.x == 0) {
+    ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    if (total > (unsigned long long)ws.cap) ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
+  }
+}
+
+// Row items -> the Gaussian index of every kept (Gaussian, tile) pair in its
+// tile's bin, in row-item order, i.e. (depth key, index) order.
+__global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
+  extern __shared__ uint32_t s_dyn[];
+  if (ws.counters[kStatus] != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt(lane);
+  const int nx = ws.tiles_x;
+  uint32_t* base = s_dyn + warp * 3 * nx;
+  uint32_t* end = base + nx;
+  uint32_t* mask = end + nx;
+  const int64_t N = ws.n;
+  const uint32_t nu = ws.counters[kRowUnits];
+  for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
+    const uint32_t b = ws.unit_seg_r[u];
+    const int ty = (int)(b % (uint32_t)ws.tiles_y);
+    const int64_t vN = (int64_t)(b / (uint32_t)ws.tiles_y) * N;
+    const uint32_t bs = ws.bucket_start[b];
+    const uint32_t i0 = bs + (u - ws.unit_first_r[b]) * kRowUnit;
+    const uint32_t i1 = min(i0 + (uint32_t)kRowUnit, bs + ws.bucket_count[b]);
+    for (int x = lane; x < nx; x += 32) {
+      const int64_t t = (int64_t)b * nx + x;
+      const uint32_t ts = ws.tile_start[t];
+      base[x] = ts + ws.unit_cnt_r[(int64_t)x * ws.units_r_max + u];
+      end[x] = ts + ws.tile_count[t];
+      mask[x] = 0;
+    }
+    __syncwarp();
+    for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
+      const uint32_t i = r0 + lane;
+      int lo = 0, hi = -1;
+      bool gap = false;
+      int64_t e = 0;
+      if (i < i1) {
+        const RowSpan sp = unpack_span(ws.row_span[i]);
+        e = ws.row_items[i];
+        lo = sp.lo;
+        hi = sp.hi;
+        gap = sp.gap;
+      }
+      // a span with a gap (very thin tilted ellipses): its tiles are tested exactly
+      Ellipse el;
+      if (gap) el = make_ellipse(ws.records[3 * e], ws.records[3 * e + 1]);
+      auto kept = [&](int x) { return !gap || tile_kept(el, x, ty, ws.width, ws.height); };
+      for (int x = lo; x <= hi; ++x)
+        if (kept(x)) atomicOr(mask + x, 1u << lane);
+      __syncwarp();
+      const uint32_t g = (uint32_t)(e - vN);
+      for (int x = lo; x <= hi; ++x) {
+        if (!kept(x)) continue;
+        const uint32_t pos = base[x] + __popc(mask[x] & lt);
+        if (pos < end[x]) ws.sorted_ids[pos] = g;
+        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+      }
+      __syncwarp();
+      for (int x = lo; x <= hi; ++x) {
+        const uint32_t m = mask[x];
+        if (m != 0 && (m & lt) == 0) {  // lowest lane of this tile
+          base[x] += __popc(m);
+          mask[x] = 0;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
+  cudaError_t err;
+  auto done = [&](void) { trace_end(st); return cudaGetLastError(); };
+  trace_begin(kKScanBuckets, st);
+  k_scan_buckets<<<1, kScanThreads, 0, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+
+  // 1. entries sorted by (view, depth key), then index inside equal keys
+  const int64_t E = (int64_t)ws.views * ws.n;
+  const int passes = 4 + (ws.views > 1 ? (ws.views > 256 ? 2 : 1) : 0);
+  trace_begin(kKDepthHist, st);
+  k_radix_counts<<<sm_count() * 4, kRadixThreads, 0, st>>>(ws, passes);
+  if ((err = done()) != cudaSuccess) return err;
+  const uint32_t* key = ws.vis_key;
+  const uint32_t* val = ws.visible;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* ko = ws.sort_key + (p & 1) * E;
+    uint32_t* vo = ws.sort_val + (p & 1) * E;
+    trace_begin(kKDepthScatter, st);
+    k_radix_pass<<<sm_count() * 4, kRadixThreads, 0, st>>>(ws, p, key, val, ko, vo);
+    if ((err = done()) != cudaSuccess) return err;
+    key = ko;
+    val = vo;
+  }
+  trace_begin(kKEntryOrder, st);
+  k_entry_order<<<sm_count() * 4, 256, 0, st>>>(ws, key, val);
+  if ((err = done()) != cudaSuccess) return err;
+  trace_begin(kKEntryUnits, st);
+  k_entry_units<<<1, kScanThreads, 0, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+
+  // 2. row items by (view, tile row), entry order inside
+  const unsigned ugrid = (unsigned)sm_count() * 8;
+  const size_t smem_er = (size_t)kUnitWarps * (ws.tiles_y + 1) * sizeof(uint32_t);
+  trace_begin(kKEntryRows, st);
+  k_entry_rows<<<ugrid, 32 * kUnitWarps, smem_er, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+  const int64_t ne = (int64_t)ws.views * ws.tiles_y;
+  trace_begin(kKUnitScan, st);
+  k_unit_scan<<<(unsigned)((ne + 7) / 8), 256, 0, st>>>(ws, ws.unit_cnt_e, ws.units_e_max, ws.unit_first_e, ws.views,
+                                                        ws.tiles_y, nullptr, ws.bucket_count);
+  if ((err = done()) != cudaSuccess) return err;
+  const size_t smem_rs = (size_t)kUnitWarps * 3 * ws.tiles_y * sizeof(uint32_t);
+  trace_begin(kKScatterRows, st);
+  k_rows_scatter<<<ugrid, 32 * kUnitWarps, smem_rs, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+
+  // 3. kept-tile spans, tile counts and ranges
+  const size_t smem_rc = (size_t)kUnitWarps * (ws.tiles_x + 1) * sizeof(uint32_t);
+  trace_begin(kKRowsCount, st);
+  k_rows_count<<<ugrid, 32 * kUnitWarps, smem_rc, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+  const int64_t nt = (int64_t)ws.views * ws.tiles_per_view;
+  trace_begin(kKUnitScan, st);
+  k_unit_scan<<<(unsigned)((nt + 7) / 8), 256, 0, st>>>(ws, ws.unit_cnt_r, ws.units_r_max, ws.unit_first_r,
+                                                        (int64_t)ws.views * ws.tiles_y, ws.tiles_x, ws.tile_count,
+                                                        nullptr);
+  if ((err = done()) != cudaSuccess) return err;
+  trace_begin(kKScan, st);
+  k_scan_tiles<<<1, kScanThreads, 0, st>>>(ws);
+  if ((err = done()) != cudaSuccess) return err;
+
+  // 4. the tile bins, filled in order
+  const size_t smem_em = (size_t)kUnitWarps * 3 * ws.tiles_x * sizeof(uint32_t);
+  trace_begin(kKRowsEmit, st);
+  k_rows_emit<<<ugrid, 32 * kUnitWarps, smem_em, st>>>(ws);
+  return done();
+}
+
+}  // namespace gsb

@@ -24,37 +24,48 @@ constexpr int kBwdBatch = 128;  // Gaussians staged in shared memory per batch b
 
 // Device view of the workspace parts (pointers resolved from gs_layout).
 struct Ws {
-  uint32_t* counters;     // [0] status [1] pairs needed [2] visible count [3] long-tile count
+  uint32_t* counters;     // see CounterSlot
   float4* records;        // [V*N][3]
   uint2* rects;           // [V*N]
   float4* adjoints;       // [V*N][3]
-  uint32_t* visible;      // [V*N]
+  uint32_t* visible;      // [V*N] visible entries v*N + g: projection order, then (view, depth key, index) order
+  uint32_t* vis_key;      // [V*N] depth key bits of each visible entry, projection order
+  uint32_t* sort_key;     // [2][V*N] radix-sort buffers (keys)
+  uint32_t* sort_val;     // [2][V*N] radix-sort buffers (entries)
+  uint32_t* radix_status; // [6][256] digit counts of the sort's passes, then [6][radix_tiles_max][256] tile status
+  uint32_t* view_start;   // [V + 1] first sorted visible entry of each view
   uint32_t* gauss_list;   // [N] Gaussians visible in at least one view
   uint32_t* tile_count;   // [V*T]
   uint32_t* tile_start;   // [V*T]
-  uint32_t* tile_cursor;  // [V*T]
-  uint32_t* long_tiles;   // [V*T] long bins from the front, medium bins from the back
   uint32_t* bucket_count;   // [V*tiles_y] row items per (view, tile row)
   uint32_t* bucket_start;   // [V*tiles_y]
-  uint32_t* bucket_cursor;  // [V*tiles_y]
-  uint2* row_items;         // [cap] (entry v*N + g, bucket v*tiles_y + ty), grouped by bucket
+  uint32_t* unit_first_e;   // [V + 1] first entry unit of each view
+  uint32_t* unit_seg_e;     // [units_e_max] view of each entry unit
+  uint32_t* unit_cnt_e;     // [units_e_max][tiles_y] row items per tile row of each entry unit, then offsets
+  uint32_t* unit_first_r;   // [V*tiles_y + 1] first row unit of each bucket
+  uint32_t* unit_seg_r;     // [units_r_max] bucket of each row unit
+  uint32_t* unit_cnt_r;     // [units_r_max][tiles_x] pairs per tile of each row unit, then offsets
+  uint32_t* row_items;      // [cap] entry of each row item, by bucket, (depth key, index) order inside
   uint32_t* row_span;       // [cap] packed kept-tile span of each row item
-  uint32_t* cta_counts;     // [kRowsGridMax][2 * tiles_x] pairs per tile of each binning CTA's window
-  unsigned long long* keys;      // [cap]
-  unsigned long long* keys_alt;  // [cap]
   uint32_t* sorted_ids;   // [cap]
   float* view_stats;      // [V][4]
   int64_t n;
   int64_t cap;
+  int64_t units_e_max, units_r_max, radix_tiles_max;
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
 
-// Most CTAs the binning kernels launch (their per-CTA tile counts have a
-// workspace slot each).
-constexpr int kRowsGridMax = 2048;
+// Binning granularity: an entry unit is up to kEntryUnit consecutive sorted
+// visible entries of one view, a row unit up to kRowUnit row items of one
+// (view, tile row) bucket; one warp processes one unit.
+constexpr int kEntryUnit = 256;
+constexpr int kRowUnit = 128;
+// Entries per tile of the sort's passes (256 threads x 8).
+constexpr int kRadixTileEntries = 2048;
 
 enum CounterSlot {
-  kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kLongCount = 3, kRowCount = 4, kGaussCount = 5, kMediumCount = 6
+  kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kEntryUnits = 3, kRowCount = 4, kGaussCount = 5, kRowUnits = 6,
+  kRadixTicket = 8  // [8, 14): tile tickets of the sort's passes
 };
 
 struct Cam {

@@ -10,9 +10,10 @@ namespace gsb {
 
 // Kernel ids reported by the tracing hook (gs_trace_start).
 enum KernelId {
-  kKProject = 0, kKScan, kKScatterRows, kKSortSmall, kKSortLong, kKRenderFwd, kKCountDepth, kKRenderBwd,
+  kKProject = 0, kKScan, kKScatterRows, kKDepthHist, kKDepthScan, kKRenderFwd, kKCountDepth, kKRenderBwd,
   kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
-  kKSortMedium, kKRenderFwdCkpt, kKRenderBwdBucket, kKNumKernels
+  kKDepthScatter, kKRenderFwdCkpt, kKRenderBwdBucket, kKEntryOrder, kKEntryUnits, kKEntryRows, kKUnitScan,
+  kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);

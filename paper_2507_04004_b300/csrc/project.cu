@@ -1,5 +1,5 @@
-// Projection and SH colour of every (view, Gaussian), tile culling, and the
-// binning of kept (Gaussian, tile) pairs into per-tile bins.
+// Projection and SH colour of every (view, Gaussian), with the tile box and
+// the row-item counts that the binning (binning.cu) starts from.
 //
 // arxiv 2507.04004, Sec. "3D Gaussian Splatting Representation":
 //   mu_hat = R mu + t, d = e3^T mu_hat, mu' = pi_c(mu_hat / d),
@@ -10,20 +10,10 @@
 // Strategies" (d): lanes carry a validity flag to one common exit and whole
 // warps whose Gaussians are all cut skip the rest.
 //
-// Binning without per-pair global atomics:
-//   1. k_project   - records, tile box, and per-CTA shared-memory counts of
-//                    "row items" (one per (Gaussian, tile row of its box))
-//                    per bucket (view, tile row), flushed once per CTA;
-//   2. scan of the bucket counts;
-//   3. k_scatter_rows - row items written grouped by bucket (per-CTA ranges
-//                    reserved with one atomic per bucket);
-//   4. k_rows_count - per row item the exact kept-tile span (16 chords); the
-//                    items of one CTA lie in one or two tile rows, so per-tile
-//                    counts accumulate in shared memory and reach global memory
-//                    once per (CTA, tile);
-//   5. scan of the tile counts;
-//   6. k_rows_emit  - keys written into the tile bins through per-CTA ranges
-//                    reserved once per (CTA, tile).
+// The projection also writes, per view, the number of row items (one per
+// (Gaussian, tile row of its box)) of every tile row as differences, and the
+// compact list of visible entries with their depth keys; binning.cu takes it
+// from there.
 #include "gs_internal.h"
 
 namespace gsb {
@@ -63,8 +53,6 @@ __device__ __forceinline__ Cam staged_cam(const float4* p) {
   c.fx = f.x; c.fy = f.y; c.cx = f.z; c.cy = f.w;
   return c;
 }
-constexpr int kMaxWindow = 2048;
-constexpr int kScatterThreads = 512;   // tiles of one CTA's row window kept in shared memory (two rows of 8K pixels)
 
 template <int DEG, bool BF16>
 __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera* __restrict__ cams, gs_config cfg,
@@ -295,7 +283,12 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         if (lane == 0) gb = atomicAdd(ws.counters + kVisibleCount, (uint32_t)wn);
         gb = __shfl_sync(kFull, gb, 0);
         __syncwarp();  // every lane's list entries before the reads below
-        for (int i = lane; i < wn; i += 32) ws.visible[gb + i] = w_vis[i];
+        for (int i = lane; i < wn; i += 32) {
+          const uint32_t e = w_vis[i];
+          ws.visible[gb + i] = e;
+          // the entry's depth key (its record was written by this warp before the __syncwarp)
+          ws.vis_key[gb + i] = __float_as_uint(ws.records[3 * (int64_t)e + 1].z);
+        }
         __syncwarp();  // read before the next chunk refills the list
       }
     }
@@ -314,182 +307,6 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
       if (s_bucket[i]) atomicAdd(ws.bucket_count + i, s_bucket[i]);
-  }
-}
-
-// Row items grouped by bucket.  Each CTA takes a contiguous range of the
-// visible list, counts its items per bucket, reserves one range per bucket
-// and fills it.
-__global__ void __launch_bounds__(kScatterThreads) k_scatter_rows(Ws ws) {
-  __shared__ uint32_t s_cnt[kMaxBuckets];
-  __shared__ uint32_t s_base[kMaxBuckets];
-  if (ws.counters[kStatus] != 0) return;
-  const uint32_t nvis = ws.counters[kVisibleCount];
-  const int nb = ws.views * ws.tiles_y;
-  const bool smem = nb <= kMaxBuckets;
-  const uint64_t lo = (uint64_t)nvis * blockIdx.x / gridDim.x, hi = (uint64_t)nvis * (blockIdx.x + 1) / gridDim.x;
-  const int64_t n = ws.n;
-  if (smem) {
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const uint32_t e = ws.visible[i];
-      const int v = (int)(e / (uint64_t)n);
-      int tx0, ty0, tx1, ty1;
-      unpack_rect(ws.rects[e], &tx0, &ty0, &tx1, &ty1);
-      for (int ty = ty0; ty <= ty1; ++ty) atomicAdd(s_cnt + v * ws.tiles_y + ty, 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-      s_base[i] = s_cnt[i] ? atomicAdd(ws.bucket_cursor + i, s_cnt[i]) : 0u;
-      s_cnt[i] = 0;
-    }
-    __syncthreads();
-  }
-  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const uint32_t e = ws.visible[i];
-    const int v = (int)(e / (uint64_t)n);
-    int tx0, ty0, tx1, ty1;
-    unpack_rect(ws.rects[e], &tx0, &ty0, &tx1, &ty1);
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      const int b = v * ws.tiles_y + ty;
-      const uint32_t slot = smem ? s_base[b] + atomicAdd(s_cnt + b, 1u) : atomicAdd(ws.bucket_cursor + b, 1u);
-      ws.row_items[slot] = make_uint2(e, (uint32_t)b);
-    }
-  }
-}
-
-// Range of row items [lo, hi) of this CTA and the buckets it spans.
-struct RowRange {
-  uint32_t lo, hi;
-  int b_first, b_last;
-};
-
-__device__ __forceinline__ RowRange row_range(const Ws& ws) {
-  RowRange r;
-  const uint32_t nr = ws.counters[kRowCount];
-  r.lo = (uint32_t)((uint64_t)nr * blockIdx.x / gridDim.x);
-  r.hi = (uint32_t)((uint64_t)nr * (blockIdx.x + 1) / gridDim.x);
-  r.b_first = r.lo < r.hi ? (int)ws.row_items[r.lo].y : 0;
-  r.b_last = r.lo < r.hi ? (int)ws.row_items[r.hi - 1].y : -1;
-  return r;
-}
-
-// Kept-tile span of every row item and per-tile pair counts.
-__global__ void __launch_bounds__(256) k_rows_count(Ws ws) {
-  __shared__ uint32_t s_cnt[kMaxWindow];
-  if (ws.counters[kStatus] != 0) return;
-  const RowRange rr = row_range(ws);
-  if (rr.lo >= rr.hi) return;
-  const int tiles_x = ws.tiles_x;
-  const int64_t win0 = (int64_t)rr.b_first * tiles_x;
-  const int nwin = (rr.b_last - rr.b_first + 1) * tiles_x;
-  const bool smem = nwin <= kMaxWindow;
-  if (smem) {
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
-  }
-  for (uint32_t i = rr.lo + threadIdx.x; i < rr.hi; i += blockDim.x) {
-    const uint2 it = ws.row_items[i];
-    const Ellipse el = make_ellipse(ws.records[3 * (int64_t)it.x], ws.records[3 * (int64_t)it.x + 1]);
-    const int ty = (int)(it.y % (uint32_t)ws.tiles_y);
-    const RowSpan sp = row_span(el, ty, ws.width, ws.height);
-    ws.row_span[i] = pack_span(sp);
-    const int64_t row0 = (int64_t)it.y * tiles_x;
-    for (int tx = sp.lo; tx <= sp.hi; ++tx) {
-      if (sp.gap && !tile_kept(el, tx, ty, ws.width, ws.height)) continue;
-      if (smem) atomicAdd(s_cnt + (row0 + tx - win0), 1u);
-      else atomicAdd(ws.tile_count + row0 + tx, 1u);
-    }
-  }
-  if (smem) {
-    __syncthreads();
-    // the window's counts also go to this CTA's slot, where k_rows_emit (same
-    // grid, same item ranges) picks them up instead of counting again
-    const bool keep = nwin <= 2 * tiles_x && blockIdx.x < kRowsGridMax;
-    uint32_t* mine = ws.cta_counts + (size_t)blockIdx.x * 2 * tiles_x;
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
-      if (s_cnt[i]) atomicAdd(ws.tile_count + win0 + i, s_cnt[i]);
-      if (keep) mine[i] = s_cnt[i];
-    }
-  }
-}
-
-// One key per kept (Gaussian, tile) pair, (depth key bits << 32) | Gaussian
-// index, written into its tile's bin through a per-CTA reserved range.
-__global__ void __launch_bounds__(256) k_rows_emit(Ws ws) {
-  __shared__ uint32_t s_cnt[kMaxWindow];
-  __shared__ uint32_t s_base[kMaxWindow];
-  if (ws.counters[kStatus] != 0) return;
-  const RowRange rr = row_range(ws);
-  if (rr.lo >= rr.hi) return;
-  const int tiles_x = ws.tiles_x;
-  const int64_t win0 = (int64_t)rr.b_first * tiles_x;
-  const int nwin = (rr.b_last - rr.b_first + 1) * tiles_x;
-  const bool smem = nwin <= kMaxWindow;
-  const int64_t n = ws.n;
-  if (smem && nwin <= 2 * tiles_x && blockIdx.x < kRowsGridMax) {
-    // this CTA's window counts, kept by k_rows_count for the same item range
-    const uint32_t* mine = ws.cta_counts + (size_t)blockIdx.x * 2 * tiles_x;
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x) s_cnt[i] = mine[i];
-  } else if (smem) {
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
-    for (uint32_t i = rr.lo + threadIdx.x; i < rr.hi; i += blockDim.x) {
-      const RowSpan sp = unpack_span(ws.row_span[i]);
-      if (sp.lo > sp.hi) continue;
-      const uint2 it = ws.row_items[i];
-      const int64_t row0 = (int64_t)it.y * tiles_x;
-      if (!sp.gap) {
-        for (int tx = sp.lo; tx <= sp.hi; ++tx) atomicAdd(s_cnt + (row0 + tx - win0), 1u);
-      } else {
-        const Ellipse el = make_ellipse(ws.records[3 * (int64_t)it.x], ws.records[3 * (int64_t)it.x + 1]);
-        const int ty = (int)(it.y % (uint32_t)ws.tiles_y);
-        for (int tx = sp.lo; tx <= sp.hi; ++tx)
-          if (tile_kept(el, tx, ty, ws.width, ws.height)) atomicAdd(s_cnt + (row0 + tx - win0), 1u);
-      }
-    }
-  }
-  if (smem) {
-    __syncthreads();
-    // reserve this CTA's range in each tile bin; s_cnt then counts down as the
-    // CTA fills it, so an index below zero (never expected: both loops take
-    // the same decisions) is caught without a global load per pair
-    for (int i = threadIdx.x; i < nwin; i += blockDim.x) {
-      if (s_cnt[i] == 0) continue;
-      s_base[i] = atomicAdd(ws.tile_cursor + win0 + i, s_cnt[i]);
-      if (s_base[i] + s_cnt[i] > ws.tile_start[win0 + i] + ws.tile_count[win0 + i]) {
-        atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
-        s_cnt[i] = 0;
-      }
-    }
-    __syncthreads();
-  }
-  for (uint32_t i = rr.lo + threadIdx.x; i < rr.hi; i += blockDim.x) {
-    const RowSpan sp = unpack_span(ws.row_span[i]);
-    if (sp.lo > sp.hi) continue;
-    const uint2 it = ws.row_items[i];
-    const int v = (int)(it.x / (uint64_t)n);
-    const uint32_t g = (uint32_t)(it.x - (uint64_t)v * n);
-    const float4 r1 = ws.records[3 * (int64_t)it.x + 1];
-    const unsigned long long key = ((unsigned long long)__float_as_uint(r1.z) << 32) | g;
-    const int64_t row0 = (int64_t)it.y * tiles_x;
-    const int ty = (int)(it.y % (uint32_t)ws.tiles_y);
-    Ellipse el;
-    if (sp.gap) el = make_ellipse(ws.records[3 * (int64_t)it.x], r1);
-    for (int tx = sp.lo; tx <= sp.hi; ++tx) {
-      if (sp.gap && !tile_kept(el, tx, ty, ws.width, ws.height)) continue;
-      const int64_t t = row0 + tx;
-      if (smem) {
-        const int local = (int)atomicSub(s_cnt + (t - win0), 1u) - 1;
-        if (local >= 0) ws.keys[s_base[t - win0] + local] = key;
-        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
-      } else {
-        const uint32_t pos = atomicAdd(ws.tile_cursor + t, 1u);
-        if (pos < ws.tile_start[t] + ws.tile_count[t]) ws.keys[pos] = key;
-        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
-      }
-    }
   }
 }
 
@@ -525,24 +342,6 @@ cudaError_t launch_project(const gs_map& map, const gs_camera* cams, const gs_co
     case 2: return bf ? launch_project_t<2, true>(map, cams, cfg, ws, st) : launch_project_t<2, false>(map, cams, cfg, ws, st);
     default: return bf ? launch_project_t<3, true>(map, cams, cfg, ws, st) : launch_project_t<3, false>(map, cams, cfg, ws, st);
   }
-}
-
-cudaError_t launch_rows(const Ws& ws, int phase, cudaStream_t st) {
-  const unsigned grid = (unsigned)(sm_count() * 8 < kRowsGridMax ? sm_count() * 8 : kRowsGridMax);
-  if (phase == 0) {
-    // large CTAs: each reserves its ranges once per bucket it touches, and the
-    // visible list mixes views, so fewer CTAs mean fewer reservations
-    trace_begin(kKScatterRows, st);
-    k_scatter_rows<<<(unsigned)sm_count() * 2, kScatterThreads, 0, st>>>(ws);
-  } else if (phase == 1) {
-    trace_begin(kKRowsCount, st);
-    k_rows_count<<<grid, 256, 0, st>>>(ws);
-  } else {
-    trace_begin(kKRowsEmit, st);
-    k_rows_emit<<<grid, 256, 0, st>>>(ws);
-  }
-  trace_end(st);
-  return cudaGetLastError();
 }
 
 }  // namespace gsb

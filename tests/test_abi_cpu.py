@@ -42,10 +42,7 @@ def test_workspace_size_and_layout(native):
     size = native.gs_workspace_size(1_000_000, f, 1 << 24)
     L = native.gs_workspace_layout(1_000_000, f, 1 << 24)
     assert size == L.total and size > 0
-    offs = [L.counters, L.records, L.rects, L.adjoints, L.visible, L.gauss_list, L.tile_count, L.tile_start,
-            L.tile_cursor,
-            L.long_tiles, L.bucket_count, L.bucket_start, L.bucket_cursor, L.row_items, L.row_span, L.cta_counts, L.keys,
-            L.keys_alt, L.sorted_ids, L.view_stats]
+    offs = [getattr(L, k) for k, _ in native.gs_layout._fields_ if k != "total"]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
     assert L.rects - L.records == 4 * 1_000_000 * 48
     # invalid geometry

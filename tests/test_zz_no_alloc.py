@@ -86,16 +86,24 @@ def test_noalloc_pair_overflow_reports_capacity_and_background():
     from paper_2507_04004_b300 import _native as N
     from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor, make_config
     rng = np.random.default_rng(synth.SEED_BASE + 77)
-    # 200k large Gaussians at 256x256: 23 MB of per-Gaussian workspace leave
-    # room for about 1.4M pairs; the scene has several million
+    # 200k large Gaussians at 256x256: the per-Gaussian workspace leaves room
+    # for about 3M pairs; the scene has several million more
     g = synth.random_map(rng, 200_000, (-4, -4, 2), (4, 4, 12), 0, log_scale_mean=-0.5, log_scale_std=0.2)
     W = H = 256
     cam = synth.camera(np.eye(3), np.zeros(3), 100.0, 100.0, W / 2, H / 2, W, H)
     gm = GaussianMap.from_host(g)
     ct = cameras_tensor([cam])
     cfg = make_config()
-    L = N.gs_workspace_layout(g.n, N.gs_frame(1, W, H), 1)
-    cap = (N.GS_NOALLOC_SCRATCH_BYTES - L.total) // 32
+    # the pair capacity the call derives: the largest whose workspace layout fits the array
+    frame = N.gs_frame(1, W, H)
+    lo, hi = 1, N.GS_NOALLOC_SCRATCH_BYTES
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if N.gs_workspace_size(g.n, frame, mid) <= N.GS_NOALLOC_SCRATCH_BYTES:
+            lo = mid
+        else:
+            hi = mid - 1
+    cap = lo
     code, status, (rgb, depth, opac), tf, nc = _noalloc(N, gm, ct, 1, W, H, cfg)
     assert code == N.GS_OK
     assert status == N.GS_ERR_CAPACITY, status
