@@ -189,6 +189,7 @@ constexpr int kSortTile = kRadixThreads * kSortItems;    // entries per tile (kR
 static_assert(kSortTile == kRadixTileEntries, "tile size of the sort");
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValueMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 16;
+constexpr int kLookBack = 16;  // earlier tiles' status words read per round trip
 
 __device__ __forceinline__ uint32_t* radix_counts(const Ws& ws) { return ws.radix_status; }  // [6][256]
 __device__ __forceinline__ uint32_t* radix_tiles(const Ws& ws, int pass) {
@@ -280,19 +281,27 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(Ws ws, int pass, c
       st[(int64_t)t * 256 + dd] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
       uint32_t excl = 0;
       if (t > 0) {
-        for (int64_t tt = (int64_t)t - 1; tt >= 0; --tt) {
-          uint32_t w = st[tt * 256 + dd];
-          for (int spin = 0; (w >> 30) == 0; ++spin) {
-            if (spin >= kSpinLimit) {
-              atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_TIMEOUT);
-              w = kFlagPrefix;
-              break;
+        // kLookBack earlier tiles' words are loaded per round trip, nearest first
+        bool found = false;
+        for (int64_t tt = (int64_t)t - 1; tt >= 0 && !found; tt -= kLookBack) {
+          uint32_t w[kLookBack];
+#pragma unroll
+          for (int q = 0; q < kLookBack; ++q) w[q] = tt - q >= 0 ? (uint32_t)st[(tt - q) * 256 + dd] : (uint32_t)kFlagPrefix;
+#pragma unroll
+          for (int q = 0; q < kLookBack; ++q) {
+            if (found) break;
+            for (int spin = 0; (w[q] >> 30) == 0; ++spin) {  // that tile has not published yet
+              if (spin >= kSpinLimit) {
+                atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_TIMEOUT);
+                w[q] = kFlagPrefix;
+                break;
+              }
+              __nanosleep(64);
+              w[q] = st[(tt - q) * 256 + dd];
             }
-            __nanosleep(64);
-            w = st[tt * 256 + dd];
+            excl += w[q] & kValueMask;
+            found = (w[q] >> 30) == 2u;
           }
-          excl += w & kValueMask;
-          if ((w >> 30) == 2u) break;
         }
         st[(int64_t)t * 256 + dd] = kFlagPrefix | (excl + run);
       }
@@ -464,15 +473,18 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
       mask[t] = 0;
     }
     __syncwarp();
+    uint32_t ne = 0;  // next round's entry and box, loaded ahead
+    uint2 nr = make_uint2(1u, 0u);
+    if (i0 + lane < i1) {
+      ne = ws.visible[i0 + lane];
+      nr = ws.rects[ne];
+    }
     for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
-      const uint32_t i = r0 + lane;
-      uint32_t e = 0;
-      int y0 = 0, y1 = -1;
-      if (i < i1) {
-        e = ws.visible[i];
-        const uint2 r = ws.rects[e];
-        y0 = (int)(r.x >> 16);
-        y1 = (int)(r.y >> 16);
+      const uint32_t e = ne;
+      const int y0 = (int)(nr.x >> 16), y1 = r0 + lane < i1 ? (int)(nr.y >> 16) : -1;
+      if (r0 + 32 + lane < i1) {
+        ne = ws.visible[r0 + 32 + lane];
+        nr = ws.rects[ne];
       }
       for (int y = y0; y <= y1; ++y) atomicOr(mask + y, 1u << lane);
       __syncwarp();
@@ -511,9 +523,21 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_count(Ws ws) {
     const uint32_t i1 = min(i0 + (uint32_t)kRowUnit, bs + ws.bucket_count[b]);
     for (int t = lane; t <= nx; t += 32) cnt[t] = 0;
     __syncwarp();
-    for (uint32_t i = i0 + lane; i < i1; i += 32) {
+    // the next item's record is loaded while this one's chords are evaluated
+    uint32_t i = i0 + lane;
+    float4 n0 = make_float4(0.f, 0.f, 1.f, 0.f), n1 = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (i < i1) {
       const int64_t e = ws.row_items[i];
-      const Ellipse el = make_ellipse(ws.records[3 * e], ws.records[3 * e + 1]);
+      n0 = ws.records[3 * e];
+      n1 = ws.records[3 * e + 1];
+    }
+    for (; i < i1; i += 32) {
+      const Ellipse el = make_ellipse(n0, n1);
+      if (i + 32 < i1) {
+        const int64_t e = ws.row_items[i + 32];
+        n0 = ws.records[3 * e];
+        n1 = ws.records[3 * e + 1];
+      }
       const RowSpan sp = row_span(el, ty, ws.width, ws.height);
       ws.row_span[i] = pack_span(sp);
       if (sp.lo > sp.hi) continue;
@@ -581,17 +605,21 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
       mask[x] = 0;
     }
     __syncwarp();
+    uint32_t nspan = 0xfffu, nitem = 0;  // next round's span and item, loaded ahead
+    if (i0 + lane < i1) {
+      nspan = ws.row_span[i0 + lane];
+      nitem = ws.row_items[i0 + lane];
+    }
     for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
-      const uint32_t i = r0 + lane;
-      int lo = 0, hi = -1;
-      bool gap = false;
-      int64_t e = 0;
-      if (i < i1) {
-        const RowSpan sp = unpack_span(ws.row_span[i]);
-        e = ws.row_items[i];
-        lo = sp.lo;
-        hi = sp.hi;
-        gap = sp.gap;
+      const RowSpan sp = unpack_span(nspan);
+      const int64_t e = nitem;
+      const int lo = sp.lo, hi = sp.hi;
+      const bool gap = sp.gap;
+      if (r0 + 32 + lane < i1) {
+        nspan = ws.row_span[r0 + 32 + lane];
+        nitem = ws.row_items[r0 + 32 + lane];
+      } else {
+        nspan = 0xfffu;
       }
       // a span with a gap (very thin tilted ellipses): its tiles are tested exactly
       Ellipse el;

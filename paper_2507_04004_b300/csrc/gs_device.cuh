@@ -305,17 +305,24 @@ __device__ __forceinline__ float2 col_p2x2(const ColTerms& c, float2 py) {
 // inside it; the union of the chords' tile ranges over the 16 rows of a tile
 // row is the kept set of that tile row.
 
+// Per-ellipse constants of the chord computation: with dy = y + 0.5 - my,
+//   disc = a q_thr - det dy^2,  det = a c - b^2,
+//   chord centre - 0.5 = (mx - 0.5) - (b / a) dy,  half width = sqrt(disc) / a.
 struct Ellipse {
-  float mx, my, a, b, c, q_thr, inv_a, det_c;
+  float my, aq, det, inv_a, b_a, mxm;
 };
 
 __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
   Ellipse e;
-  e.mx = r0.x; e.my = r0.y; e.a = r0.z; e.b = r0.w; e.c = r1.x; e.q_thr = r1.w;
   // explicit roundings and single-instruction approximations (no branches):
   // every kernel that evaluates a chord takes bit-identical decisions
-  e.inv_a = __fdividef(1.f, e.a);
-  e.det_c = __fsub_rn(__fmul_rn(e.a, e.c), __fmul_rn(e.b, e.b));
+  const float a = r0.z, b = r0.w, c = r1.x;
+  e.my = r0.y;
+  e.inv_a = __fdividef(1.f, a);
+  e.det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+  e.aq = __fmul_rn(a, r1.w);
+  e.b_a = __fmul_rn(b, e.inv_a);
+  e.mxm = __fsub_rn(r0.x, 0.5f);
   return e;
 }
 
@@ -324,13 +331,13 @@ __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
 // lanes of a warp stay converged across the 16 rows of a tile row.
 __device__ __forceinline__ bool row_tiles(const Ellipse& e, int y, int width, int* tl, int* tr) {
   const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), e.my);
-  const float disc = __fsub_rn(__fmul_rn(e.a, e.q_thr), __fmul_rn(__fmul_rn(e.det_c, dy), dy));
+  const float disc = __fmaf_rn(-__fmul_rn(e.det, dy), dy, e.aq);
   const float dpos = fmaxf(disc, 1e-30f);
   const float half = __fmul_rn(__fmul_rn(dpos, rsqrtf(dpos)), e.inv_a);  // sqrt(disc) / a
-  const float xc = __fsub_rn(e.mx, __fmul_rn(__fmul_rn(e.b, dy), e.inv_a));
+  const float cm = __fmaf_rn(-e.b_a, dy, e.mxm);                         // chord centre - 0.5
   const float wm1 = (float)(width - 1);
-  const float xl = ceilf(__fsub_rn(__fsub_rn(xc, half), 0.5f));
-  const float xr = floorf(__fsub_rn(__fadd_rn(xc, half), 0.5f));
+  const float xl = ceilf(__fsub_rn(cm, half));
+  const float xr = floorf(__fadd_rn(cm, half));
   const bool ok = (disc >= 0.f) & (xl <= xr) & (xr >= 0.f) & (xl <= wm1);
   *tl = (int)fminf(fmaxf(xl, 0.f), wm1) >> 4;
   *tr = (int)fminf(fmaxf(xr, 0.f), wm1) >> 4;
