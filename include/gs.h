@@ -369,6 +369,32 @@ gs_status gs_expand_init(const float* points_dev, const float* rgb_dev, int64_t 
                          const uint32_t* count_dev, const gs_camera* cam_dev, int64_t first, const gs_param_set* dst,
                          int64_t n_dst, int32_t sh_degree, float init_opacity, gs_stream_t stream);
 
+/* Spatial storage order of the map (measurement-driven; no counterpart in
+ * the paper, which leaves the storage order open).  A view sees a fraction
+ * of the Gaussians; ordered along a space-filling curve of their means, the
+ * Gaussians a view or a tile sees are contiguous runs of the SoA arrays, so
+ * the projection, the projection backward and the sparse Adam step
+ * (Sec. "Additional Strategies" (a)) read and write whole sectors.
+ *   gs_morton_scratch_bytes: bytes of the scratch buffer for n Gaussians
+ *     (0 if n < 1 or n >= 2^30).
+ *   gs_morton_order: perm_out [n] (device uint32) = the Gaussian indices
+ *     sorted by the 30-bit Morton code of mean [3][n] (device FP32): per
+ *     axis q = floor((m - lo) 1024 / (hi - lo)) clamped to [0, 1023] over the
+ *     bounding box of the finite means (0 for a flat axis or a non-finite
+ *     mean), x, y, z bits interleaved with x the most significant; equal
+ *     codes in index order.  scratch: caller-owned device buffer of
+ *     gs_morton_scratch_bytes(n) bytes, 256-byte aligned, overwritten.
+ *   gs_permute_rows: dst[r][i] = src[r][perm[i]] for rows SoA rows of n
+ *     elements of elem_bytes (2 or 4) bytes, e.g. each parameter array of a
+ *     gs_param_set and the matching Adam moments; src and dst are distinct
+ *     device buffers; an out-of-range perm[i] leaves dst[.][i] as it was.
+ * The library keeps the caller's indexing everywhere: after permuting the
+ * arrays, gradients, tile lists and outputs refer to the new order. */
+size_t gs_morton_scratch_bytes(int64_t n);
+gs_status gs_morton_order(const float* mean_dev, int64_t n, void* scratch, uint32_t* perm_out, gs_stream_t stream);
+gs_status gs_permute_rows(const void* src_dev, void* dst_dev, int64_t rows, int64_t n, int32_t elem_bytes,
+                          const uint32_t* perm_dev, gs_stream_t stream);
+
 /* Forward render that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc - code running
  * inside a host framework that owns all device memory (an inference-engine

@@ -18,7 +18,8 @@ EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_pr
             "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
             "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
             "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
-            "gs_expand_select", "gs_expand_init", "gs_trace_start",
+            "gs_expand_select", "gs_expand_init", "gs_morton_scratch_bytes", "gs_morton_order", "gs_permute_rows",
+            "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
 
@@ -118,6 +119,10 @@ def lib():
         L.gs_sparse_adam.argtypes = [C.POINTER(gs_workspace), I32] + [C.POINTER(gs_param_set)] * 4 + [
             P, C.POINTER(gs_adam_map_config), P]
         L.gs_adam_pose.argtypes = [P, P, P, P, P, I32, C.POINTER(gs_adam_config), P, P, P, P]
+        L.gs_morton_scratch_bytes.argtypes = [I64]
+        L.gs_morton_scratch_bytes.restype = C.c_size_t
+        L.gs_morton_order.argtypes = [P, I64, P, P, P]
+        L.gs_permute_rows.argtypes = [P, P, I64, I64, I32, P, P]
         L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
         L.gs_trace_start.restype = I32
         L.gs_trace_stop.argtypes = []
@@ -130,7 +135,8 @@ def lib():
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_blend_counts", "gs_render_bwd",
                      "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose",
-                     "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes"):
+                     "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes",
+                     "gs_morton_order", "gs_permute_rows"):
             getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -284,6 +290,20 @@ def gs_expand_init(points, rgb, n_points: int, idx, count, cam, first: int, dst:
     check("gs_expand_init", lib().gs_expand_init(_ptr(points), _ptr(rgb), int(n_points), _ptr(idx), _ptr(count),
                                                  _ptr(cam), int(first), C.byref(dst), int(n_dst), int(sh_degree),
                                                  float(init_opacity), C.c_void_p(stream)))
+
+
+def gs_morton_scratch_bytes(n: int) -> int:
+    return int(lib().gs_morton_scratch_bytes(int(n)))
+
+
+def gs_morton_order(mean, n: int, scratch, perm, stream: int) -> None:
+    check("gs_morton_order", lib().gs_morton_order(_ptr(mean), int(n), _ptr(scratch), _ptr(perm),
+                                                   C.c_void_p(stream)))
+
+
+def gs_permute_rows(src, dst, rows: int, n: int, elem_bytes: int, perm, stream: int) -> None:
+    check("gs_permute_rows", lib().gs_permute_rows(_ptr(src), _ptr(dst), int(rows), int(n), int(elem_bytes),
+                                                   _ptr(perm), C.c_void_p(stream)))
 
 
 def gs_render_fwd_noalloc(m: gs_map, cams, frame: gs_frame, cfg: gs_config, rgb, depth, opac, t_final, n_contrib,

@@ -25,23 +25,13 @@
 // lower lanes that cover the same bin (per-warp lane masks in shared memory).
 // Pairs and row items thus keep their input order, and no bin is sorted.
 #include "gs_internal.h"
+#include "radix.cuh"
 
 namespace gsb {
 
 constexpr int kScanThreads = 1024;
-constexpr int kRadixThreads = 256;
 constexpr int kUnitWarps = 8;  // warps (units in flight) per CTA of the unit kernels
 
-__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
 
 // Exclusive scan of count(i), i < n, by one CTA of kScanThreads: start[i] =
 // sum of counts before i; returns the 64-bit total (to every thread).  Each
@@ -151,187 +141,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
 }
 
 // ---------------------------------------------------------------- entry sort
-// Digit of an entry in pass p: bytes of the depth key for p < 4, then the
-// bytes of the view (entry / N).  LSD order makes the last pass the most
-// significant: (view, depth key).
-__device__ __forceinline__ uint32_t radix_digit(uint32_t key, uint32_t val, int pass, uint32_t n_per_view) {
-  if (pass < 4) return (key >> (8 * pass)) & 255u;
-  const uint32_t v = val / n_per_view;
-  return (pass == 4 ? v : v >> 8) & 255u;
-}
-
-
-// Lanes of the warp whose (active) digit equals this lane's: the AND of the
-// eight ballots of the digit's bits, each taken as is or complemented.
-__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool act) {
-  unsigned peers = __ballot_sync(kFull, act);
-#pragma unroll
-  for (int bit = 0; bit < 8; ++bit) {
-    const bool on = (d >> bit) & 1u;
-    const unsigned m = __ballot_sync(kFull, on);
-    peers &= on ? m : ~m;
+// Digit of a visible entry (key = depth key bits, val = entry v*N + g) in
+// pass p: bytes of the depth key for p < 4, then the bytes of the view.  LSD
+// order makes the last pass the most significant: (view, depth key).
+struct DepthDigit {
+  uint32_t n_per_view;
+  __device__ __forceinline__ uint32_t operator()(uint32_t key, uint32_t val, int pass) const {
+    if (pass < 4) return (key >> (8 * pass)) & 255u;
+    const uint32_t v = val / n_per_view;
+    return (pass == 4 ? v : v >> 8) & 255u;
   }
-  return peers;
-}
+};
 
-// The sort is "onesweep": the digit counts of every pass come from one read
-// of the entries (the counts do not depend on the order), and each pass is
-// one kernel whose CTAs take tiles of kSortTile consecutive entries by
-// ticket, rank them stably, and find where their run of each digit starts by
-// looking back over the earlier tiles' published counts (decoupled
-// look-back).  A tile's status word per digit: bits 30-31 = 1 (its own count
-// in bits 0-29) or 2 (the count of all tiles up to and including it); the
-// workspace allows fewer than 2^30 (view, Gaussian) entries.  Waits on an
-// earlier tile are bounded: past kSpinLimit polls the status word of the
-// workspace becomes GS_ERR_TIMEOUT and the pass writes only in-range slots.
-constexpr int kSortItems = 8;                            // entries per thread
-constexpr int kSortTile = kRadixThreads * kSortItems;    // entries per tile (kRadixTileEntries)
-static_assert(kSortTile == kRadixTileEntries, "tile size of the sort");
-constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kValueMask = (1u << 30) - 1u;
-constexpr int kSpinLimit = 1 << 16;
-constexpr int kLookBack = 16;  // earlier tiles' status words read per round trip
 
-__device__ __forceinline__ uint32_t* radix_counts(const Ws& ws) { return ws.radix_status; }  // [6][256]
-__device__ __forceinline__ uint32_t* radix_tiles(const Ws& ws, int pass) {
-  return ws.radix_status + 6 * 256 + (int64_t)pass * ws.radix_tiles_max * 256;
-}
-
-// Digit counts of every pass over all visible entries; clears the tile status
-// words the passes will use.  The counts were zeroed by k_scan_buckets.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_counts(Ws ws, int passes) {
-  __shared__ uint32_t h[6][256];
-  if (ws.counters[kStatus] != 0) return;
-  const uint64_t n = ws.counters[kVisibleCount];
-  const uint64_t ntiles = (n + kSortTile - 1) / kSortTile;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
-  for (int p = 0; p < passes; ++p) {
-    uint32_t* st = radix_tiles(ws, p);
-    for (uint64_t i = tid; i < ntiles * 256; i += stride) st[i] = 0;
-  }
-  for (int i = threadIdx.x; i < 6 * 256; i += kRadixThreads) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t N = (uint32_t)ws.n;
-  for (uint64_t i = tid; i < n; i += stride) {
-    const uint32_t k = ws.vis_key[i], v = ws.visible[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][radix_digit(k, v, p, N)], 1u);
-  }
-  __syncthreads();
-  uint32_t* g = radix_counts(ws);
-  for (int i = threadIdx.x; i < passes * 256; i += kRadixThreads) {
-    const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(g + i, c);
-  }
-}
-
-// One LSD pass: stable scatter of the entries by the pass's digit.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_pass(Ws ws, int pass, const uint32_t* __restrict__ key_in,
-                                                              const uint32_t* __restrict__ val_in,
-                                                              uint32_t* __restrict__ key_out,
-                                                              uint32_t* __restrict__ val_out) {
-  constexpr int NW = kRadixThreads / 32;
-  __shared__ uint32_t s_wcnt[NW][256];  // per warp: count of each digit, then its first slot in the tile
-  __shared__ uint32_t s_base[256];      // first output slot of each digit's run of this tile
-  __shared__ uint32_t s_ticket;
-  if (ws.counters[kStatus] != 0) return;
-  const uint64_t n = ws.counters[kVisibleCount];
-  const uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt(lane);
-  const uint32_t N = (uint32_t)ws.n;
-  uint32_t* status = radix_tiles(ws, pass);
-  const uint32_t* counts = radix_counts(ws) + pass * 256;
-  for (;;) {
-    for (int i = threadIdx.x; i < NW * 256; i += kRadixThreads) (&s_wcnt[0][0])[i] = 0;
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ws.counters + kRadixTicket + pass, 1u);
-    __syncthreads();
-    const uint32_t t = s_ticket;
-    if (t >= ntiles) return;
-    // this warp's 256 entries, taken lane-minor: entry order = (j, lane) order
-    const uint64_t base = (uint64_t)t * kSortTile + (uint64_t)warp * 32 * kSortItems;
-    uint32_t k[kSortItems], v[kSortItems], d[kSortItems], r[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const uint64_t i = base + 32 * j + lane;
-      k[j] = i < n ? key_in[i] : 0u;
-      v[j] = i < n ? val_in[i] : 0u;
-    }
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const bool act = base + 32 * j + lane < n;
-      d[j] = radix_digit(k[j], v[j], pass, N);
-      const unsigned peers = digit_peers(d[j], act);
-      const uint32_t prev = s_wcnt[warp][d[j]];
-      r[j] = prev + __popc(peers & lt);
-      __syncwarp();
-      if (act && (peers & lt) == 0) s_wcnt[warp][d[j]] = prev + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    if (threadIdx.x < 256) {
-      const int dd = threadIdx.x;
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = s_wcnt[w][dd];
-        s_wcnt[w][dd] = run;
-        run += c;
-      }
-      // publish this tile's count, then look back for the runs of earlier tiles
-      volatile uint32_t* st = status;
-      st[(int64_t)t * 256 + dd] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
-      uint32_t excl = 0;
-      if (t > 0) {
-        // kLookBack earlier tiles' words are loaded per round trip, nearest first
-        bool found = false;
-        for (int64_t tt = (int64_t)t - 1; tt >= 0 && !found; tt -= kLookBack) {
-          uint32_t w[kLookBack];
-#pragma unroll
-          for (int q = 0; q < kLookBack; ++q) w[q] = tt - q >= 0 ? (uint32_t)st[(tt - q) * 256 + dd] : (uint32_t)kFlagPrefix;
-#pragma unroll
-          for (int q = 0; q < kLookBack; ++q) {
-            if (found) break;
-            for (int spin = 0; (w[q] >> 30) == 0; ++spin) {  // that tile has not published yet
-              if (spin >= kSpinLimit) {
-                atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_TIMEOUT);
-                w[q] = kFlagPrefix;
-                break;
-              }
-              __nanosleep(64);
-              w[q] = st[(tt - q) * 256 + dd];
-            }
-            excl += w[q] & kValueMask;
-            found = (w[q] >> 30) == 2u;
-          }
-        }
-        st[(int64_t)t * 256 + dd] = kFlagPrefix | (excl + run);
-      }
-      // first slot of the digit: all entries of lower digits, then earlier tiles
-      s_base[dd] = excl;
-    }
-    __syncthreads();
-    // exclusive scan of the pass's digit counts (one warp), added to s_base
-    if (warp == 0) {
-      uint32_t c8[8], tot = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { c8[q] = counts[lane * 8 + q]; tot += c8[q]; }
-      uint32_t run = warp_incl_scan(tot, lane) - tot;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] += run; run += c8[q]; }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const uint64_t i = base + 32 * j + lane;
-      if (i >= n) continue;
-      const uint64_t pos = (uint64_t)s_base[d[j]] + s_wcnt[warp][d[j]] + r[j];
-      if (pos < n) {
-        key_out[pos] = k[j];
-        val_out[pos] = v[j];
-      }
-    }
-    __syncthreads();  // s_wcnt and s_base are reused by the next tile
-  }
-}
 
 // Runs of equal (view, depth key) put in Gaussian-index order, the sorted
 // entries written to ws.visible; first sorted entry of every view.
@@ -658,8 +480,17 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   // 1. entries sorted by (view, depth key), then index inside equal keys
   const int64_t E = (int64_t)ws.views * ws.n;
   const int passes = 4 + (ws.views > 1 ? (ws.views > 256 ? 2 : 1) : 0);
+  // the sort's host view of its scratch (device pointers and the entry count's slot)
+  RadixScratch rs;
+  rs.n = ws.counters + kVisibleCount;
+  rs.status = ws.counters + kStatus;
+  rs.counts = ws.radix_status;
+  rs.tiles = ws.radix_status + 6 * 256;
+  rs.tickets = ws.counters + kRadixTicket;
+  rs.tiles_max = ws.radix_tiles_max;
+  const DepthDigit dg{(uint32_t)ws.n};
   trace_begin(kKDepthHist, st);
-  k_radix_counts<<<sm_count() * 4, kRadixThreads, 0, st>>>(ws, passes);
+  k_radix_counts<<<sm_count() * 4, kRadixThreads, 0, st>>>(rs, dg, passes, ws.vis_key, ws.visible);
   if ((err = done()) != cudaSuccess) return err;
   const uint32_t* key = ws.vis_key;
   const uint32_t* val = ws.visible;
@@ -667,7 +498,7 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
     uint32_t* ko = ws.sort_key + (p & 1) * E;
     uint32_t* vo = ws.sort_val + (p & 1) * E;
     trace_begin(kKDepthScatter, st);
-    k_radix_pass<<<sm_count() * 4, kRadixThreads, 0, st>>>(ws, p, key, val, ko, vo);
+    k_radix_pass<<<sm_count() * 4, kRadixThreads, 0, st>>>(rs, dg, p, key, val, ko, vo);
     if ((err = done()) != cudaSuccess) return err;
     key = ko;
     val = vo;

@@ -97,17 +97,11 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
       ls[0] = map.log_scale[g]; ls[1] = map.log_scale[n + g]; ls[2] = map.log_scale[2 * n + g];
       logit = map.logit_opacity[g];
     }
-    if (!BF16) {
-      cp_async_wait_all();  // the previous Gaussian's copies (long done) before the column is refilled
-      if (in_range) {
-        const float* dc = static_cast<const float*>(map.sh_dc);
-        const float* rest = static_cast<const float*>(map.sh_rest);
-#pragma unroll
-        for (int q = 0; q < 3 * K; ++q)
-          cp_async4(s_shc + q * blockDim.x + threadIdx.x, q < 3 ? dc + q * n + g : rest + (int64_t)(q - 3) * n + g);
-      }
-      cp_async_commit();
-    }
+    // FP32 SH: the copy into this thread's shared-memory column is issued once
+    // the cheap candidate test below finds a view the Gaussian may reach, so
+    // the coefficients of Gaussians no view sees are never read
+    bool sh_pending = !BF16 && in_range;
+    if (!BF16) cp_async_wait_all();  // the previous Gaussian's copies (long done) before the column is refilled
     const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
     const bool g_ok = in_range && qq > 0.f;
     const float qi = g_ok ? rsqrtf(qq) : 1.f;
@@ -163,6 +157,15 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
         }
         if (c) cand |= 1u << j;
         else if (in_range) ws.rects[(int64_t)v * n + g] = empty_rect();
+      }
+      if (!BF16 && sh_pending && cand != 0) {
+        sh_pending = false;
+        const float* dc = static_cast<const float*>(map.sh_dc);
+        const float* rest = static_cast<const float*>(map.sh_rest);
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q)
+          cp_async4(s_shc + q * blockDim.x + threadIdx.x, q < 3 ? dc + q * n + g : rest + (int64_t)(q - 3) * n + g);
+        cp_async_commit();
       }
       // warp-uniform loop (the list append below takes a ballot of all lanes)
       while (__any_sync(kFull, cand != 0)) {

@@ -61,6 +61,17 @@ class GaussianMap:
         return cls(f(d["mean"]), f(d["log_scale"]), f(d["quat"]), f(d["logit_opacity"]),
                    f(d["sh_dc"]).to(sd).contiguous(), f(d["sh_rest"]).to(sd).contiguous(), int(d["sh_degree"]))
 
+    def permuted(self, perm: torch.Tensor) -> "GaussianMap":
+        """The map with Gaussian i of the result = Gaussian perm[i] of this one."""
+        p = lambda t: permute_rows(t, perm)
+        return GaussianMap(p(self.mean), p(self.log_scale), p(self.quat), p(self.logit_opacity), p(self.sh_dc),
+                           p(self.sh_rest), self.sh_degree)
+
+    def spatially_ordered(self) -> tuple["GaussianMap", torch.Tensor]:
+        """(the map in Morton order of its means, the permutation applied)."""
+        perm = morton_order(self)
+        return self.permuted(perm), perm
+
     def struct(self) -> N.gs_map:
         for t in (self.mean, self.log_scale, self.quat, self.logit_opacity, self.sh_dc, self.sh_rest):
             if not t.is_cuda or not t.is_contiguous():
@@ -69,6 +80,29 @@ class GaussianMap:
         return N.gs_map(self.n, self.sh_degree, 1 if self.sh_bf16 else 0, self.mean.data_ptr(),
                         self.log_scale.data_ptr(), self.quat.data_ptr(), self.logit_opacity.data_ptr(),
                         self.sh_dc.data_ptr(), rest)
+
+
+def morton_order(gmap: "GaussianMap") -> torch.Tensor:
+    """Permutation [N] (int32, device) sorting the Gaussians along the Morton
+    curve of their means (gs_morton_order)."""
+    dev = gmap.mean.device
+    nbytes = N.gs_morton_scratch_bytes(gmap.n)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    off = (-buf.data_ptr()) % 256
+    perm = torch.empty(gmap.n, dtype=torch.int32, device=dev)
+    N.gs_morton_order(gmap.mean, gmap.n, buf[off:off + nbytes], perm, torch.cuda.current_stream(dev).cuda_stream)
+    return perm
+
+
+def permute_rows(t: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
+    """t[..., perm] for an SoA array whose last axis is the Gaussian index
+    (gs_permute_rows), as a new tensor."""
+    n = int(t.shape[-1])
+    out = torch.empty_like(t)
+    if t.numel():
+        N.gs_permute_rows(t, out, t.numel() // n, n, t.element_size(), perm,
+                          torch.cuda.current_stream(t.device).cuda_stream)
+    return out
 
 
 def cameras_tensor(cams, device="cuda") -> torch.Tensor:
@@ -330,6 +364,12 @@ class SparseAdam:
         self.step_count = torch.zeros(1, dtype=torch.int32, device=gmap.mean.device)
         self.cfg = N.gs_adam_map_config(lr_mean * spatial_scale, lr_log_scale, lr_quat, lr_logit_opacity, lr_sh_dc,
                                         lr_sh_rest, betas[0], betas[1], eps)
+
+    def permute(self, perm: torch.Tensor) -> None:
+        """Reorder the moments with the map (Gaussian i <- Gaussian perm[i])."""
+        for st in (self.m, self.v):
+            for k in ("mean", "log_scale", "quat", "logit_opacity", "sh_dc", "sh_rest"):
+                setattr(st, k, permute_rows(getattr(st, k), perm))
 
     def step(self, gmap: GaussianMap, grads: Grads, rast: Rasterizer) -> None:
         N.gs_sparse_adam(rast.ws, gmap.sh_degree, N.param_set(gmap), N.param_set(grads), N.param_set(self.m),
