@@ -27,8 +27,8 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
   const int64_t tx = (f->width + 15) / 16, ty = (f->height + 15) / 16;
   const int64_t B = V * ty;
-  const int64_t units_e = (E + kEntryUnit - 1) / kEntryUnit + V;
-  const int64_t units_r = (cap + kRowUnit - 1) / kRowUnit + B;
+  const int64_t units_e = (E + kEntryUnit - 1) / kEntryUnit + V * (unit_ramp(kEntryUnit) + 1);
+  const int64_t units_r = (cap + kRowUnit - 1) / kRowUnit + B * (unit_ramp(kRowUnit) + 1);
   L->counters = take(16 * sizeof(uint32_t));
   L->records = take((size_t)E * 3 * sizeof(float4));
   L->rects = take((size_t)E * sizeof(uint2));
@@ -95,8 +95,8 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.tiles_x = (ws.width + 15) / 16;
   ws.tiles_y = (ws.height + 15) / 16;
   ws.tiles_per_view = ws.tiles_x * ws.tiles_y;
-  ws.units_e_max = ((int64_t)ws.views * ws.n + kEntryUnit - 1) / kEntryUnit + ws.views;
-  ws.units_r_max = (ws.cap + kRowUnit - 1) / kRowUnit + (int64_t)ws.views * ws.tiles_y;
+  ws.units_e_max = ((int64_t)ws.views * ws.n + kEntryUnit - 1) / kEntryUnit + ws.views * (unit_ramp(kEntryUnit) + 1);
+  ws.units_r_max = (ws.cap + kRowUnit - 1) / kRowUnit + (int64_t)ws.views * ws.tiles_y * (unit_ramp(kRowUnit) + 1);
   ws.radix_tiles_max = ((int64_t)ws.views * ws.n + kRadixTileEntries - 1) / kRadixTileEntries;
   return ws;
 }

@@ -82,14 +82,14 @@ __device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
   return total;
 }
 
-// Units of n_seg segments of cnt(s) items, unit_len items per unit: first[s]
+// Units of n_seg segments of cnt(s) items (unit_count / unit_start): first[s]
 // = first unit of segment s (first[n_seg] = total), seg[u] = segment of unit
 // u, *total_out = total.  One CTA; more than max_units units (not expected:
 // the workspace is sized for the capacities checked before) flag an error.
 template <typename F>
-__device__ void build_units(F cnt, int64_t n_seg, uint32_t unit_len, int64_t max_units, uint32_t* first, uint32_t* seg,
+__device__ void build_units(F cnt, int64_t n_seg, int unit_cap, int64_t max_units, uint32_t* first, uint32_t* seg,
                             uint32_t* total_out, uint32_t* status) {
-  auto nu = [&](int64_t s) { return (uint32_t)((cnt(s) + unit_len - 1) / unit_len); };
+  auto nu = [&](int64_t s) { return unit_count(cnt(s), unit_cap); };
   const unsigned long long total = block_scan(nu, first, n_seg);
   if (threadIdx.x == 0) {
     first[n_seg] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
@@ -246,8 +246,9 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_entry_rows(Ws ws) {
   const uint32_t nu = ws.counters[kEntryUnits];
   for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
     const uint32_t v = ws.unit_seg_e[u];
-    const uint32_t i0 = ws.view_start[v] + (u - ws.unit_first_e[v]) * kEntryUnit;
-    const uint32_t i1 = min(i0 + (uint32_t)kEntryUnit, ws.view_start[v + 1]);
+    const uint32_t k = u - ws.unit_first_e[v];
+    const uint32_t i0 = ws.view_start[v] + (uint32_t)unit_start(k, kEntryUnit);
+    const uint32_t i1 = min(ws.view_start[v] + (uint32_t)unit_start(k + 1, kEntryUnit), ws.view_start[v + 1]);
     for (int t = lane; t <= ny; t += 32) cnt[t] = 0;
     __syncwarp();
     for (uint32_t i = i0 + lane; i < i1; i += 32) {
@@ -267,17 +268,57 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_entry_rows(Ws ws) {
   }
 }
 
-// Stable ranking inside a warp: the 32 lanes' inputs each cover some bins;
-// a lane marks its bit in a per-warp mask of every bin it covers, reads back
-// the masks to rank itself among the lower lanes of the same bin, and the
-// lowest lane of each bin advances the bin's base and clears its mask.
+// Stable scatter of one warp round: lane l's input (payload p_l, flag q_l)
+// covers c_l consecutive bins from lo_l.  The round's (input, bin) pairs are
+// enumerated in input order, 32 per sub-round, each lane finding its input by
+// a binary search of the inputs' exclusive prefix counts (shuffles).  Inside
+// a bin the pairs of one sub-round come from distinct inputs in lane order,
+// and a later sub-round's from later inputs, so ranking the lanes of each bin
+// within its sub-round (per-warp lane masks in shared memory) and advancing
+// the bin's base after every sub-round keeps input order; all 32 lanes stay
+// busy however unequal the inputs' bin counts are.
+//   keep(p, q, bin): whether the pair takes a slot;
+//   emit(p, bin, slot): writes it (slot = the bin's next free slot + rank).
+template <class Keep, class Emit>
+__device__ __forceinline__ void warp_stable_scatter(uint32_t lo, uint32_t c, uint32_t payload, uint32_t flag,
+                                                    int lane, uint32_t* base, uint32_t* mask, Keep keep, Emit emit) {
+  const unsigned lt = lanemask_lt(lane);
+  const uint32_t incl = warp_incl_scan(c, lane);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t pre = incl - c;
+  for (uint32_t f0 = 0; f0 < total; f0 += 32) {
+    const uint32_t f = f0 + lane;
+    int src = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t p = __shfl_sync(kFull, pre, src + step);
+      if (p <= f) src += step;
+    }
+    const uint32_t bin = __shfl_sync(kFull, lo, src) + (f - __shfl_sync(kFull, pre, src));
+    const uint32_t ps = __shfl_sync(kFull, payload, src), qs = __shfl_sync(kFull, flag, src);
+    const bool act = f < total && keep(ps, qs, bin);
+    if (act) atomicOr(mask + bin, 1u << lane);
+    __syncwarp();
+    uint32_t m = 0, rank = 0;
+    if (act) {
+      m = mask[bin];
+      rank = __popc(m & lt);
+      emit(ps, bin, base[bin] + rank);
+    }
+    __syncwarp();
+    if (act && rank == 0) {  // lowest lane of this bin in the sub-round
+      base[bin] += __popc(m);
+      mask[bin] = 0;
+    }
+    __syncwarp();
+  }
+}
 
 // Sorted entries -> row items, grouped by (view, tile row), in entry order.
 __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
   extern __shared__ uint32_t s_dyn[];
   if (ws.counters[kStatus] != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt(lane);
   const int ny = ws.tiles_y;
   uint32_t* base = s_dyn + warp * 3 * ny;
   uint32_t* end = base + ny;
@@ -285,8 +326,9 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
   const uint32_t nu = ws.counters[kEntryUnits];
   for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < nu; u += gridDim.x * kUnitWarps) {
     const uint32_t v = ws.unit_seg_e[u];
-    const uint32_t i0 = ws.view_start[v] + (u - ws.unit_first_e[v]) * kEntryUnit;
-    const uint32_t i1 = min(i0 + (uint32_t)kEntryUnit, ws.view_start[v + 1]);
+    const uint32_t k = u - ws.unit_first_e[v];
+    const uint32_t i0 = ws.view_start[v] + (uint32_t)unit_start(k, kEntryUnit);
+    const uint32_t i1 = min(ws.view_start[v] + (uint32_t)unit_start(k + 1, kEntryUnit), ws.view_start[v + 1]);
     for (int t = lane; t < ny; t += 32) {
       const int64_t b = (int64_t)v * ny + t;
       const uint32_t bs = ws.bucket_start[b];
@@ -303,27 +345,18 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
     }
     for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
       const uint32_t e = ne;
-      const int y0 = (int)(nr.x >> 16), y1 = r0 + lane < i1 ? (int)(nr.y >> 16) : -1;
+      const uint32_t y0 = nr.x >> 16;
+      const uint32_t c = r0 + lane < i1 ? (nr.y >> 16) - y0 + 1 : 0u;
       if (r0 + 32 + lane < i1) {
         ne = ws.visible[r0 + 32 + lane];
         nr = ws.rects[ne];
       }
-      for (int y = y0; y <= y1; ++y) atomicOr(mask + y, 1u << lane);
-      __syncwarp();
-      for (int y = y0; y <= y1; ++y) {
-        const uint32_t pos = base[y] + __popc(mask[y] & lt);
-        if (pos < end[y]) ws.row_items[pos] = e;
-        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
-      }
-      __syncwarp();
-      for (int y = y0; y <= y1; ++y) {
-        const uint32_t m = mask[y];
-        if (m != 0 && (m & lt) == 0) {  // lowest lane of this row
-          base[y] += __popc(m);
-          mask[y] = 0;
-        }
-      }
-      __syncwarp();
+      warp_stable_scatter(
+          y0, c, e, 0u, lane, base, mask, [](uint32_t, uint32_t, uint32_t) { return true; },
+          [&](uint32_t es, uint32_t row, uint32_t pos) {
+            if (pos < end[row]) ws.row_items[pos] = es;
+            else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+          });
     }
   }
 }
@@ -341,8 +374,9 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_count(Ws ws) {
     const uint32_t b = ws.unit_seg_r[u];
     const int ty = (int)(b % (uint32_t)ws.tiles_y);
     const uint32_t bs = ws.bucket_start[b];
-    const uint32_t i0 = bs + (u - ws.unit_first_r[b]) * kRowUnit;
-    const uint32_t i1 = min(i0 + (uint32_t)kRowUnit, bs + ws.bucket_count[b]);
+    const uint32_t k = u - ws.unit_first_r[b];
+    const uint32_t i0 = bs + (uint32_t)unit_start(k, kRowUnit);
+    const uint32_t i1 = min(bs + (uint32_t)unit_start(k + 1, kRowUnit), bs + ws.bucket_count[b]);
     for (int t = lane; t <= nx; t += 32) cnt[t] = 0;
     __syncwarp();
     // the next item's record is loaded while this one's chords are evaluated
@@ -405,7 +439,6 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
   extern __shared__ uint32_t s_dyn[];
   if (ws.counters[kStatus] != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt(lane);
   const int nx = ws.tiles_x;
   uint32_t* base = s_dyn + warp * 3 * nx;
   uint32_t* end = base + nx;
@@ -417,8 +450,9 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
     const int ty = (int)(b % (uint32_t)ws.tiles_y);
     const int64_t vN = (int64_t)(b / (uint32_t)ws.tiles_y) * N;
     const uint32_t bs = ws.bucket_start[b];
-    const uint32_t i0 = bs + (u - ws.unit_first_r[b]) * kRowUnit;
-    const uint32_t i1 = min(i0 + (uint32_t)kRowUnit, bs + ws.bucket_count[b]);
+    const uint32_t k = u - ws.unit_first_r[b];
+    const uint32_t i0 = bs + (uint32_t)unit_start(k, kRowUnit);
+    const uint32_t i1 = min(bs + (uint32_t)unit_start(k + 1, kRowUnit), bs + ws.bucket_count[b]);
     for (int x = lane; x < nx; x += 32) {
       const int64_t t = (int64_t)b * nx + x;
       const uint32_t ts = ws.tile_start[t];
@@ -434,38 +468,27 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
     }
     for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
       const RowSpan sp = unpack_span(nspan);
-      const int64_t e = nitem;
-      const int lo = sp.lo, hi = sp.hi;
-      const bool gap = sp.gap;
+      const uint32_t e = nitem;
+      const uint32_t c = sp.lo <= sp.hi ? (uint32_t)(sp.hi - sp.lo + 1) : 0u;
+      const uint32_t lo = sp.lo <= sp.hi ? (uint32_t)sp.lo : 0u;
       if (r0 + 32 + lane < i1) {
         nspan = ws.row_span[r0 + 32 + lane];
         nitem = ws.row_items[r0 + 32 + lane];
       } else {
         nspan = 0xfffu;
       }
-      // a span with a gap (very thin tilted ellipses): its tiles are tested exactly
-      Ellipse el;
-      if (gap) el = make_ellipse(ws.records[3 * e], ws.records[3 * e + 1]);
-      auto kept = [&](int x) { return !gap || tile_kept(el, x, ty, ws.width, ws.height); };
-      for (int x = lo; x <= hi; ++x)
-        if (kept(x)) atomicOr(mask + x, 1u << lane);
-      __syncwarp();
-      const uint32_t g = (uint32_t)(e - vN);
-      for (int x = lo; x <= hi; ++x) {
-        if (!kept(x)) continue;
-        const uint32_t pos = base[x] + __popc(mask[x] & lt);
-        if (pos < end[x]) ws.sorted_ids[pos] = g;
-        else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
-      }
-      __syncwarp();
-      for (int x = lo; x <= hi; ++x) {
-        const uint32_t m = mask[x];
-        if (m != 0 && (m & lt) == 0) {  // lowest lane of this tile
-          base[x] += __popc(m);
-          mask[x] = 0;
-        }
-      }
-      __syncwarp();
+      warp_stable_scatter(
+          lo, c, e, sp.gap ? 1u : 0u, lane, base, mask,
+          [&](uint32_t es, uint32_t gap, uint32_t x) {
+            // a span with a gap (very thin tilted ellipses): its tiles are tested exactly
+            if (!gap) return true;
+            const Ellipse el = make_ellipse(ws.records[3 * (int64_t)es], ws.records[3 * (int64_t)es + 1]);
+            return tile_kept(el, (int)x, ty, ws.width, ws.height);
+          },
+          [&](uint32_t es, uint32_t x, uint32_t pos) {
+            if (pos < end[x]) ws.sorted_ids[pos] = (uint32_t)((int64_t)es - vN);
+            else atomicExch(ws.counters + kStatus, (uint32_t)GS_ERR_CUDA);
+          });
     }
   }
 }

@@ -55,11 +55,36 @@ struct Ws {
   int32_t views, width, height, tiles_x, tiles_y, tiles_per_view;
 };
 
-// Binning granularity: an entry unit is up to kEntryUnit consecutive sorted
-// visible entries of one view, a row unit up to kRowUnit row items of one
-// (view, tile row) bucket; one warp processes one unit.
+// Binning granularity: an entry unit is a run of consecutive sorted visible
+// entries of one view, a row unit a run of row items of one (view, tile row)
+// bucket; one warp processes one unit.  Inputs come in depth order, nearest
+// (largest on screen, most rows and tiles) first, so unit sizes grow
+// geometrically along a segment - kUnitFirst, 2 kUnitFirst, ... up to the
+// cap (kEntryUnit, kRowUnit) - which splits the heavy front finely.
 constexpr int kEntryUnit = 256;
 constexpr int kRowUnit = 128;
+constexpr int kUnitFirst = 4;
+
+// Units of the growing schedule before the cap is reached, and the items they hold.
+__host__ __device__ constexpr int unit_ramp(int cap) { return cap <= kUnitFirst ? 0 : 1 + unit_ramp(cap / 2); }
+// First item of unit k of a segment (units of kUnitFirst * 2^k items, then `cap`).
+__host__ __device__ inline int64_t unit_start(int64_t k, int cap) {
+  const int r = unit_ramp(cap);
+  if (k <= r) return (int64_t)kUnitFirst * ((int64_t(1) << k) - 1);
+  return (int64_t)kUnitFirst * ((int64_t(1) << r) - 1) + (k - r) * cap;
+}
+// Units covering c items.
+__host__ __device__ inline uint32_t unit_count(uint32_t c, int cap) {
+  const int r = unit_ramp(cap);
+  const int64_t ramp_items = (int64_t)kUnitFirst * ((int64_t(1) << r) - 1);
+  if (c == 0) return 0;
+  if ((int64_t)c <= ramp_items) {
+    uint32_t k = 0;
+    while (unit_start(k + 1, cap) < (int64_t)c) ++k;
+    return k + 1;
+  }
+  return (uint32_t)(r + (c - ramp_items + cap - 1) / cap);
+}
 // Entries per tile of the sort's passes (256 threads x 8).
 constexpr int kRadixTileEntries = 2048;
 
