@@ -412,14 +412,15 @@ gs_status gs_permute_rows(const void* src_dev, void* dst_dev, int64_t rows, int6
  * background only: t_final 1, n_contrib 0); or GS_ERR_CUDA if the binning
  * found its per-tile counts inconsistent (an internal error, not expected).
  * Requests whose per-Gaussian and per-tile parts do not fit in the array are
- * rejected with GS_ERR_UNSUPPORTED before anything is enqueued.  Those parts
- * take V*N*108 bytes (projected records, tile boxes, 2D adjoints, visible
- * list) + N*4 bytes (Gaussian list) + V*T*16 bytes (per-tile counts, starts,
- * cursors, bin lists; T tiles per view) + V*ceil(H/16)*12 bytes (per tile-row
- * counts) + 2048*2*ceil(W/16)*4 bytes (the binning CTAs' count slots, about
- * 2 MB at 1920 wide), each part rounded up to 256 bytes; whatever is left
- * holds 32 bytes per (Gaussian, tile) pair.  No cudaMalloc, cudaFree or
- * allocating library routine is called.
+ * rejected with GS_ERR_UNSUPPORTED before anything is enqueued.  With E =
+ * V*N entries, T tiles per view and TY = ceil(H/16), TX = ceil(W/16), those
+ * parts take about E*(131 + TY/64) bytes (projected records, tile boxes, 2D
+ * adjoints, the visible list and its sort) + N*4 bytes (Gaussian list) +
+ * V*T*8 bytes (per-tile counts and starts) + V*TY*(8 + 28*(1 + TX)) bytes
+ * (per tile-row counts and the first binning units) + 6 KB; whatever is left
+ * holds 12 + (1 + TX)/32 bytes per (Gaussian, tile) pair (about 16 B at
+ * 1920 wide).  The call computes the split exactly with gs_workspace_size.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
  *
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress (with that device current) and caches it with the id

@@ -160,7 +160,8 @@ def test_multiview_ragged_sh3(oracle, sh_bf16, degenerate):
 
 
 def test_long_tiles_and_merge_path(oracle):
-    """Bins longer than one CTA's shared memory (> 2,048 and > 16,384 keys)."""
+    """Bins of more than 16,384 pairs: every pair of a very long tile list in
+    (depth key, index) order."""
     rng = np.random.default_rng(5)
     n = 24000
     g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
@@ -169,16 +170,16 @@ def test_long_tiles_and_merge_path(oracle):
     rast, gm, ct, out = gpu_render(g, [cam])
     _, count, _ = rast.tile_lists()
     assert int(count.max()) > 16384
-    compare_tiles(oracle, m, cam, rast, 0, label="bins > 16,384 keys (merge path)")
+    compare_tiles(oracle, m, cam, rast, 0, label="bins > 16,384 pairs")
     o_r = oracle.render(m, cam)
     _check_images(o_r, out, 0, "long tiles")
 
 
 @pytest.mark.parametrize("n,lo,hi", [(900, 65, 768), (2600, 769, 2048)])
 def test_bin_size_classes(oracle, n, lo, hi):
-    """Bins sorted by a small CTA per bin (65..768 keys) and by the
-    persistent medium-bin CTAs (769..2,048 keys): tile lists bit-exact
-    against the oracle."""
+    """Bins of 65..768 and of 769..2,048 pairs, where one warp round of the
+    stable scatter meets many earlier rounds' pairs of the same tile: tile
+    lists bit-exact against the oracle."""
     rng = np.random.default_rng(6)
     g = synth.random_map(rng, n, (-0.6, -0.5, 4), (0.6, 0.5, 40), 0, log_scale_mean=-0.5, log_scale_std=0.3)
     cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 40.0, 24.0, 20.0, 48, 40)
@@ -187,8 +188,8 @@ def test_bin_size_classes(oracle, n, lo, hi):
     _, count, _ = rast.tile_lists()
     c = count.cpu().numpy()
     assert ((c >= lo) & (c <= hi)).any(), c
-    compare_tiles(oracle, m, cam, rast, 0, label=f"bins of {lo}..{hi} keys")
-    _check_images(oracle.render(m, cam), out, 0, f"bins of {lo}..{hi} keys")
+    compare_tiles(oracle, m, cam, rast, 0, label=f"bins of {lo}..{hi} pairs")
+    _check_images(oracle.render(m, cam), out, 0, f"bins of {lo}..{hi} pairs")
 
 
 def test_capacity_overflow_reports_and_retries(oracle):
