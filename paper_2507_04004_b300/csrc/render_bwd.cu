@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
   // ---- per-pixel adjoints (dL/dC, dL/dD, dL/dO) and loss
   float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gO[PPT], T[PPT], py[PPT];
   // S = adjoint-weighted value of everything behind the current Gaussian:
-  // sum over later contributors j of (gC.c_j + gD d_j + gO) alpha_j T_j / T_next, plus gC.bg
+  // sum over later contributors j of (gC.c_j + gD d_j + gO) alpha_j T_j / T_next, plus gC.bg.
+  // The walk keeps S - gO instead: it obeys the same recursion
+  // S_i = alpha_i x_i + (1 - alpha_i) S_{i+1} with gO dropped from every
+  // value x_i, so gO needs no register of its own.
   float S[PPT];
   uint32_t last[PPT];
   float loss = 0.f;
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
       if (DEP && a.dl_dopac) gO[k] = a.dl_dopac[v * HW + p];
     }
     mx = max(mx, last[k]);
-    S[k] = gC0[k] * cfg.bg[0] + gC1[k] * cfg.bg[1] + gC2[k] * cfg.bg[2];
+    S[k] = gC0[k] * cfg.bg[0] + gC1[k] * cfg.bg[1] + gC2[k] * cfg.bg[2] - gO[k];
   }
   // CTA reductions: loss sum and the longest contributor prefix
 #pragma unroll
@@ -180,17 +183,16 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
 
   // ---- back-to-front walk over vertical pixel pairs (k = 2h, 2h + 1)
   constexpr int NP = PPT / 2;
-  float2 C0[NP], C1[NP], C2[NP], GD[NP], GO[NP], T2[NP], S2[NP], Y[NP];
+  float2 C0[NP], C1[NP], C2[NP], GD[NP], T2[NP], S2[NP], Y[NP];
 #pragma unroll
   for (int h = 0; h < NP; ++h) {
     C0[h] = make_float2(gC0[2 * h], gC0[2 * h + 1]);
     C1[h] = make_float2(gC1[2 * h], gC1[2 * h + 1]);
     C2[h] = make_float2(gC2[2 * h], gC2[2 * h + 1]);
     GD[h] = make_float2(gD[2 * h], gD[2 * h + 1]);
-    GO[h] = make_float2(gO[2 * h], gO[2 * h + 1]);
     T2[h] = make_float2(T[2 * h], T[2 * h + 1]);
-    S2[h] = make_float2(S[2 * h], S[2 * h + 1]);
     Y[h] = make_float2(py[2 * h], py[2 * h + 1]);
+    S2[h] = make_float2(S[2 * h], S[2 * h + 1]);
   }
   const float a_max = cfg.alpha_max;
   const float lt = __log2f(cfg.alpha_min);
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
         // transmittance in front of this Gaussian
         T2[h] = mul2(T2[h], make_float2(a0 ? __fdividef(1.f, om.x) : 1.f, a1 ? __fdividef(1.f, om.y) : 1.f));
         const float2 w = mul2(al, T2[h]);
-        const float2 gx = DEP ? fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, fma2(GD[h], dep, GO[h]))))
+        const float2 gx = DEP ? fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, mul2(GD[h], dep))))
                               : fma2(C0[h], cr, fma2(C1[h], cg, mul2(C2[h], cb)));
         const float2 e = fma2(S2[h], f2(-1.f), gx);
         const float2 dA = mul2(T2[h], e);  // dL/dalpha
