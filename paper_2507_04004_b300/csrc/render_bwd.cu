@@ -213,20 +213,22 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
       for (int q = 0; q < 10; ++q) s_acc[i][q] = 0.f;
     }
     __syncthreads();
+#pragma unroll 2
     for (int j = nb - 1; j >= 0; --j) {
       const float4 g0 = s_g0[j], g1 = s_g1[j];
       const uint32_t pos = (uint32_t)(beg + j);
       const float dx = px - g0.x;
       const ColTerms ct = col_terms(g0, g1, px);
-      float2 p2[NP];
-      bool act[PPT];
+      float2 ea[NP];  // o 2^p2 where the pixel takes part, 0 elsewhere
       bool any = false;
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
-        p2[h] = col_p2x2(ct, Y[h]);
-        act[2 * h] = (pos < last[2 * h]) & (p2[h].x >= lt);
-        act[2 * h + 1] = (pos < last[2 * h + 1]) & (p2[h].y >= lt);
-        any |= act[2 * h] | act[2 * h + 1];
+        const float2 p2 = col_p2x2(ct, Y[h]);
+        const bool a0 = (pos < last[2 * h]) & (p2.x >= lt);
+        const bool a1 = (pos < last[2 * h + 1]) & (p2.y >= lt);
+        const float e0 = ex2_approx(p2.x), e1 = ex2_approx(p2.y);
+        ea[h] = make_float2(a0 ? e0 : 0.f, a1 ? e1 : 0.f);
+        any |= a0 | a1;
       }
       if (!__any_sync(kFull, any)) continue;
       // Per-Gaussian sums over this thread's pixels.  With dp = dL/dpower
@@ -246,20 +248,20 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
       auto walk = [&](auto clamp) {
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
-        const bool a0 = act[2 * h], a1 = act[2 * h + 1];
-        const float e0 = ex2_approx(p2[h].x), e1 = ex2_approx(p2[h].y);
         float2 al, ag;
         if (decltype(clamp)::value) {
-          al = make_float2(a0 ? fminf(a_max, e0) : 0.f, a1 ? fminf(a_max, e1) : 0.f);
+          al = make_float2(fminf(a_max, ea[h].x), fminf(a_max, ea[h].y));
           // alpha = o exp(power): dL/dpower = dL/dalpha alpha, zero where alpha is clamped
-          ag = make_float2(e0 > a_max ? 0.f : al.x, e1 > a_max ? 0.f : al.y);
+          ag = make_float2(ea[h].x > a_max ? 0.f : al.x, ea[h].y > a_max ? 0.f : al.y);
         } else {
-          al = make_float2(a0 ? e0 : 0.f, a1 ? e1 : 0.f);
+          al = ea[h];
           ag = al;
         }
-        const float2 om = fma2(al, f2(-1.f), f2(1.f));  // 1 - alpha >= 0.01
+        // 1 - alpha >= 0.01; exactly 1 where alpha = 0, whose reciprocal leaves T as it is
+        // (up to the approximate reciprocal's one-ulp bound)
+        const float2 om = fma2(al, f2(-1.f), f2(1.f));
         // transmittance in front of this Gaussian
-        T2[h] = mul2(T2[h], make_float2(a0 ? __fdividef(1.f, om.x) : 1.f, a1 ? __fdividef(1.f, om.y) : 1.f));
+        T2[h] = mul2(T2[h], make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y)));
         const float2 w = mul2(al, T2[h]);
         const float2 gx = DEP ? fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, mul2(GD[h], dep))))
                               : fma2(C0[h], cr, fma2(C1[h], cg, mul2(C2[h], cb)));
@@ -297,7 +299,11 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
       val[9] = v9.x + v9.y;
       int slot;
       const float sum = warp_reduce_scatter10(val, lane, &slot);
-      if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) atomicAdd(&s_acc[j][slot], sum);
+      if (NW == 1) {  // the tile's only warp owns the slots: plain stores
+        if (slot >= 0 && (lane & 1) == 0) s_acc[j][slot] = sum;
+      } else if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) {
+        atomicAdd(&s_acc[j][slot], sum);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += NT) {
