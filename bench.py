@@ -427,10 +427,14 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
       preprocess_bwd: per listed Gaussian parameters + SH read and their
                 gradients read and written ((44 + SH) x 3); per visible
                 entry 96 B (record, adjoint); ~300 ops per visible entry
-      count_depth: 4 B per pixel."""
+      count_depth: 4 B per pixel.
+      tile_work: n_contrib read (4 B per pixel), per (view, tile) item its
+                class slot taken and written; a max per pixel, ~40 ops per
+                item."""
     deg = WORKLOAD["sh_degree"] if sh_degree is None else sh_degree
     b_sh = 4 * 3 * (deg + 1) ** 2
     px = views * hw
+    tiles = views * ((WORKLOAD["width"] + 15) // 16) * ((WORKLOAD["height"] + 15) // 16)
     passes = 4 + (1 if views > 1 else 0)
     return {
         "project": (44.0 * n + b_sh * n_vis + 100.0 * n_vis + 8.0 * views * n + 8.0 * n_vis,
@@ -445,6 +449,7 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
         "render_fwd": (52.0 * p_proc + 28.0 * px,
                        k_blend * BLEND_OPS["render_fwd"][0] + k_skip * BLEND_OPS["render_fwd"][1]),
         "count_depth": (4.0 * px, 2.0 * px),
+        "tile_work": (4.0 * px + 8.0 * tiles, 2.0 * px + 40.0 * tiles),
         "render_bwd": (44.0 * px + 100.0 * p_proc,
                        k_blend * BLEND_OPS["render_bwd"][0] + k_skip * BLEND_OPS["render_bwd"][1]),
         "preprocess_bwd": ((44.0 + b_sh) * 3 * n_listed + 96.0 * n_vis, 300.0 * n_vis),

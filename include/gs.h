@@ -137,6 +137,9 @@ typedef struct {
   size_t row_span;    /* uint32[cap]: kept tile columns of each row item */
   size_t sorted_ids;  /* uint32[cap]: Gaussian index of each pair, sorted by (tile, depth key, index) */
   size_t view_stats;  /* float[V][4]: per-view loss accumulators and valid-depth counts */
+  size_t work_fill;   /* uint32[64]: items in each of the blend backward's 64 work classes */
+  size_t work_lists;  /* uint32[64][V*T]: (view, tile) items of each work class; class c holds the tiles
+                         whose longest contributor prefix w has floor(6 log2(w + 1)) = c (63: or more) */
   size_t total;       /* bytes */
 } gs_layout;
 
@@ -163,11 +166,13 @@ gs_status gs_read_status(const gs_workspace* ws, gs_stream_t stream, int32_t* st
 gs_status gs_project(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg, const gs_workspace* ws,
                      gs_stream_t stream);
 
-/* Binning and sorting: exclusive scan of the per-tile counts (tile ranges),
- * one key (depth key bits << 32 | Gaussian index) per kept (Gaussian, tile)
- * pair written into its tile's bin, and a sort of every bin, giving the
- * Gaussians of each tile in (depth key, index) order.  On overflow the status
- * word becomes GS_ERR_CAPACITY and the later calls of the batch do nothing. */
+/* Binning and sorting: the visible (view, Gaussian) entries sorted once by
+ * (view, depth key bits, Gaussian index), then stable scatters into (view,
+ * tile row) buckets and into the tile bins of the kept (Gaussian, tile)
+ * pairs, so each tile's Gaussians come out in (depth key, index) order, the
+ * order of a sort on 64-bit (tile, depth) keys; tile ranges from the per-tile
+ * counts.  On overflow the status word becomes GS_ERR_CAPACITY and the later
+ * calls of the batch do nothing. */
 gs_status gs_bin_sort(const gs_workspace* ws, gs_stream_t stream);
 
 /* Front-to-back compositing per 16x16 tile (Eq. alpha, Eq. rendered_rgb,
@@ -198,7 +203,13 @@ gs_status gs_blend_counts(const gs_config* cfg, const gs_workspace* ws, uint64_t
  * where given (any of the three may be NULL = zero; with tgt_rgb == NULL they
  * are the whole adjoint, e.g. of an autograd graph; with it they add further
  * loss terms such as gs_dssim's gradient).  Recomputes each
- * pixel's blending state back to front from t_final and n_contrib.
+ * pixel's blending state back to front from t_final and n_contrib.  The
+ * blend stage walks a work list of the batch's (view, tile) items, longest
+ * first: each tile goes into one of 64 classes by its longest contributor
+ * prefix (the maximum of its pixels' n_contrib), and CTA b of the one launch
+ * over all views takes item b of the classes' items, longest class first.  The
+ * order only schedules the work: any order gives the same gradients up to
+ * the summation order of float atomics.
  * Gradients are ADDED to grad_* (caller zeroes them): grad_mean [3][N],
  * grad_log_scale [3][N], grad_quat [4][N], grad_logit_opacity [N],
  * grad_sh_dc [3][N], grad_sh_rest [K-1][3][N] (FP32 even for BF16 SH; may be
@@ -416,7 +427,7 @@ gs_status gs_permute_rows(const void* src_dev, void* dst_dev, int64_t rows, int6
  * V*N entries, T tiles per view and TY = ceil(H/16), TX = ceil(W/16), those
  * parts take about E*(131 + TY/64) bytes (projected records, tile boxes, 2D
  * adjoints, the visible list and its sort) + N*4 bytes (Gaussian list) +
- * V*T*8 bytes (per-tile counts and starts) + V*TY*(8 + 28*(1 + TX)) bytes
+ * V*T*264 bytes (per-tile counts and starts, the backward's work lists) + V*TY*(8 + 28*(1 + TX)) bytes
  * (per tile-row counts and the first binning units) + 6 KB; whatever is left
  * holds 12 + (1 + TX)/32 bytes per (Gaussian, tile) pair (about 16 B at
  * 1920 wide).  The call computes the split exactly with gs_workspace_size.

@@ -53,7 +53,8 @@ class gs_layout(C.Structure):
                                           "sort_val", "radix_status", "view_start", "gauss_list", "tile_count",
                                           "tile_start", "bucket_count", "bucket_start", "unit_first_e", "unit_seg_e",
                                           "unit_cnt_e", "unit_first_r", "unit_seg_r", "unit_cnt_r", "row_items",
-                                          "row_span", "sorted_ids", "view_stats", "total")]
+                                          "row_span", "sorted_ids", "view_stats", "work_fill",
+                                          "work_lists", "total")]
 
 
 class gs_adam_config(C.Structure):

@@ -54,6 +54,8 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   L->row_span = take((size_t)cap * sizeof(uint32_t));
   L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
   L->view_stats = take((size_t)V * 4 * sizeof(float));
+  L->work_fill = take((size_t)kWorkClasses * sizeof(uint32_t));
+  L->work_lists = take((size_t)kWorkClasses * (V * T) * sizeof(uint32_t));
   L->total = off;
   return GS_OK;
 }
@@ -87,6 +89,8 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.row_span = u32(L.row_span);
   ws.sorted_ids = u32(L.sorted_ids);
   ws.view_stats = reinterpret_cast<float*>(b + L.view_stats);
+  ws.work_fill = u32(L.work_fill);
+  ws.work_lists = u32(L.work_lists);
   ws.n = w->n;
   ws.cap = w->pair_capacity;
   ws.views = w->frame.n_views;
@@ -446,7 +450,7 @@ const char* gs_kernel_name(int32_t id) {
       "project",    "scan",           "scatter_rows",   "depth_hist",    "depth_scan",  "render_fwd",
       "count_depth", "render_bwd",    "preprocess_bwd", "pose_jacobian", "scan_buckets", "rows_count",
       "rows_emit",  "ssim_fwd",       "ssim_bwd",       "sparse_adam",   "depth_scatter", "render_fwd_ckpt",
-      "render_bwd_bucket", "entry_order", "entry_units", "entry_rows",   "unit_scan"};
+      "render_bwd_bucket", "entry_order", "entry_units", "entry_rows",   "unit_scan", "tile_work"};
   return (id >= 0 && id < kKNumKernels) ? names[id] : "unknown";
 }
 

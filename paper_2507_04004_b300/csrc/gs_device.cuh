@@ -20,6 +20,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // pixels per thread in the blend kernels (a tile is 256 / PPT threads)
 constexpr int kFwdPPT = 4;
 constexpr int kBwdPPT = 8;
+constexpr int kWorkClasses = 64;  // classes of the blend backward's work list
+static_assert(kWorkClasses % 32 == 0, "work classes are scanned 32 at a time");
 constexpr int kBwdBatch = 128;  // Gaussians staged in shared memory per batch by the backward blend
 
 // Device view of the workspace parts (pointers resolved from gs_layout).
@@ -49,6 +51,8 @@ struct Ws {
   uint32_t* row_span;       // [cap] packed kept-tile span of each row item
   uint32_t* sorted_ids;   // [cap]
   float* view_stats;      // [V][4]
+  uint32_t* work_fill;    // [kWorkClasses] items per work class
+  uint32_t* work_lists;   // [kWorkClasses][V*T] (view, tile) items of each class
   int64_t n;
   int64_t cap;
   int64_t units_e_max, units_r_max, radix_tiles_max;

@@ -13,7 +13,7 @@ enum KernelId {
   kKProject = 0, kKScan, kKScatterRows, kKDepthHist, kKDepthScan, kKRenderFwd, kKCountDepth, kKRenderBwd,
   kKPreprocessBwd, kKPoseJacobian, kKScanBuckets, kKRowsCount, kKRowsEmit, kKSsimFwd, kKSsimBwd, kKSparseAdam,
   kKDepthScatter, kKRenderFwdCkpt, kKRenderBwdBucket, kKEntryOrder, kKEntryUnits, kKEntryRows, kKUnitScan,
-  kKNumKernels
+  kKTileWork, kKNumKernels
 };
 // Bracket one kernel launch with the caller's trace events (no-op when off).
 void trace_begin(int kernel_id, cudaStream_t st);

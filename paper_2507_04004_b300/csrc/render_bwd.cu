@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "gs_internal.h"
+#include "radix.cuh"
 
 namespace gsb {
 
@@ -72,11 +73,12 @@ __device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int la
   return z;
 }
 
-// DEP: the pixel adjoints of depth and opacity may be nonzero (a depth loss or
-// the caller's depth / opacity adjoints); without them (colour-only losses,
-// e.g. tracking) they and their terms are left out at compile time.
+// One (view, tile) item of the blend backward.  DEP: the pixel adjoints of
+// depth and opacity may be nonzero (a depth loss or the caller's depth /
+// opacity adjoints); without them (colour-only losses, e.g. tracking) they
+// and their terms are left out at compile time.
 template <bool FUSED, bool DEP, int PPT>
-__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 / (256 / PPT) / 2) k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+__device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, const BwdArgs& a, const int64_t tile) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
@@ -86,8 +88,6 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
   __shared__ float s_acc[NB][10];
   __shared__ float s_red[NW];
   __shared__ uint32_t s_max[NW];
-  if (ws.counters[kStatus] != 0) return;
-  const int64_t tile = blockIdx.x;
   const int v = (int)(tile / ws.tiles_per_view);
   const int t = (int)(tile - (int64_t)v * ws.tiles_per_view);
   const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
@@ -320,6 +320,113 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
       if (q[7] != 0.f || q[8] != 0.f || q[9] != 0.f) atomicAdd(dst + 2, make_float4(q[7], q[8], q[9], 0.f));
     }
   }
+}
+
+// Work list of the blend backward.  A tile's work is its longest contributor
+// prefix w (the maximum of its pixels' n_contrib: the list positions its
+// backward walks); k_tile_work puts every (view, tile) item into one of
+// kWorkClasses classes, class floor(6 log2(w + 1)) (classes grow by 2^(1/6)),
+// and CTA b of the backward takes item b of the classes' items, longest
+// class first, so the last CTAs to start are short and the launch ends
+// evenly.  Order inside a class is arbitrary; any order gives the same
+// gradients up to the summation order of float atomics.
+__device__ __forceinline__ uint32_t work_class(uint32_t w) {
+  return (uint32_t)min(kWorkClasses - 1, (int)(6.f * __log2f((float)w + 1.f)));
+}
+
+constexpr int kWorkThreads = 1024;                  // threads of one CTA of k_tile_work
+constexpr int kWorkPerWarp = 4;                     // items per warp, their loads in flight together
+constexpr int kWorkItemsPerCta = kWorkThreads / 32 * kWorkPerWarp;
+
+// Per CTA kWorkItemsPerCta (view, tile) items, kWorkPerWarp per warp: each
+// item's work from the tile's n_contrib words (a half-warp reads one pixel
+// row, 16 consecutive words); the CTA's items counted per class in shared
+// memory, one reservation per class of the CTA, then every item written to
+// its class list (fill counts cleared before).
+__global__ void __launch_bounds__(kWorkThreads) k_tile_work(Ws ws, const uint32_t* __restrict__ n_contrib) {
+  __shared__ uint32_t s_cnt[kWorkClasses], s_base[kWorkClasses];
+  __shared__ uint32_t s_cls[kWorkItemsPerCta], s_rank[kWorkItemsPerCta];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
+  const int64_t first = (int64_t)blockIdx.x * kWorkItemsPerCta + (int64_t)warp * kWorkPerWarp;
+  for (int c = threadIdx.x; c < kWorkClasses; c += kWorkThreads) s_cnt[c] = 0;
+  uint32_t w[kWorkPerWarp];
+#pragma unroll
+  for (int q = 0; q < kWorkPerWarp; ++q) {
+    w[q] = 0;
+    const int64_t item = first + q;
+    if (item >= items) continue;
+    const int v = (int)(item / ws.tiles_per_view);
+    const int t = (int)(item - (int64_t)v * ws.tiles_per_view);
+    const int tx = t % ws.tiles_x, ty = t / ws.tiles_x;
+    const int x = tx * kTile + (lane & 15);
+#pragma unroll
+    for (int r = 0; r < kTile; r += 2) {
+      const int y = ty * kTile + r + (lane >> 4);
+      if (x < ws.width && y < ws.height) w[q] = max(w[q], n_contrib[((int64_t)v * ws.height + y) * ws.width + x]);
+    }
+  }
+  __syncthreads();  // s_cnt cleared
+#pragma unroll
+  for (int q = 0; q < kWorkPerWarp; ++q) {
+    const uint32_t m = __reduce_max_sync(kFull, w[q]);
+    const int64_t item = first + q;
+    if (lane == 0 && item < items) {
+      const int li = warp * kWorkPerWarp + q;
+      const uint32_t c = work_class(min(m, ws.tile_count[item]));
+      s_cls[li] = c;
+      s_rank[li] = atomicAdd(&s_cnt[c], 1u);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kWorkClasses; c += kWorkThreads)
+    if (s_cnt[c]) s_base[c] = atomicAdd(ws.work_fill + c, s_cnt[c]);
+  __syncthreads();
+  for (int li = threadIdx.x; li < kWorkItemsPerCta; li += kWorkThreads) {
+    const int64_t it = (int64_t)blockIdx.x * kWorkItemsPerCta + li;
+    if (it < items) {
+      const uint32_t c = s_cls[li];
+      ws.work_lists[(int64_t)c * items + s_base[c] + s_rank[li]] = (uint32_t)it;
+    }
+  }
+}
+
+// The blend backward over the work list: CTA b takes item b of the
+// sequence of the classes' items, longest class first (the hardware starts
+// CTAs in index order); when the lists do not hold every item once (not
+// filled since the last binning), item b is tile b.
+template <bool FUSED, bool DEP, int PPT>
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 / (256 / PPT) / 2)
+    k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
+  __shared__ uint32_t s_item;
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    uint32_t k = blockIdx.x, item = k;
+    uint32_t run = 0, total = 0;
+    bool found = false;
+#pragma unroll
+    for (int h = 0; h < kWorkClasses; h += 32) {  // classes longest first, 32 at a time
+      const int c = kWorkClasses - 1 - (h + lane);
+      const uint32_t f = ws.work_fill[c];
+      const uint32_t incl = warp_incl_scan(f, lane) + run;
+      // the first lane whose running count passes k holds k's class
+      const unsigned m = __ballot_sync(kFull, k < incl);
+      if (!found && m) {
+        const int l = __ffs(m) - 1;
+        const uint32_t before = __shfl_sync(kFull, incl - f, l);
+        const int cc = kWorkClasses - 1 - (h + l);
+        item = ws.work_lists[(int64_t)cc * items + (k - before)];
+        found = true;
+      }
+      run = __shfl_sync(kFull, incl, 31);
+    }
+    total = run;
+    if (lane == 0) s_item = total == (uint32_t)items ? item : (uint32_t)blockIdx.x;
+  }
+  __syncthreads();
+  bwd_tile<FUSED, DEP, PPT>(cfg, ws, a, (int64_t)s_item);
 }
 
 // Chain of the 2D adjoints through the projection, per Gaussian over all
@@ -668,22 +775,38 @@ cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, cons
   }
 }
 
+// One CTA per work item; the hardware starts them in index order, which is
+// the work list's longest-first order.
+template <bool FUSED, bool DEP>
+static cudaError_t launch_blend_bwd(const gs_config& cfg, const Ws& ws, const BwdArgs& a, int64_t items,
+                                    cudaStream_t st) {
+  if (items < 1) return cudaSuccess;
+  k_render_bwd<FUSED, DEP, kBwdPPT><<<(unsigned)items, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                               const BwdArgs& a, cudaStream_t st) {
   cudaError_t err = launch_bwd_prologue(ws, a, st);
   if (err != cudaSuccess) return err;
   const bool fused = a.tgt_rgb != nullptr;
-  const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
+  const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
   const bool dep = (fused && a.tgt_depth && a.w_depth != 0.f) || a.dl_ddepth || a.dl_dopac;
+  if ((err = cudaMemsetAsync(ws.work_fill, 0, kWorkClasses * sizeof(uint32_t), st)) != cudaSuccess) return err;
+  trace_begin(kKTileWork, st);
+  k_tile_work<<<(unsigned)((items + kWorkItemsPerCta - 1) / kWorkItemsPerCta), kWorkThreads, 0, st>>>(ws, a.n_contrib);
+  trace_end(st);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
   trace_begin(kKRenderBwd, st);
   if (fused) {
-    if (dep) k_render_bwd<true, true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
-    else k_render_bwd<true, false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+    if (dep) err = launch_blend_bwd<true, true>(cfg, ws, a, items, st);
+    else err = launch_blend_bwd<true, false>(cfg, ws, a, items, st);
   } else {
-    if (dep) k_render_bwd<false, true, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
-    else k_render_bwd<false, false, kBwdPPT><<<ntiles, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+    if (dep) err = launch_blend_bwd<false, true>(cfg, ws, a, items, st);
+    else err = launch_blend_bwd<false, false>(cfg, ws, a, items, st);
   }
   trace_end(st);
+  if (err != cudaSuccess) return err;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   return launch_preprocess_bwd(map, cams, cfg, ws, a, st);
 }

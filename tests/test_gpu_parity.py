@@ -371,6 +371,41 @@ def test_backward_twice_gives_same_gradients(backward):
         assert rel_err(a.cpu().numpy(), b.cpu().numpy()) <= 1e-4
 
 
+def _work_list(rast):
+    """The blend backward's work list: (class of every item, items longest class first)."""
+    nt = rast.views * ((rast.width + 15) // 16) * ((rast.height + 15) // 16)
+    fill = rast._view(rast.layout.work_fill, 64, torch.int32).cpu().numpy().astype(np.int64)
+    lists = rast._view(rast.layout.work_lists, 64 * nt, torch.int32).view(64, nt).cpu().numpy().astype(np.int64)
+    cls = np.full(nt, -1, np.int64)
+    order = []
+    for c in range(63, -1, -1):
+        items = lists[c, :fill[c]]
+        cls[items] = c
+        order.append(items)
+    return cls, np.concatenate(order), fill
+
+
+def test_backward_work_list_longest_first():
+    """Every (view, tile) item of the batch sits in one work class, the class
+    of its longest contributor prefix w: floor(6 log2(w + 1)), at most 63."""
+    import torch.nn.functional as F
+    g, cams = _mapping_small(n=20000)
+    rast, gm, ct, out = gpu_render(g, cams)
+    dl = torch.randn(len(cams), 3, cams[0]["height"], cams[0]["width"], device="cuda")
+    rast.backward(gm, ct, out, dl_drgb=dl)
+    torch.cuda.synchronize()
+    cls, order, fill = _work_list(rast)
+    nt = cls.size
+    assert np.array_equal(np.sort(order), np.arange(nt))
+    V, H, W = out.n_contrib.shape
+    x = F.pad(out.n_contrib.float().view(V, 1, H, W), (0, (-W) % 16, 0, (-H) % 16))
+    w = F.max_pool2d(x, 16).view(-1).cpu().numpy().astype(np.float64)
+    e = 6.0 * np.log2(w + 1.0)
+    # the device evaluates the logarithm approximately: allow a hair at class edges
+    assert np.all((cls >= np.floor(e - 1e-4)) & (cls <= np.minimum(63, np.floor(e + 1e-4))))
+    assert len(np.unique(cls)) > 3
+
+
 def test_autograd_function_matches_backward():
     from paper_2507_04004_b300.raster import rasterize
     g, cams = _mapping_small(n=6000, n_views=2)
