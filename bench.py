@@ -399,7 +399,8 @@ BLEND_OPS = {  # kernel: (blended ops, skipped ops, blended FLOP, skipped FLOP)
 }
 
 
-def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip, sh_degree=None):
+def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip, k_tested=None,
+               sh_degree=None):
     """Algorithmic (bytes, lane operations) per launch of every kernel of the
     mapping step, from the step's work counters.  Bytes: what the method must
     move to or from HBM at least once; operations: the arithmetic the method
@@ -421,7 +422,10 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
       rows_emit: per row item 4 + 4 B read, 4 B Gaussian index written per
                 pair; ~10 ops per pair
       render_fwd: 52 B (record + index) per processed pair, 28 B per pixel
-                written (RGB, depth, opacity, T_final, n_contrib)
+                written (RGB, depth, opacity, T_final, n_contrib); operations
+                per blended evaluation and per other list position a pixel
+                tests (up to the Gaussian it stops at, else its tile's whole
+                list: positions past the last contributor still need the test)
       render_bwd: 44 B per pixel read (RGB, target RGB, depth, opacity,
                 T_final, n_contrib, target depth), 52 B per processed pair,
                 48 B of 2D adjoints added per processed pair
@@ -435,6 +439,7 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
     deg = WORKLOAD["sh_degree"] if sh_degree is None else sh_degree
     b_sh = 4 * 3 * (deg + 1) ** 2
     px = views * hw
+    k_fwd = k_tested if k_tested is not None else k_blend + k_skip  # evaluations the forward makes
     tiles = views * ((WORKLOAD["width"] + 15) // 16) * ((WORKLOAD["height"] + 15) // 16)
     passes = 4 + (1 if views > 1 else 0)
     return {
@@ -448,7 +453,7 @@ def step_model(n, views, hw, n_vis, n_rows, n_pairs, n_listed, p_proc, k_blend, 
         "rows_count": (40.0 * n_rows, 16 * 14.0 * n_rows),
         "rows_emit": (8.0 * n_rows + 4.0 * n_pairs, 10.0 * n_pairs),
         "render_fwd": (52.0 * p_proc + 28.0 * px,
-                       k_blend * BLEND_OPS["render_fwd"][0] + k_skip * BLEND_OPS["render_fwd"][1]),
+                       k_blend * BLEND_OPS["render_fwd"][0] + (k_fwd - k_blend) * BLEND_OPS["render_fwd"][1]),
         "count_depth": (4.0 * px, 2.0 * px),
         "tile_work": (4.0 * px + 8.0 * tiles, 2.0 * px + 40.0 * tiles),
         "render_bwd": (44.0 * px + 100.0 * p_proc,
@@ -806,11 +811,12 @@ def run_ours(args):
     counters = rast._view(rast.layout.counters, 8, torch.int32).cpu().numpy()
     n_visible, n_pairs, n_rows, n_listed = int(counters[2]), int(counters[1]), int(counters[4]), int(counters[5])
     k_eval = float(out.n_contrib.to(torch.float64).sum().item())
-    bc = torch.zeros(args.views, 2, dtype=torch.int64, device=d.dev)
+    bc = torch.zeros(args.views, 3, dtype=torch.int64, device=d.dev)
     N.gs_blend_counts(rast.cfg, rast.ws, bc, torch.cuda.current_stream(d.dev).cuda_stream)
     bc = bc.cpu().numpy().sum(0)
     k_blend = float(bc[1])
     k_skip = float(bc[0]) - k_blend
+    k_tested = float(bc[2])  # list positions the forward's pixels must test (up to their stop, else all)
     p_proc = float(tile_max_prefix(out.n_contrib))
     px_step = V * H * W
     peaks = measured_peaks()
@@ -818,7 +824,8 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(d.dev).multi_processor_count
     issue = n_sm * 4 * sm_mhz * 1e6  # warp instructions per second (4 schedulers per SM)
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 FLOP
-    model = step_model(args.n, args.views, H * W, n_visible, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip)
+    model = step_model(args.n, args.views, H * W, n_visible, n_rows, n_pairs, n_listed, p_proc, k_blend, k_skip,
+                       k_tested)
     bw = peaks["hbm_gbs"] * 1e9
 
     def roof(k):
@@ -930,6 +937,7 @@ def run_ours(args):
                          "gaussians_listed": n_listed, "pairs_processed": p_proc,
                          "blend_evaluations": k_eval, "blend_evaluations_blended": k_blend,
                          "blend_evaluations_skipped": k_skip,
+                         "forward_positions_tested": k_tested,
                          "lidar_valid_frac": [round(x, 4) for x in w.meta["depth_frac"]]}}
         print(json.dumps(line), flush=True)
     d.close()

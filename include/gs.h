@@ -188,11 +188,13 @@ gs_status gs_render_fwd(const gs_config* cfg, const gs_workspace* ws, float* rgb
 /* Work counters of the compositing (measurement support; no counterpart in
  * the paper): runs the front-to-back compositing of gs_render_fwd over the
  * workspace's tile lists without writing an image and sets, per view,
- * counts_dev[2v] = number of (pixel, tile-list position) evaluations up to
- * each pixel's last blended Gaussian (the sum of gs_render_fwd's n_contrib)
- * and counts_dev[2v + 1] = how many of them were blended (the others were
- * skipped below alpha_min).  counts_dev: device uint64 [V][2], 8-byte
- * aligned, overwritten. */
+ * counts_dev[3v] = number of (pixel, tile-list position) evaluations up to
+ * each pixel's last blended Gaussian (the sum of gs_render_fwd's n_contrib),
+ * counts_dev[3v + 1] = how many of them were blended (the others were
+ * skipped below alpha_min) and counts_dev[3v + 2] = the tile-list positions
+ * the pixels test (each up to and including the Gaussian at which it stops,
+ * else its tile's whole list: the evaluations the forward cannot avoid).
+ * counts_dev: device uint64 [V][3], 8-byte aligned, overwritten. */
 gs_status gs_blend_counts(const gs_config* cfg, const gs_workspace* ws, uint64_t* counts_dev, gs_stream_t stream);
 
 /* Backward pass (Eq. depth_loss back through Eq. rendered_* and the

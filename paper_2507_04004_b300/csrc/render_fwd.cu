@@ -15,8 +15,10 @@
 //
 // The counting variant (STATS) composites the same way but writes no image:
 // it adds, per view, the number of (pixel, list position) evaluations up to
-// each pixel's last contributor and how many of them were blended (the rest
-// were skipped below alpha_min) into ckpt reinterpreted as uint64 [V][2].
+// each pixel's last contributor, how many of them were blended (the rest
+// were skipped below alpha_min), and the list positions the pixels test (up
+// to the Gaussian at which each stops, else the whole list) into ckpt
+// reinterpreted as uint64 [V][3].
 #include "gs_internal.h"
 
 namespace gsb {
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   float thr[PPT];
   uint32_t last[PPT];
   uint32_t n_blend = 0;  // STATS only
+  uint32_t stop_at[PPT];  // STATS only: list positions a pixel tests (up to its stop, else the whole list)
   bool all_done = true;
   const float inf = __int_as_float(0x7f800000);
 #pragma unroll
@@ -60,6 +63,7 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
     last[k] = 0;
     const bool out = !(x < ws.width && yb + k < ws.height);
     thr[k] = out ? inf : lt;
+    stop_at[k] = out ? 0u : cnt;
     all_done &= out;
   }
 #pragma unroll
@@ -122,7 +126,11 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
         T[h] = mul2(T[h], fma2(ak, f2(-1.f), f2(1.f)));
         last[2 * h] = k0 ? nxt : last[2 * h];
         last[2 * h + 1] = k1 ? nxt : last[2 * h + 1];
-        if (STATS) n_blend += (uint32_t)k0 + (uint32_t)k1;
+        if (STATS) {
+          n_blend += (uint32_t)k0 + (uint32_t)k1;
+          stop_at[2 * h] = s0 ? nxt : stop_at[2 * h];
+          stop_at[2 * h + 1] = s1 ? nxt : stop_at[2 * h + 1];
+        }
       }
       // the thread leaves once all its pixels are done, checked every 8
       // Gaussians (a done pixel takes no part in the ones in between)
@@ -136,18 +144,23 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
   }
   const int64_t HW = (int64_t)ws.width * ws.height;
   if (STATS) {
-    unsigned long long ev = 0, bl = n_blend;
+    unsigned long long ev = 0, bl = n_blend, need = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) ev += last[k];
+    for (int k = 0; k < PPT; ++k) {
+      ev += last[k];
+      need += stop_at[k];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ev += __shfl_xor_sync(kFull, ev, o);
       bl += __shfl_xor_sync(kFull, bl, o);
+      need += __shfl_xor_sync(kFull, need, o);
     }
-    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ckpt) + 2 * v;
-    if ((threadIdx.x & 31) == 0 && ev) {
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ckpt) + 3 * v;
+    if ((threadIdx.x & 31) == 0 && need) {
       atomicAdd(counts, ev);
       atomicAdd(counts + 1, bl);
+      atomicAdd(counts + 2, need);
     }
     return;
   }
@@ -196,7 +209,7 @@ namespace gsb {
 
 cudaError_t launch_blend_counts(const gs_config& cfg, const Ws& ws, unsigned long long* counts, cudaStream_t st) {
   const unsigned ntiles = (unsigned)((int64_t)ws.views * ws.tiles_per_view);
-  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)ws.views * 2 * sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)ws.views * 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   k_render_fwd<kFwdPPT, false, true><<<ntiles, 256 / kFwdPPT, 0, st>>>(cfg, ws, nullptr, nullptr, nullptr, nullptr,
                                                                         nullptr, reinterpret_cast<float*>(counts));

@@ -82,13 +82,16 @@ def test_tiny_forward_tiles_and_images(oracle):
 
 def test_blend_counts_split_evaluations(oracle):
     """gs_blend_counts: per view, the evaluations up to each pixel's last
-    contributor (= sum of n_contrib) and how many of them were blended
-    (= the oracle's count of blended Gaussians per pixel, summed)."""
+    contributor (= sum of n_contrib), how many of them were blended (= the
+    oracle's count of blended Gaussians per pixel, summed), and the list
+    positions the pixels test: at least up to the last contributor, at most
+    the tile's whole list, and the whole list wherever a pixel keeps T above
+    the stop threshold to the end."""
     from paper_2507_04004_b300 import _native as N
     g, cams = _mapping_small(n=8000)
     m = host_map(g)
     rast, gm, ct, out = gpu_render(g, cams)
-    counts = torch.zeros(len(cams), 2, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(len(cams), 3, dtype=torch.int64, device="cuda")
     N.gs_blend_counts(rast.cfg, rast.ws, counts, torch.cuda.current_stream().cuda_stream)
     c = counts.cpu().numpy()
     for v, cam in enumerate(cams):
@@ -97,6 +100,16 @@ def test_blend_counts_split_evaluations(oracle):
         nflag = int((o["flags"] != 0).sum())
         assert abs(int(c[v, 1]) - int(o["n_contrib"].sum())) <= 8 * nflag, (v, c[v], int(o["n_contrib"].sum()), nflag)
         assert 0 < c[v, 1] <= c[v, 0]
+        # positions tested: per pixel between n_contrib and its tile's list length
+        H, W = out.n_contrib.shape[1:]
+        T = ((W + 15) // 16) * ((H + 15) // 16)
+        cnt = rast.tile_lists()[1][v * T:(v + 1) * T].to(torch.int64)
+        full = int(cnt.view((H + 15) // 16, (W + 15) // 16).repeat_interleave(16, 0).repeat_interleave(16, 1)[:H, :W].sum())
+        assert c[v, 0] <= c[v, 2] <= full
+        # a pixel whose T stays above 1e-4 / (1 - 0.99) = 0.01 cannot stop: it tests the whole list
+        t = out.t_final[v].cpu().numpy()
+        ln = cnt.view((H + 15) // 16, (W + 15) // 16).repeat_interleave(16, 0).repeat_interleave(16, 1)[:H, :W].cpu().numpy()
+        assert c[v, 2] >= int(ln[t >= 0.01].sum())
 
 
 def test_projection_records_match_oracle(oracle):
