@@ -53,6 +53,7 @@ static gs_status layout(int64_t n, const gs_frame* f, int64_t cap, gs_layout* L)
   L->row_items = take((size_t)cap * sizeof(uint32_t));
   L->row_span = take((size_t)cap * sizeof(uint32_t));
   L->sorted_ids = take((size_t)cap * sizeof(uint32_t));
+  // view_stats and work_fill stay adjacent: the blend backward clears both with one memset
   L->view_stats = take((size_t)V * 4 * sizeof(float));
   L->work_fill = take((size_t)kWorkClasses * sizeof(uint32_t));
   L->work_lists = take((size_t)kWorkClasses * (V * T) * sizeof(uint32_t));

@@ -44,7 +44,15 @@ __device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
   const int64_t seg = (n + NW - 1) / NW;
   const int64_t b = min(n, (int64_t)warp * seg), e = min(n, b + seg);
   unsigned long long s = 0;
-  for (int64_t i = b + lane; i < e; i += 32) s += count(i);
+  for (int64_t i0 = b; i0 < e; i0 += 128) {  // four loads in flight per lane
+    unsigned long long c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + 32 * j + lane;
+      c[j] = i < e ? count(i) : 0u;
+    }
+    s += c[0] + c[1] + c[2] + c[3];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   if (lane == 0) wbase[warp] = s;
@@ -62,20 +70,29 @@ __device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
   }
   __syncthreads();
   unsigned long long run = wbase[warp];
-  for (int64_t i0 = b; i0 < e; i0 += 32) {
-    const int64_t i = i0 + lane;
-    const unsigned long long c = i < e ? count(i) : 0u;
-    unsigned long long inc = c;
+  for (int64_t i00 = b; i00 < e; i00 += 128) {  // four loads in flight per lane, then four scans
+    unsigned long long cc[4];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc += y;
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i00 + 32 * j + lane;
+      cc[j] = i < e ? count(i) : 0u;
     }
-    if (i < e) {
-      const unsigned long long ex = run + inc - c;
-      start[i] = ex > 0xffffffffull ? 0xffffffffu : (uint32_t)ex;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i00 + 32 * j + lane;
+      const unsigned long long c = cc[j];
+      unsigned long long inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (i < e) {
+        const unsigned long long ex = run + inc - c;
+        start[i] = ex > 0xffffffffull ? 0xffffffffu : (uint32_t)ex;
+      }
+      run += __shfl_sync(kFull, inc, 31);
     }
-    run += __shfl_sync(kFull, inc, 31);
   }
   const unsigned long long total = wbase[NW];
   __syncthreads();

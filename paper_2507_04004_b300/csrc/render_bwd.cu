@@ -342,18 +342,25 @@ constexpr int kWorkItemsPerCta = kWorkThreads / 32 * kWorkPerWarp;
 // item's work from the tile's n_contrib words (a half-warp reads one pixel
 // row, 16 consecutive words); the CTA's items counted per class in shared
 // memory, one reservation per class of the CTA, then every item written to
-// its class list (fill counts cleared before).
-__global__ void __launch_bounds__(kWorkThreads) k_tile_work(Ws ws, const uint32_t* __restrict__ n_contrib) {
+// its class list (fill counts cleared before).  With tgt_depth given, the
+// same pass counts the valid LiDAR pixels (D_s > 0) of every view: |M_d| of
+// Eq. depth_loss, added to view_stats (cleared before).
+__global__ void __launch_bounds__(kWorkThreads) k_tile_work(Ws ws, const uint32_t* __restrict__ n_contrib,
+                                                            const float* __restrict__ tgt_depth) {
   __shared__ uint32_t s_cnt[kWorkClasses], s_base[kWorkClasses];
   __shared__ uint32_t s_cls[kWorkItemsPerCta], s_rank[kWorkItemsPerCta];
+  __shared__ uint32_t s_depth[2];  // valid depth pixels of the CTA's first view and the next one
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
   const int64_t first = (int64_t)blockIdx.x * kWorkItemsPerCta + (int64_t)warp * kWorkPerWarp;
+  const int v_cta = (int)((int64_t)blockIdx.x * kWorkItemsPerCta / ws.tiles_per_view);
   for (int c = threadIdx.x; c < kWorkClasses; c += kWorkThreads) s_cnt[c] = 0;
-  uint32_t w[kWorkPerWarp];
+  if (threadIdx.x < 2) s_depth[threadIdx.x] = 0;
+  uint32_t w[kWorkPerWarp], nd[kWorkPerWarp];
 #pragma unroll
   for (int q = 0; q < kWorkPerWarp; ++q) {
     w[q] = 0;
+    nd[q] = 0;
     const int64_t item = first + q;
     if (item >= items) continue;
     const int v = (int)(item / ws.tiles_per_view);
@@ -363,22 +370,34 @@ __global__ void __launch_bounds__(kWorkThreads) k_tile_work(Ws ws, const uint32_
 #pragma unroll
     for (int r = 0; r < kTile; r += 2) {
       const int y = ty * kTile + r + (lane >> 4);
-      if (x < ws.width && y < ws.height) w[q] = max(w[q], n_contrib[((int64_t)v * ws.height + y) * ws.width + x]);
+      if (x < ws.width && y < ws.height) {
+        const int64_t p = ((int64_t)v * ws.height + y) * ws.width + x;
+        w[q] = max(w[q], n_contrib[p]);
+        if (tgt_depth) nd[q] += tgt_depth[p] > 0.f ? 1u : 0u;
+      }
     }
   }
-  __syncthreads();  // s_cnt cleared
+  __syncthreads();  // s_cnt, s_depth cleared
 #pragma unroll
   for (int q = 0; q < kWorkPerWarp; ++q) {
     const uint32_t m = __reduce_max_sync(kFull, w[q]);
+    const uint32_t d = tgt_depth ? __reduce_add_sync(kFull, nd[q]) : 0u;
     const int64_t item = first + q;
     if (lane == 0 && item < items) {
       const int li = warp * kWorkPerWarp + q;
       const uint32_t c = work_class(min(m, ws.tile_count[item]));
       s_cls[li] = c;
       s_rank[li] = atomicAdd(&s_cnt[c], 1u);
+      if (d) {
+        const int v = (int)(item / ws.tiles_per_view);
+        if (v - v_cta < 2) atomicAdd(&s_depth[v - v_cta], d);
+        else atomicAdd(ws.view_stats + 4 * v + 1, (float)d);  // views of fewer tiles than a CTA's items
+      }
     }
   }
   __syncthreads();
+  if (tgt_depth && threadIdx.x < 2 && s_depth[threadIdx.x] && v_cta + (int)threadIdx.x < ws.views)
+    atomicAdd(ws.view_stats + 4 * (v_cta + threadIdx.x) + 1, (float)s_depth[threadIdx.x]);
   for (int c = threadIdx.x; c < kWorkClasses; c += kWorkThreads)
     if (s_cnt[c]) s_base[c] = atomicAdd(ws.work_fill + c, s_cnt[c]);
   __syncthreads();
@@ -787,14 +806,18 @@ static cudaError_t launch_blend_bwd(const gs_config& cfg, const Ws& ws, const Bw
 
 cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                               const BwdArgs& a, cudaStream_t st) {
-  cudaError_t err = launch_bwd_prologue(ws, a, st);
-  if (err != cudaSuccess) return err;
   const bool fused = a.tgt_rgb != nullptr;
   const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
   const bool dep = (fused && a.tgt_depth && a.w_depth != 0.f) || a.dl_ddepth || a.dl_dopac;
-  if ((err = cudaMemsetAsync(ws.work_fill, 0, kWorkClasses * sizeof(uint32_t), st)) != cudaSuccess) return err;
+  // per-view loss accumulators and valid-depth counts, then the work-list fill counts (adjacent in the layout)
+  const size_t cleared = (size_t)(reinterpret_cast<char*>(ws.work_fill + kWorkClasses) -
+                                  reinterpret_cast<char*>(ws.view_stats));
+  cudaError_t err = cudaMemsetAsync(ws.view_stats, 0, cleared, st);
+  if (err != cudaSuccess) return err;
+  const float* depth_count = fused && a.tgt_depth && a.w_depth != 0.f ? a.tgt_depth : nullptr;
   trace_begin(kKTileWork, st);
-  k_tile_work<<<(unsigned)((items + kWorkItemsPerCta - 1) / kWorkItemsPerCta), kWorkThreads, 0, st>>>(ws, a.n_contrib);
+  k_tile_work<<<(unsigned)((items + kWorkItemsPerCta - 1) / kWorkItemsPerCta), kWorkThreads, 0, st>>>(
+      ws, a.n_contrib, depth_count);
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   trace_begin(kKRenderBwd, st);
