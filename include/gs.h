@@ -468,6 +468,23 @@ const char* gs_status_str(gs_status s);
 /* Library version string ("gsb300 <major>.<minor>"). */
 const char* gs_version(void);
 
+/* Test support (no counterpart in the paper): the library's only device wait
+ * is the radix sort's look-back of a tile on the tiles before it (binning),
+ * bounded at 65536 polls, after which the sort's error word becomes
+ * GS_ERR_TIMEOUT and the pass goes on writing only in-range slots.
+ * gs_sort_wait_probe runs one pass of that sort on one CTA over a synthetic
+ * array of 4096 keys held in scratch_dev (caller-owned device memory of at
+ * least gs_sort_wait_probe_bytes() bytes, 16-byte aligned, overwritten).
+ * skip_first_tile != 0 starts the pass's tile tickets at 1, so no CTA ever
+ * takes tile 0 and the wait of tile 1 on it runs out (tens of milliseconds);
+ * otherwise the pass is an ordinary stable sort by the keys' low byte.  The
+ * pass's error word (GS_OK or GS_ERR_TIMEOUT) is copied to *status_dev
+ * (device int32).  Returns GS_ERR_ARG for a NULL or short or misaligned
+ * buffer; asynchronous on the stream otherwise. */
+size_t gs_sort_wait_probe_bytes(void);
+gs_status gs_sort_wait_probe(void* scratch_dev, size_t scratch_bytes, int32_t skip_first_tile, int32_t* status_dev,
+                             gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_pr
             "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
             "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_morton_scratch_bytes", "gs_morton_order", "gs_permute_rows",
-            "gs_trace_start",
+            "gs_sort_wait_probe_bytes", "gs_sort_wait_probe", "gs_trace_start",
             "gs_trace_stop",
             "gs_kernel_name", "gs_status_str", "gs_version")
 
@@ -124,6 +124,9 @@ def lib():
         L.gs_morton_scratch_bytes.restype = C.c_size_t
         L.gs_morton_order.argtypes = [P, I64, P, P, P]
         L.gs_permute_rows.argtypes = [P, P, I64, I64, I32, P, P]
+        L.gs_sort_wait_probe_bytes.argtypes = []
+        L.gs_sort_wait_probe_bytes.restype = C.c_size_t
+        L.gs_sort_wait_probe.argtypes = [P, C.c_size_t, I32, P, P]
         L.gs_trace_start.argtypes = [C.POINTER(C.c_void_p), I32, P]
         L.gs_trace_start.restype = I32
         L.gs_trace_stop.argtypes = []
@@ -137,7 +140,7 @@ def lib():
                      "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose",
                      "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes",
-                     "gs_morton_order", "gs_permute_rows"):
+                     "gs_morton_order", "gs_permute_rows", "gs_sort_wait_probe"):
             getattr(L, name).restype = I32
         _lib = L
     return _lib
@@ -335,3 +338,13 @@ _trace_keep: list = []
 
 def gs_version() -> str:
     return lib().gs_version().decode()
+
+
+def gs_sort_wait_probe_bytes() -> int:
+    return int(lib().gs_sort_wait_probe_bytes())
+
+
+def gs_sort_wait_probe(scratch, skip_first_tile: bool, status, stream: int) -> None:
+    check("gs_sort_wait_probe", lib().gs_sort_wait_probe(_ptr(scratch), int(scratch.numel() * scratch.element_size()),
+                                                         1 if skip_first_tile else 0, _ptr(status),
+                                                         C.c_void_p(stream)))
