@@ -9,7 +9,9 @@ camera image as 8-bit RGB, the LiDAR depth map as its valid pixels only
 expands both on the device, on the copy stream, into the FP32 planes the loss
 reads.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
 (projection, binning/sort, compositing, fused loss backward) over a batch of
-keyframes and returns the per-view loss as a pinned host tensor.
+keyframes and returns the per-view loss as a pinned host tensor; its device
+work is replayed from one CUDA graph per upload slot (captured on first use),
+so the ~30 launches and memsets of a step leave no gaps for the host to fill.
 """
 from __future__ import annotations
 
@@ -20,6 +22,28 @@ import torch
 
 from . import _native as N
 from .raster import GaussianMap, Grads, Rasterizer, RenderOut
+
+
+class GraphStep:
+    """A stream-ordered callable of fixed device buffers (no host reads, no
+    allocation), replayed from a CUDA graph: run twice on a side stream, then
+    captured.  replay() enqueues it on the current stream."""
+
+    def __init__(self, fn, device=None, warmup: int = 2):
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            fn()
+        torch.cuda.current_stream(dev).wait_stream(side)
+
+    def replay(self) -> None:
+        self.graph.replay()
 
 
 def pack_sparse_depth(depth: np.ndarray):
@@ -68,8 +92,9 @@ class HostKeyframes:
 class MappingStep:
     """Double-buffered host-to-device upload + one rasterizer pass per batch."""
 
-    def __init__(self, rast: Rasterizer, gmap: GaussianMap, w_rgb: float, w_depth: float):
+    def __init__(self, rast: Rasterizer, gmap: GaussianMap, w_rgb: float, w_depth: float, graphs: bool = True):
         self.rast, self.gmap, self.w_rgb, self.w_depth = rast, gmap, float(w_rgb), float(w_depth)
+        self.graphs = bool(graphs)
         V, H, W = rast.views, rast.height, rast.width
         dev = rast.device
         self.copy_stream = torch.cuda.Stream(device=dev)
@@ -116,16 +141,24 @@ class MappingStep:
         self.h2d_bytes = kf.nbytes()
         return slot
 
-    def step(self, slot: dict) -> torch.Tensor:
-        """One fwd+bwd pass on the current stream over an uploaded batch."""
-        cur = torch.cuda.current_stream(self.rast.device)
-        cur.wait_event(slot["ready"])
+    def _work(self, slot: dict) -> None:
         g = self.grads
         for t in (g.mean, g.log_scale, g.quat, g.logit_opacity, g.sh_dc, g.sh_rest, g.pose, g.loss):
             t.zero_()
         self.rast.render(self.gmap, slot["cams"], check=False, out=self.out)
         self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=slot["rgb"], tgt_depth=slot["depth"],
                            w_rgb=self.w_rgb, w_depth=self.w_depth, grads=g)
+
+    def step(self, slot: dict) -> torch.Tensor:
+        """One fwd+bwd pass on the current stream over an uploaded batch."""
+        cur = torch.cuda.current_stream(self.rast.device)
+        cur.wait_event(slot["ready"])
+        if self.graphs:
+            if "graph" not in slot:
+                slot["graph"] = GraphStep(lambda: self._work(slot), self.rast.device)
+            slot["graph"].replay()
+        else:
+            self._work(slot)
         slot["free"].record(cur)
-        self.loss_host.copy_(g.loss, non_blocking=True)
+        self.loss_host.copy_(self.grads.loss, non_blocking=True)
         return self.loss_host

@@ -73,7 +73,10 @@ def _batch(seed, w):
     return tgt, depth
 
 
-def test_mapping_step_matches_device_resident_pass():
+@pytest.mark.parametrize("graphs", [True, False])
+def test_mapping_step_matches_device_resident_pass(graphs):
+    """The host-fed step (eager, or replayed from a CUDA graph per upload
+    slot) gives the loss and gradients of the device-resident pass."""
     from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
     w = synth.mapping(n=20_000, width=160, height=96, focal=90.0, n_views=2, sh_degree=2)
     gm = GaussianMap.from_host(w.gmap)
@@ -90,11 +93,11 @@ def test_mapping_step_matches_device_resident_pass():
         return {k: getattr(g, k).cpu().numpy() for k in ("loss", "mean", "sh_dc", "logit_opacity", "pose")}
 
     refs = [resident(*b) for b in batches]
-    ms = MappingStep(rast, gm, w.w_rgb, w.w_depth)
+    ms = MappingStep(rast, gm, w.w_rgb, w.w_depth, graphs=graphs)
     kfs = [HostKeyframes.from_dense(synth.to_uint8(t), d, cams.cpu()) for t, d in batches]
     slots = [ms.upload(kf) for kf in kfs]          # both batches in flight
     assert ms.h2d_bytes == kfs[1].nbytes()
-    for slot, ref in zip(slots, refs):
+    for slot, ref in list(zip(slots, refs)) * 2:  # second round: graphs already captured
         loss = ms.step(slot)
         torch.cuda.synchronize()
         np.testing.assert_allclose(loss.numpy(), ref["loss"], rtol=1e-5)
