@@ -110,7 +110,7 @@ typedef struct {
 typedef struct {
   size_t counters;    /* uint32[16]: [0] status, [1] pairs (or row items) needed, [2] visible entries,
                          [3] entry units, [4] row items, [5] Gaussians in gauss_list, [6] row units,
-                         [8..13] tile tickets of the sort's passes */
+                         [8..13] tile tickets of the sort's passes, [15] chunk tickets of the projection */
   size_t records;     /* float4[E][3]: (mx, my, conic a, conic b), (conic c, opacity, depth, -), (r, g, b, -) */
   size_t rects;       /* uint32[E][2]: tile box (x0 | y0 << 16, x1 | y1 << 16), empty when x0 > x1 */
   size_t adjoints;    /* float4[E][3]: 2D adjoints (mx, my, a, b), (c, o, depth, -), (r, g, b, -) */

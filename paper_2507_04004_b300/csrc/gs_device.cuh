@@ -94,7 +94,8 @@ constexpr int kRadixTileEntries = 2048;
 
 enum CounterSlot {
   kStatus = 0, kPairsNeeded = 1, kVisibleCount = 2, kEntryUnits = 3, kRowCount = 4, kGaussCount = 5, kRowUnits = 6,
-  kRadixTicket = 8  // [8, 14): tile tickets of the sort's passes
+  kRadixTicket = 8,  // [8, 14): tile tickets of the sort's passes
+  kProjectTicket = 15  // chunk tickets of the projection
 };
 
 struct Cam {

@@ -84,7 +84,21 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
   // One thread per Gaussian, all views in turn: the parameters are read and
   // activated once, and the SH rows it reads again for later views are still
   // in cache.  Whole warps step together so that warp votes see all 32 lanes.
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+  // CTAs take chunks of blockDim.x Gaussians by ticket: with the map in a
+  // spatial order, a chunk is either mostly seen by some view or mostly not,
+  // so a static split would leave SMs idle at the end.  Thread 0 takes the
+  // next ticket when a chunk starts; the atomic's round trip overlaps it.
+  __shared__ uint32_t s_chunk;
+  uint32_t next_chunk = 0;
+  if (threadIdx.x == 0) next_chunk = atomicAdd(ws.counters + kProjectTicket, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_chunk = next_chunk;
+      next_chunk = atomicAdd(ws.counters + kProjectTicket, 1u);
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)s_chunk * blockDim.x;
+    if (base >= n) break;  // the whole CTA
     const int64_t g = base + threadIdx.x;
     const bool in_range = g < n;
     float mw[3] = {0.f, 0.f, 1.f};
@@ -305,6 +319,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
       slot = __shfl_sync(kFull, slot, leader);
       if (seen) ws.gauss_list[slot + __popc(sn & ((1u << lane) - 1u))] = (uint32_t)g;
     }
+    __syncthreads();  // every thread has read s_chunk before thread 0 rewrites it
   }
   if (smem_buckets) {
     __syncthreads();
@@ -317,7 +332,7 @@ template <int DEG, bool BF16>
 static cudaError_t launch_project_t(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                     cudaStream_t st) {
   const int64_t need = (ws.n + 255) / 256;
-  const int64_t cap = (int64_t)sm_count() * 6;
+  const int64_t cap = (int64_t)sm_count() * 3;  // the CTAs resident at once (registers: 3 per SM)
   const unsigned grid = (unsigned)(need < cap ? need : cap);
   const size_t smem = (BF16 ? 0 : (size_t)3 * (DEG + 1) * (DEG + 1) * 256 * sizeof(float)) +
                       (size_t)kCamChunk * kCamF4 * sizeof(float4) +
