@@ -38,39 +38,47 @@ __global__ void __launch_bounds__(256) k_count_depth(const float* __restrict__ t
   }
 }
 
-// Warp reduce-scatter of 10 values: after the call, lane l with (l & 1) == 0
-// and *slot >= 0 holds the warp-wide sum of value *slot (10 lanes in all).
-__device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int lane, int* slot) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+// 1 / x on the special-function unit (PTX rcp.approx.ftz.f32, relative
+// error near 2^-23).  The backward divides only by 1 - alpha, which lies in
+// [1 - alpha_max, 1], so no range handling is needed around it.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The backward's per-Gaussian sums leave the warp through shared memory:
+// every lane writes its 10 partial sums of a Gaussian to s_part[slot][lane]
+// (rows of 12 floats, so a quarter-warp's 16-byte stores hit 32 distinct
+// banks), and every kRedGroup Gaussians the warp reduces the group at once,
+// 8 lanes per Gaussian (lane = 8 g + s, each lane summing the rows of lanes
+// s, s + 8, s + 16, s + 24), then a reduce-scatter over the 8 lanes.
+constexpr int kRedGroup = 4;
+constexpr int kRedRow = 12;
+
+// Reduce-scatter of 10 values over the 8 lanes s = lane & 7 of a group
+// (butterflies over lane bits 2, 1, 0).  Afterwards lane s holds in y0 / y1
+// the 8-lane sums of values: s=0: 0, 1; s=1: 2; s=2: 3, 4; s=4: 5, 6;
+// s=5: 7; s=6: 8, 9 (the other slots hold nothing meaningful).
+__device__ __forceinline__ void group8_reduce_scatter10(const float v[10], int s, float* y0, float* y1) {
+  const bool b2 = s & 4, b1 = s & 2, b0 = s & 1;
   float w[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const float keep = b4 ? v[i + 5] : v[i];
-    const float send = b4 ? v[i] : v[i + 5];
-    w[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    const float keep = b2 ? v[i + 5] : v[i];
+    const float send = b2 ? v[i] : v[i + 5];
+    w[i] = keep + __shfl_xor_sync(kFull, send, 4);
   }
   float x[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float hi = (i + 3 < 5) ? w[i + 3] : 0.f;
-    const float keep = b3 ? hi : w[i];
-    const float send = b3 ? w[i] : hi;
-    x[i] = keep + __shfl_xor_sync(kFull, send, 8);
-  }
-  float y[2];
-#pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float hi = (i + 2 < 3) ? x[i + 2] : 0.f;
-    const float keep = b2 ? hi : x[i];
-    const float send = b2 ? x[i] : hi;
-    y[i] = keep + __shfl_xor_sync(kFull, send, 4);
+    const float keep = b1 ? w[i + 3] : w[i];
+    const float send = b1 ? w[i] : w[i + 3];
+    x[i] = keep + __shfl_xor_sync(kFull, send, 2);
   }
-  float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(kFull, b1 ? y[0] : y[1], 2);
-  z += __shfl_xor_sync(kFull, z, 1);
-  const int idx3 = (b2 ? 2 : 0) + (b1 ? 1 : 0);
-  const bool valid = idx3 < (b3 ? 2 : 3);
-  *slot = valid ? (b4 ? 5 : 0) + (b3 ? 3 : 0) + idx3 : -1;
-  return z;
+  x[2] = (b1 ? 0.f : w[2]) + __shfl_xor_sync(kFull, b1 ? w[2] : 0.f, 2);
+  *y0 = (b0 ? x[2] : x[0]) + __shfl_xor_sync(kFull, b0 ? x[0] : x[2], 1);
+  *y1 = (b0 ? 0.f : x[1]) + __shfl_xor_sync(kFull, b0 ? x[1] : 0.f, 1);
 }
 
 // One (view, tile) item of the blend backward.  DEP: the pixel adjoints of
@@ -82,10 +90,13 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
   // a thread owns PPT vertically adjacent pixels; a warp covers a 16 x (2 PPT) block
-  constexpr int NB = kBwdBatch;  // Gaussians staged per batch
+  // Gaussians staged per batch (fewer without the depth terms, whose
+  // lighter register use lets more CTAs share an SM's shared memory)
+  constexpr int NB = DEP ? kBwdBatch : kBwdBatch * 3 / 4;
   __shared__ float4 s_g0[NB], s_g1[NB], s_c[NB];
   __shared__ uint32_t s_gid[NB];
-  __shared__ float s_acc[NB][10];
+  static_assert(NW == 1, "the per-Gaussian sums are reduced by the tile's only warp");
+  __shared__ __align__(16) float s_part[kRedGroup][32][kRedRow];
   __shared__ float s_red[NW];
   __shared__ uint32_t s_max[NW];
   const int v = (int)(tile / ws.tiles_per_view);
@@ -209,8 +220,6 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
       s_g0[i] = sg.g0;
       s_g1[i] = sg.g1;
       s_c[i] = r[2];
-#pragma unroll
-      for (int q = 0; q < 10; ++q) s_acc[i][q] = 0.f;
     }
     __syncthreads();
 #pragma unroll 2
@@ -230,7 +239,8 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
         ea[h] = make_float2(a0 ? e0 : 0.f, a1 ? e1 : 0.f);
         any |= a0 | a1;
       }
-      if (!__any_sync(kFull, any)) continue;
+      float val[10];  // this lane's partial sums of the Gaussian (zero when no pixel of the warp takes part)
+      if (__any_sync(kFull, any)) {
       // Per-Gaussian sums over this thread's pixels.  With dp = dL/dpower
       // (power = -q/2, zero where alpha is clamped), the conic and opacity
       // gradients need only the moments of dp; their constant factors are
@@ -261,18 +271,18 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
         // (up to the approximate reciprocal's one-ulp bound)
         const float2 om = fma2(al, f2(-1.f), f2(1.f));
         // transmittance in front of this Gaussian
-        T2[h] = mul2(T2[h], make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y)));
+        T2[h] = mul2(T2[h], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
         const float2 w = mul2(al, T2[h]);
         const float2 gx = DEP ? fma2(C0[h], cr, fma2(C1[h], cg, fma2(C2[h], cb, mul2(GD[h], dep))))
                               : fma2(C0[h], cr, fma2(C1[h], cg, mul2(C2[h], cb)));
         const float2 e = fma2(S2[h], f2(-1.f), gx);
-        const float2 dA = mul2(T2[h], e);  // dL/dalpha
         S2[h] = fma2(al, e, S2[h]);
         if (DEP) v6 = fma2(GD[h], w, v6);
         v7 = fma2(C0[h], w, v7);
         v8 = fma2(C1[h], w, v8);
         v9 = fma2(C2[h], w, v9);
-        const float2 dp = mul2(dA, ag);
+        // dp = dL/dalpha alpha with dL/dalpha = T e; unclamped, that is w e
+        const float2 dp = decltype(clamp)::value ? mul2(mul2(T2[h], e), ag) : mul2(w, e);
         M0 = add2(M0, dp);
         M1 = fma2(dp, make_float2((float)(2 * h), (float)(2 * h + 1)), M1);
         M2 = fma2(dp, make_float2((float)(4 * h * h), (float)((2 * h + 1) * (2 * h + 1))), M2);
@@ -283,7 +293,6 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
       // of p2): other Gaussians take the path without it
       if (g1.y > clamp_from) walk(std::true_type{});
       else walk(std::false_type{});
-      float val[10];
       const float m0 = M0.x + M0.y, m1 = M1.x + M1.y, m2 = M2.x + M2.y;
       const float dy0 = Y[0].x - g0.y;
       const float sy = fmaf(dy0, m0, m1);  // sum dp dy
@@ -297,27 +306,63 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
       val[7] = v7.x + v7.y;
       val[8] = v8.x + v8.y;
       val[9] = v9.x + v9.y;
-      int slot;
-      const float sum = warp_reduce_scatter10(val, lane, &slot);
-      if (NW == 1) {  // the tile's only warp owns the slots: plain stores
-        if (slot >= 0 && (lane & 1) == 0) s_acc[j][slot] = sum;
-      } else if (slot >= 0 && (lane & 1) == 0 && sum != 0.f) {
-        atomicAdd(&s_acc[j][slot], sum);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) val[q] = 0.f;
       }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += NT) {
-      const float* q = s_acc[i];
-      const float4 g0 = s_g0[i], g1 = s_g1[i];
-      // d power / d mx = a dx + b dy, with a = -2 ln2 ha, b = -ln2 hb, c = -2 ln2 hc;
-      // d power / d(a, b, c) = (-dx^2/2, -dx dy, -dy^2/2); d alpha / d o = alpha / o
-      const float gmx = -kLn2 * (2.f * g0.z * q[0] + g0.w * q[1]);
-      const float gmy = -kLn2 * (g0.w * q[0] + 2.f * g1.x * q[1]);
-      const float ga = -0.5f * q[2], gb = -q[3], gc = -0.5f * q[4], go = q[5] * g1.w;
-      float4* dst = adj + 3 * (int64_t)s_gid[i];
-      if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f) atomicAdd(dst, make_float4(gmx, gmy, ga, gb));
-      if (q[4] != 0.f || q[5] != 0.f || q[6] != 0.f) atomicAdd(dst + 1, make_float4(gc, go, q[6], 0.f));
-      if (q[7] != 0.f || q[8] != 0.f || q[9] != 0.f) atomicAdd(dst + 2, make_float4(q[7], q[8], q[9], 0.f));
+      // slot of this Gaussian in its group (groups start at the batch's last Gaussian)
+      const int gs = (nb - 1 - j) & (kRedGroup - 1);
+      float* row = &s_part[gs][lane][0];
+      *reinterpret_cast<float4*>(row) = make_float4(val[0], val[1], val[2], val[3]);
+      *reinterpret_cast<float4*>(row + 4) = make_float4(val[4], val[5], val[6], val[7]);
+      *reinterpret_cast<float2*>(row + 8) = make_float2(val[8], val[9]);
+      if (gs == kRedGroup - 1 || j == 0) {
+        // the group's Gaussians: slot g holds staged Gaussian j + gs - g
+        __syncwarp();
+        const int g = lane >> 3, s = lane & 7;
+        const bool mine = g <= gs;
+        float2 acc2[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc2[q] = f2(0.f);
+        if (mine) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float* src = &s_part[g][s + 8 * k][0];
+            const float4 u0 = *reinterpret_cast<const float4*>(src);
+            const float4 u1 = *reinterpret_cast<const float4*>(src + 4);
+            const float2 u2 = *reinterpret_cast<const float2*>(src + 8);
+            acc2[0] = add2(acc2[0], make_float2(u0.x, u0.y));
+            acc2[1] = add2(acc2[1], make_float2(u0.z, u0.w));
+            acc2[2] = add2(acc2[2], make_float2(u1.x, u1.y));
+            acc2[3] = add2(acc2[3], make_float2(u1.z, u1.w));
+            acc2[4] = add2(acc2[4], u2);
+          }
+        }
+        const float acc[10] = {acc2[0].x, acc2[0].y, acc2[1].x, acc2[1].y, acc2[2].x,
+                               acc2[2].y, acc2[3].x, acc2[3].y, acc2[4].x, acc2[4].y};
+        float y0, y1;
+        group8_reduce_scatter10(acc, s, &y0, &y1);
+        // gather each atomic's values into one lane: s=0 takes values 2 (from
+        // s=1) and 3 (s=2); s=4 takes value 4 (s=2); s=6 takes value 7 (s=5)
+        const float h1 = __shfl_sync(kFull, y0, lane + (s == 0 ? 1 : (s == 6 ? -1 : 0)));
+        const float h2 = __shfl_sync(kFull, y0, lane + (s == 0 ? 2 : 0));
+        const float h3 = __shfl_sync(kFull, y1, lane - (s == 4 ? 2 : 0));
+        // lanes s = 0, 4, 6 add parts 0, 1, 2 of the Gaussian's adjoint record
+        // (branch-free: the three roles differ only in selects)
+        const int jg = mine ? j + gs - g : j;
+        const float4 q0 = s_g0[jg], q1 = s_g1[jg];
+        const uint32_t gid = s_gid[jg];
+        const bool r0 = s == 0, r1 = s == 4;
+        // d power / d mx = a dx + b dy, with a = -2 ln2 ha, b = -ln2 hb, c = -2 ln2 hc;
+        // d power / d(a, b, c) = (-dx^2/2, -dx dy, -dy^2/2); d alpha / d o = alpha / o
+        const float gmx = -kLn2 * (2.f * q0.z * y0 + q0.w * y1);
+        const float gmy = -kLn2 * (q0.w * y0 + 2.f * q1.x * y1);
+        const float4 out = make_float4(r0 ? gmx : (r1 ? -0.5f * h3 : h1), r0 ? gmy : (r1 ? y0 * q1.w : y0),
+                                       r0 ? -0.5f * h1 : y1, r0 ? -h2 : 0.f);
+        if (mine && (r0 || r1 || s == 6) && (out.x != 0.f || out.y != 0.f || out.z != 0.f || out.w != 0.f))
+          atomicAdd(adj + 3 * (int64_t)gid + (s + 2) / 4, out);
+        __syncwarp();
+      }
     }
   }
 }
