@@ -304,6 +304,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Four-float reduction into global memory with no value returned (PTX
+// red.global.add.v4.f32): unlike an atomic whose result registers must be
+// written back before they are reused, nothing in the issuing warp waits for it.
+__device__ __forceinline__ void red_add4(float4* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
 // Asynchronous 4-byte global -> shared copies (cp.async), their commit and
 // the wait for all of a thread's outstanding copies.
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {

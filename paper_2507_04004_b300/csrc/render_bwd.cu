@@ -222,8 +222,13 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
       s_c[i] = r[2];
     }
     __syncthreads();
-#pragma unroll 2
-    for (int j = nb - 1; j >= 0; --j) {
+    // groups of kRedGroup Gaussians, back to front; slot gs of a group holds
+    // staged Gaussian j0 - gs
+    for (int j0 = nb - 1; j0 >= 0; j0 -= kRedGroup) {
+#pragma unroll
+    for (int gs = 0; gs < kRedGroup; ++gs) {
+      const int j = j0 - gs;
+      if (j < 0) break;
       const float4 g0 = s_g0[j], g1 = s_g1[j];
       const uint32_t pos = (uint32_t)(beg + j);
       const float dx = px - g0.x;
@@ -310,17 +315,16 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
 #pragma unroll
         for (int q = 0; q < 10; ++q) val[q] = 0.f;
       }
-      // slot of this Gaussian in its group (groups start at the batch's last Gaussian)
-      const int gs = (nb - 1 - j) & (kRedGroup - 1);
       float* row = &s_part[gs][lane][0];
       *reinterpret_cast<float4*>(row) = make_float4(val[0], val[1], val[2], val[3]);
       *reinterpret_cast<float4*>(row + 4) = make_float4(val[4], val[5], val[6], val[7]);
       *reinterpret_cast<float2*>(row + 8) = make_float2(val[8], val[9]);
-      if (gs == kRedGroup - 1 || j == 0) {
-        // the group's Gaussians: slot g holds staged Gaussian j + gs - g
+    }
+      {
+        const int filled = min(kRedGroup, j0 + 1);  // Gaussians of this group
         __syncwarp();
         const int g = lane >> 3, s = lane & 7;
-        const bool mine = g <= gs;
+        const bool mine = g < filled;
         float2 acc2[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc2[q] = f2(0.f);
@@ -349,7 +353,7 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
         const float h3 = __shfl_sync(kFull, y1, lane - (s == 4 ? 2 : 0));
         // lanes s = 0, 4, 6 add parts 0, 1, 2 of the Gaussian's adjoint record
         // (branch-free: the three roles differ only in selects)
-        const int jg = mine ? j + gs - g : j;
+        const int jg = mine ? j0 - g : j0;
         const float4 q0 = s_g0[jg], q1 = s_g1[jg];
         const uint32_t gid = s_gid[jg];
         const bool r0 = s == 0, r1 = s == 4;
@@ -360,7 +364,7 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
         const float4 out = make_float4(r0 ? gmx : (r1 ? -0.5f * h3 : h1), r0 ? gmy : (r1 ? y0 * q1.w : y0),
                                        r0 ? -0.5f * h1 : y1, r0 ? -h2 : 0.f);
         if (mine && (r0 || r1 || s == 6) && (out.x != 0.f || out.y != 0.f || out.z != 0.f || out.w != 0.f))
-          atomicAdd(adj + 3 * (int64_t)gid + (s + 2) / 4, out);
+          red_add4(adj + 3 * (int64_t)gid + (s + 2) / 4, out);
         __syncwarp();
       }
     }

@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(32 * kBkWarps, 6) k_render_bwd_bucket(gs_confi
       const float gmy = -kLn2 * (g0.w * q0 + 2.f * g1.x * q1);
       const float ga = -0.5f * q2, gb = -q3, gc = -0.5f * q4, go = q5 * g1.w;
       float4* dst = adj + 3 * (int64_t)gid;
-      if (q0 != 0.f || q1 != 0.f || q2 != 0.f || q3 != 0.f) atomicAdd(dst, make_float4(gmx, gmy, ga, gb));
-      if (q4 != 0.f || q5 != 0.f || v6 != 0.f) atomicAdd(dst + 1, make_float4(gc, go, v6, 0.f));
-      if (v7 != 0.f || v8 != 0.f || v9 != 0.f) atomicAdd(dst + 2, make_float4(v7, v8, v9, 0.f));
+      if (q0 != 0.f || q1 != 0.f || q2 != 0.f || q3 != 0.f) red_add4(dst, make_float4(gmx, gmy, ga, gb));
+      if (q4 != 0.f || q5 != 0.f || v6 != 0.f) red_add4(dst + 1, make_float4(gc, go, v6, 0.f));
+      if (v7 != 0.f || v8 != 0.f || v9 != 0.f) red_add4(dst + 2, make_float4(v7, v8, v9, 0.f));
     }
   }
 }
