@@ -84,7 +84,13 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
       s_c[i] = r[2];
     }
     __syncthreads();
-    for (uint32_t j = 0; j < nb && !all_done; ++j) {
+    // groups of 8 Gaussians; the thread leaves once all its pixels are done,
+    // checked after each group (a done pixel takes no part in the ones in between)
+    for (uint32_t j0 = 0; j0 < nb && !all_done; j0 += 8) {
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      const uint32_t j = j0 + u;
+      if (j >= nb) break;
       if (CKPT && ((b0 + j) & 31u) == 0) {
         float* ck = ckpt + ((int64_t)(start >> 5) + tile + ((b0 + j) >> 5)) * (5 * 256);
 #pragma unroll
@@ -132,13 +138,10 @@ __global__ void __launch_bounds__(256 / PPT) k_render_fwd(gs_config cfg, Ws ws, 
           stop_at[2 * h + 1] = s1 ? nxt : stop_at[2 * h + 1];
         }
       }
-      // the thread leaves once all its pixels are done, checked every 8
-      // Gaussians (a done pixel takes no part in the ones in between)
-      if ((j & 7u) == 7u || j + 1 == nb) {
-        all_done = true;
+    }
+      all_done = true;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) all_done &= thr[k] == inf;
-      }
+      for (int k = 0; k < PPT; ++k) all_done &= thr[k] == inf;
     }
     // pixels whose list ended are done only when the whole list is walked
   }
