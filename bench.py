@@ -488,9 +488,7 @@ def run_bucket_backward(args, rast0, gm, cams, tgt_rgb, tgt_depth, w, k_blend, k
     grads = rast.new_grads(gm)
 
     def step():
-        for t in (grads.mean, grads.log_scale, grads.quat, grads.logit_opacity, grads.sh_dc, grads.sh_rest,
-                  grads.pose, grads.loss):
-            t.zero_()
+        grads.zero_()
         rast.render(gm, cams, check=False, out=out)
         rast.backward(gm, cams, out, tgt_rgb=tgt_rgb, tgt_depth=tgt_depth, w_rgb=w.w_rgb, w_depth=w.w_depth,
                       grads=grads)
@@ -735,9 +733,7 @@ def run_ours(args):
     grads = rast.new_grads(gm)
 
     def step():
-        for t in (grads.mean, grads.log_scale, grads.quat, grads.logit_opacity, grads.sh_dc, grads.sh_rest,
-                  grads.pose, grads.loss):
-            t.zero_()
+        grads.zero_()
         rast.render(gm, cams, check=False, out=out)
         rast.backward(gm, cams, out, tgt_rgb=tgt_rgb, tgt_depth=tgt_depth, w_rgb=w.w_rgb, w_depth=w.w_depth,
                       grads=grads)

@@ -143,8 +143,7 @@ class MappingStep:
 
     def _work(self, slot: dict) -> None:
         g = self.grads
-        for t in (g.mean, g.log_scale, g.quat, g.logit_opacity, g.sh_dc, g.sh_rest, g.pose, g.loss):
-            t.zero_()
+        g.zero_()
         self.rast.render(self.gmap, slot["cams"], check=False, out=self.out)
         self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=slot["rgb"], tgt_depth=slot["depth"],
                            w_rgb=self.w_rgb, w_depth=self.w_depth, grads=g)

@@ -133,6 +133,17 @@ class Grads:
     sh_rest: torch.Tensor
     pose: torch.Tensor       # [V][6]
     loss: torch.Tensor       # [V]
+    flat: torch.Tensor | None = None  # one buffer holding all of the above (new_grads), else None
+
+    def zero_(self) -> "Grads":
+        """Clears every gradient: one fill of the shared buffer when there is one."""
+        if self.flat is not None:
+            self.flat.zero_()
+        else:
+            for t in (self.mean, self.log_scale, self.quat, self.logit_opacity, self.sh_dc, self.sh_rest,
+                      self.pose, self.loss):
+                t.zero_()
+        return self
 
 
 class Rasterizer:
@@ -249,11 +260,19 @@ class Rasterizer:
         return out
 
     def new_grads(self, gmap: GaussianMap) -> Grads:
-        f = dict(device=self.device, dtype=torch.float32)
+        """Zeroed gradient buffers, all views of one allocation (each part
+        starting on a 256-byte boundary), so that Grads.zero_ clears them in
+        one fill."""
         K = (gmap.sh_degree + 1) ** 2
-        return Grads(torch.zeros(3, self.n, **f), torch.zeros(3, self.n, **f), torch.zeros(4, self.n, **f),
-                     torch.zeros(self.n, **f), torch.zeros(3, self.n, **f), torch.zeros(K - 1, 3, self.n, **f),
-                     torch.zeros(self.views, 6, **f), torch.zeros(self.views, **f))
+        shapes = [(3, self.n), (3, self.n), (4, self.n), (self.n,), (3, self.n), (K - 1, 3, self.n),
+                  (self.views, 6), (self.views,)]
+        sizes = [int(np.prod(sh)) for sh in shapes]
+        offs = [0]
+        for sz in sizes:
+            offs.append(offs[-1] + (sz + 63) // 64 * 64)
+        flat = torch.zeros(offs[-1], device=self.device, dtype=torch.float32)
+        parts = [flat[o:o + sz].view(*sh) for o, sz, sh in zip(offs, sizes, shapes)]
+        return Grads(*parts, flat=flat)
 
     def backward(self, gmap: GaussianMap, cams: torch.Tensor, out: RenderOut, tgt_rgb=None, tgt_depth=None,
                  w_rgb: float = 1.0, w_depth: float = 0.0, dl_drgb=None, dl_ddepth=None, dl_dopac=None,
