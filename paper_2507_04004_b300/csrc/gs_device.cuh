@@ -304,6 +304,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// 1 / x on the special-function unit (PTX rcp.approx.ftz.f32, relative
+// error near 2^-23).  The backward kernels divide only by 1 - alpha, which
+// lies in [1 - alpha_max, 1], so no range handling is needed around it.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Four-float reduction into global memory with no value returned (PTX
 // red.global.add.v4.f32): unlike an atomic whose result registers must be
 // written back before they are reused, nothing in the issuing warp waits for it.

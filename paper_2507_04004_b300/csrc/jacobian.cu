@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(128) k_pose_jacobian(gs_map map, const gs_came
     pose_tangents<DEG, BF16>(map, gid, cam, cfg, ws.width, ws.height, r0, r1, tg);
     const float dx = px - r0.x, dy = py - r0.y;
     const float w = al * T;
+    const float inv_om = rcp_approx(__fsub_rn(1.f, al));  // 1 - alpha >= 1 - alpha_max
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       float dal = 0.f;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128) k_pose_jacobian(gs_map map, const gs_came
       const float dT = -T * S[i];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) dC[ch][i] += tg.col[ch][i] * w + col[ch] * (dal * T + al * dT);
-      S[i] += dal / (1.f - al);
+      S[i] += dal * inv_om;
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) C[ch] += col[ch] * w;

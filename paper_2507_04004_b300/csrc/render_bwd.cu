@@ -38,15 +38,6 @@ __global__ void __launch_bounds__(256) k_count_depth(const float* __restrict__ t
   }
 }
 
-// 1 / x on the special-function unit (PTX rcp.approx.ftz.f32, relative
-// error near 2^-23).  The backward divides only by 1 - alpha, which lies in
-// [1 - alpha_max, 1], so no range handling is needed around it.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // The backward's per-Gaussian sums leave the warp through shared memory:
 // every lane writes its 10 partial sums of a Gaussian to s_part[slot][lane]
 // (rows of 12 floats, so a quarter-warp's 16-byte stores hit 32 distinct

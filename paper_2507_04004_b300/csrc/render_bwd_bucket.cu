@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(32 * kBkWarps, 6) k_render_bwd_bucket(gs_confi
           A = fma2(aT, wg, A);
           const float2 om = fma2(al, f2(-1.f), f2(1.f));
           const float2 behind = fma2(A, f2(-1.f), make_float2(a2.z, a2.w));  // a.Y - A
-          const float2 dA = fma2(mul2(behind, make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y))), f2(-1.f),
+          const float2 dA = fma2(mul2(behind, make_float2(rcp_approx(om.x), rcp_approx(om.y))), f2(-1.f),
                                  mul2(T, wg));
           T = mul2(T, om);
           const float2 dp = mul2(dA, ag);
