@@ -493,6 +493,145 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
 // partials are reduced per view across the CTA.
 constexpr int kPoseSmemViews = 256;  // per-CTA pose sums in shared memory up to this many views
 
+// The chain rule of one (view, Gaussian) entry: its 2D adjoints A0-A2 (mean,
+// conic, opacity, depth, colour) through the projection of Sec. "3D Gaussian
+// Splatting Representation" to the Gaussian's mean, scale, rotation, opacity
+// and SH coefficients (added to g_* and, per coefficient q, through
+// gsh_add(q, value), when PARAMS) and, when want_pose, to the view's six pose
+// terms under the right perturbation T Exp(xi) (Eq. 3dgs_jacobi), written to
+// pose[].  R0, R1: the entry's record (the conic the forward used); mu, s, Rg:
+// the Gaussian's mean, scales and rotation; sh(k, ch): its SH coefficient k of
+// colour channel ch.
+template <int DEG, bool PARAMS, class ShAt, class ShGradAdd>
+__device__ __forceinline__ void entry_chain(const Cam& cam, const gs_config& cfg, int width, int height,
+                                            const float (&mu)[3], const float (&s)[3], const float (&Rg)[3][3],
+                                            float4 R0, float4 R1, float4 A0, float4 A1, float4 A2, ShAt sh,
+                                            ShGradAdd gsh_add, float (&g_mu)[3], float (&g_s)[3], float (&g_R)[3][3],
+                                            float& g_o, bool want_pose, float* pose) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
+  const float gcol[3] = {A2.x, A2.y, A2.z};
+  const float3 mh = to_camera(cam, mu[0], mu[1], mu[2]);
+  const float iz = 1.f / mh.z;
+  const float limx = cfg.fov_clamp * 0.5f * (float)width / cam.fx;
+  const float limy = cfg.fov_clamp * 0.5f * (float)height / cam.fy;
+  const float txr = mh.x * iz, tyr = mh.y * iz;
+  const bool clx = txr > limx || txr < -limx, cly = tyr > limy || tyr < -limy;
+  const float txc = fminf(limx, fmaxf(-limx, txr)), tyc = fminf(limy, fmaxf(-limy, tyr));
+  const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz, j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
+  float m0[3], m1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
+    m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
+  }
+  float U[3], Vv[3], rm0[3], rm1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    rm0[k] = Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2];
+    rm1[k] = Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2];
+    U[k] = s[k] * rm0[k];
+    Vv[k] = s[k] * rm1[k];
+  }
+  // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
+  const float qa = R0.z, qb = R0.w, qc = R1.x;
+  // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
+  const float hb = 0.5f * gb;
+  const float P00 = qa * ga + qb * hb, P01 = qa * hb + qb * gc, P10 = qb * ga + qc * hb, P11 = qb * hb + qc * gc;
+  const float gA = -(P00 * qa + P01 * qb);
+  const float gBh = -(P00 * qb + P01 * qc);  // d/dSigma'_01 (one of the two symmetric entries)
+  const float gCc = -(P10 * qb + P11 * qc);
+  const float gB = 2.f * gBh;
+  // A = U.U + dil, B = U.V, C = V.V + dil
+  float gU[3], gV[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gU[k] = 2.f * gA * U[k] + gB * Vv[k];
+    gV[k] = gB * U[k] + 2.f * gCc * Vv[k];
+  }
+  float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (PARAMS) g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (PARAMS) g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
+      gm0[i] += s[k] * gU[k] * Rg[i][k];
+      gm1[i] += s[k] * gV[k] * Rg[i][k];
+    }
+  }
+  // m0 = R^T J0, m1 = R^T J1  ->  dL/dJ0 = R gm0, dL/dJ1 = R gm1
+  float gJ0[3], gJ1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gJ0[i] = cam.R[3 * i] * gm0[0] + cam.R[3 * i + 1] * gm0[1] + cam.R[3 * i + 2] * gm0[2];
+    gJ1[i] = cam.R[3 * i] * gm1[0] + cam.R[3 * i + 1] * gm1[1] + cam.R[3 * i + 2] * gm1[2];
+  }
+  const float iz2 = iz * iz;
+  float gx = gmx * cam.fx * iz, gy = gmy * cam.fy * iz;
+  float gz = gdep - gmx * cam.fx * mh.x * iz2 - gmy * cam.fy * mh.y * iz2;
+  gz += -gJ0[0] * cam.fx * iz2 - gJ1[1] * cam.fy * iz2;
+  // J02 = -fx txc / z: unclamped txc = x/z, clamped txc constant
+  gz += gJ0[2] * cam.fx * txc * iz2 * (clx ? 1.f : 2.f);
+  if (!clx) gx += -gJ0[2] * cam.fx * iz2;
+  gz += gJ1[2] * cam.fy * tyc * iz2 * (cly ? 1.f : 2.f);
+  if (!cly) gy += -gJ1[2] * cam.fy * iz2;
+  // dL/dmu through mu_hat = R mu + t
+  float gWm[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) gWm[j] = cam.R[j] * gx + cam.R[3 + j] * gy + cam.R[6 + j] * gz;
+  // colour: raw = sum_k SH_k Y_k(dir) + 0.5, clamped at 0
+  const float3 cw = camera_centre(cam);
+  float dv[3] = {mu[0] - cw.x, mu[1] - cw.y, mu[2] - cw.z};
+  const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
+  float Y[16];
+  sh_basis<DEG>(dx, dy, dz, Y);
+  float graw[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float raw = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) raw += sh(k, ch) * Y[k];
+    graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (PARAMS) gsh_add(3 * k + ch, graw[ch] * Y[k]);
+  }
+  // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
+  float wk[16];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    wk[k] = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * sh(k, ch);
+  }
+  const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
+  const float gdir[3] = {gd3.x, gd3.y, gd3.z};
+  const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
+  const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    if (PARAMS) g_mu[j] += gWm[j] + gv[j];
+  if (PARAMS) g_o += gop;
+  if (want_pose) {
+    // right perturbation T Exp(xi), xi = (rho, theta):
+    //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
+    const float gcw[3] = {-gv[0], -gv[1], -gv[2]};
+    pose[0] = gWm[0] - gcw[0];
+    pose[1] = gWm[1] - gcw[1];
+    pose[2] = gWm[2] - gcw[2];
+    // theta: mu x (R^T g_mu_hat) + gm0 x m0 + gm1 x m1 + g_cw x c_w
+    const float c_w[3] = {cw.x, cw.y, cw.z};
+    pose[3] = mu[1] * gWm[2] - mu[2] * gWm[1] + gm0[1] * m0[2] - gm0[2] * m0[1] + gm1[1] * m1[2] -
+              gm1[2] * m1[1] + gcw[1] * c_w[2] - gcw[2] * c_w[1];
+    pose[4] = mu[2] * gWm[0] - mu[0] * gWm[2] + gm0[2] * m0[0] - gm0[0] * m0[2] + gm1[2] * m1[0] -
+              gm1[0] * m1[2] + gcw[2] * c_w[0] - gcw[0] * c_w[2];
+    pose[5] = mu[0] * gWm[1] - mu[1] * gWm[0] + gm0[0] * m0[1] - gm0[1] * m0[0] + gm1[0] * m1[1] -
+              gm1[1] * m1[0] + gcw[0] * c_w[1] - gcw[1] * c_w[0];
+  }
+}
+
 // PARAMS: parameter gradients are wanted; without them (the pose gradient
 // alone, the map held fixed) their accumulation is left out at compile time.
 template <int DEG, bool BF16, bool PARAMS>
@@ -558,132 +697,12 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   auto view_bwd = [&](const int v, float pose[6]) {
     const int64_t e = (int64_t)v * n + g;
     float4* ad = ws.adjoints + 3 * e;
-    const float4 A0 = ad[0], A1 = ad[1], A2 = ad[2];
-    const float4 R0 = ws.records[3 * e], R1 = ws.records[3 * e + 1];
-    const float gmx = A0.x, gmy = A0.y, ga = A0.z, gb = A0.w, gc = A1.x, gop = A1.y, gdep = A1.z;
-    const float gcol[3] = {A2.x, A2.y, A2.z};
-    const Cam cam = load_cam(cams, v);
-    const float3 mh = to_camera(cam, mu[0], mu[1], mu[2]);
-    const float iz = 1.f / mh.z;
-    const float limx = cfg.fov_clamp * 0.5f * (float)ws.width / cam.fx;
-    const float limy = cfg.fov_clamp * 0.5f * (float)ws.height / cam.fy;
-    const float txr = mh.x * iz, tyr = mh.y * iz;
-    const bool clx = txr > limx || txr < -limx, cly = tyr > limy || tyr < -limy;
-    const float txc = fminf(limx, fmaxf(-limx, txr)), tyc = fminf(limy, fmaxf(-limy, tyr));
-    const float j00 = cam.fx * iz, j02 = -cam.fx * txc * iz, j11 = cam.fy * iz, j12 = -cam.fy * tyc * iz;
-    float m0[3], m1[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      m0[j] = cam.R[j] * j00 + cam.R[6 + j] * j02;
-      m1[j] = cam.R[3 + j] * j11 + cam.R[6 + j] * j12;
-    }
-    float U[3], Vv[3], rm0[3], rm1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      rm0[k] = Rg[0][k] * m0[0] + Rg[1][k] * m0[1] + Rg[2][k] * m0[2];
-      rm1[k] = Rg[0][k] * m1[0] + Rg[1][k] * m1[1] + Rg[2][k] * m1[2];
-      U[k] = s[k] * rm0[k];
-      Vv[k] = s[k] * rm1[k];
-    }
-    // conic = Q = Sigma'^-1 from the stored record (the values the forward used)
-    const float qa = R0.z, qb = R0.w, qc = R1.x;
-    // dL/dSigma' = -Q G Q with G = [[ga, gb/2], [gb/2, gc]]
-    const float hb = 0.5f * gb;
-    const float P00 = qa * ga + qb * hb, P01 = qa * hb + qb * gc, P10 = qb * ga + qc * hb, P11 = qb * hb + qc * gc;
-    const float gA = -(P00 * qa + P01 * qb);
-    const float gBh = -(P00 * qb + P01 * qc);  // d/dSigma'_01 (one of the two symmetric entries)
-    const float gCc = -(P10 * qb + P11 * qc);
-    const float gB = 2.f * gBh;
-    // A = U.U + dil, B = U.V, C = V.V + dil
-    float gU[3], gV[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      gU[k] = 2.f * gA * U[k] + gB * Vv[k];
-      gV[k] = gB * U[k] + 2.f * gCc * Vv[k];
-    }
-    float gm0[3] = {0.f, 0.f, 0.f}, gm1[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (PARAMS) g_s[k] += gU[k] * rm0[k] + gV[k] * rm1[k];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        if (PARAMS) g_R[i][k] += s[k] * (gU[k] * m0[i] + gV[k] * m1[i]);
-        gm0[i] += s[k] * gU[k] * Rg[i][k];
-        gm1[i] += s[k] * gV[k] * Rg[i][k];
-      }
-    }
-    // m0 = R^T J0, m1 = R^T J1  ->  dL/dJ0 = R gm0, dL/dJ1 = R gm1
-    float gJ0[3], gJ1[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      gJ0[i] = cam.R[3 * i] * gm0[0] + cam.R[3 * i + 1] * gm0[1] + cam.R[3 * i + 2] * gm0[2];
-      gJ1[i] = cam.R[3 * i] * gm1[0] + cam.R[3 * i + 1] * gm1[1] + cam.R[3 * i + 2] * gm1[2];
-    }
-    const float iz2 = iz * iz;
-    float gx = gmx * cam.fx * iz, gy = gmy * cam.fy * iz;
-    float gz = gdep - gmx * cam.fx * mh.x * iz2 - gmy * cam.fy * mh.y * iz2;
-    gz += -gJ0[0] * cam.fx * iz2 - gJ1[1] * cam.fy * iz2;
-    // J02 = -fx txc / z: unclamped txc = x/z, clamped txc constant
-    gz += gJ0[2] * cam.fx * txc * iz2 * (clx ? 1.f : 2.f);
-    if (!clx) gx += -gJ0[2] * cam.fx * iz2;
-    gz += gJ1[2] * cam.fy * tyc * iz2 * (cly ? 1.f : 2.f);
-    if (!cly) gy += -gJ1[2] * cam.fy * iz2;
-    // dL/dmu through mu_hat = R mu + t
-    float gWm[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) gWm[j] = cam.R[j] * gx + cam.R[3 + j] * gy + cam.R[6 + j] * gz;
-    // colour: raw = sum_k SH_k Y_k(dir) + 0.5, clamped at 0
-    const float3 cw = camera_centre(cam);
-    float dv[3] = {mu[0] - cw.x, mu[1] - cw.y, mu[2] - cw.z};
-    const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-    const float dx = dv[0] * inv, dy = dv[1] * inv, dz = dv[2] * inv;
-    float Y[16];
-    sh_basis<DEG>(dx, dy, dz, Y);
-    float graw[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float raw = 0.5f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) raw += s_sh[3 * k + ch][threadIdx.x] * Y[k];
-      graw[ch] = raw > 0.f ? gcol[ch] : 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (PARAMS) s_gsh[3 * k + ch][threadIdx.x] += graw[ch] * Y[k];
-    }
-    // d colour / d dir = sum_k (sum_ch graw_ch SH_k,ch) grad Y_k
-    float wk[16];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      wk[k] = 0.f;
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) wk[k] += graw[ch] * s_sh[3 * k + ch][threadIdx.x];
-    }
-    const float3 gd3 = sh_weighted_grad<DEG>(wk, dx, dy, dz);
-    const float gdir[3] = {gd3.x, gd3.y, gd3.z};
-    const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
-    const float gv[3] = {(gdir[0] - dx * dd) * inv, (gdir[1] - dy * dd) * inv, (gdir[2] - dz * dd) * inv};
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      if (PARAMS) g_mu[j] += gWm[j] + gv[j];
-    if (PARAMS) g_o += gop;
+    entry_chain<DEG, PARAMS>(
+        load_cam(cams, v), cfg, ws.width, ws.height, mu, s, Rg, ws.records[3 * e], ws.records[3 * e + 1], ad[0],
+        ad[1], ad[2], [&](int k, int ch) { return s_sh[3 * k + ch][threadIdx.x]; },
+        [&](int q, float val) { s_gsh[q][threadIdx.x] += val; }, g_mu, g_s, g_R, g_o, want_pose, pose);
     // consume: leave the adjoint area zero for the next backward of this projection
     ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (want_pose) {
-      // right perturbation T Exp(xi), xi = (rho, theta):
-      //   d mu_hat = R rho + R (theta x mu), d m = m x theta, d c_w = -rho + c_w x theta
-      const float gcw[3] = {-gv[0], -gv[1], -gv[2]};
-      pose[0] = gWm[0] - gcw[0];
-      pose[1] = gWm[1] - gcw[1];
-      pose[2] = gWm[2] - gcw[2];
-      // theta: mu x (R^T g_mu_hat) + gm0 x m0 + gm1 x m1 + g_cw x c_w
-      const float c_w[3] = {cw.x, cw.y, cw.z};
-      pose[3] = mu[1] * gWm[2] - mu[2] * gWm[1] + gm0[1] * m0[2] - gm0[2] * m0[1] + gm1[1] * m1[2] -
-                gm1[2] * m1[1] + gcw[1] * c_w[2] - gcw[2] * c_w[1];
-      pose[4] = mu[2] * gWm[0] - mu[0] * gWm[2] + gm0[2] * m0[0] - gm0[0] * m0[2] + gm1[2] * m1[0] -
-                gm1[0] * m1[2] + gcw[2] * c_w[0] - gcw[0] * c_w[2];
-      pose[5] = mu[0] * gWm[1] - mu[1] * gWm[0] + gm0[0] * m0[1] - gm0[1] * m0[0] + gm1[0] * m1[1] -
-                gm1[1] * m1[0] + gcw[0] * c_w[1] - gcw[1] * c_w[0];
-    }
   };
   // Views are taken 32 at a time.  Each lane collects the views in which its
   // Gaussian has a non-empty box.  When those sets are much alike across the
@@ -785,6 +804,102 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
   }
 }
 
+// Pose-only projection backward (the map held fixed, e.g. camera tracking):
+// one thread per visible (view, Gaussian) entry, in the binning's sorted
+// order, so that a view's entries come in one run and every thread has one
+// entry's work.  (A thread per Gaussian walks the views that see it, which
+// differ from lane to lane when the cameras sit inside the map.)  A CTA takes
+// a contiguous share of the entries.  A warp whose 32 entries share one view
+// reduces their pose terms with shuffles, else each lane adds its own.  The
+// CTA's sums of the first kPoseEntryViews views of its share are kept in
+// shared memory and added to grad_pose once; any later view of the share
+// gets global atomics.
+constexpr int kPoseEntryViews = 64;
+constexpr int kPoseEntryThreads = 256;
+
+template <int DEG, bool BF16>
+__global__ void __launch_bounds__(kPoseEntryThreads) k_pose_bwd_entries(gs_map map, const gs_camera* __restrict__ cams,
+                                                                      gs_config cfg, Ws ws, BwdArgs a) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  __shared__ float s_pose[6 * kPoseEntryViews];
+  if (ws.counters[kStatus] != 0) return;
+  const int64_t n = ws.n;
+  const uint32_t nvis = ws.counters[kVisibleCount];
+  const uint32_t per = ((nvis + gridDim.x - 1) / gridDim.x + kPoseEntryThreads - 1) / kPoseEntryThreads *
+                       kPoseEntryThreads;
+  const uint64_t i0 = (uint64_t)blockIdx.x * per;
+  if (i0 >= nvis) return;  // the whole CTA
+  const uint64_t i1 = min((uint64_t)nvis, i0 + per);
+  const int vlo = (int)(ws.visible[i0] / (uint64_t)n);
+  const bool want_pose = a.grad_pose != nullptr;
+  for (int i = threadIdx.x; i < 6 * kPoseEntryViews; i += kPoseEntryThreads) s_pose[i] = 0.f;
+  __syncthreads();
+  auto add_pose = [&](int v, int k, float val) {
+    if (val == 0.f) return;
+    if (v - vlo < kPoseEntryViews) atomicAdd(&s_pose[6 * (v - vlo) + k], val);
+    else atomicAdd(a.grad_pose + 6 * v + k, val);
+  };
+  for (uint64_t b = i0; b < i1; b += kPoseEntryThreads) {
+    const uint64_t i = b + threadIdx.x;
+    const bool act = i < i1;
+    const uint32_t e = ws.visible[act ? i : i0];
+    const int v = (int)(e / (uint64_t)n);
+    const int64_t g = (int64_t)e - (int64_t)v * n;
+    float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (act) {
+      const float mu[3] = {map.mean[g], map.mean[n + g], map.mean[2 * n + g]};
+      const float q[4] = {map.quat[g], map.quat[n + g], map.quat[2 * n + g], map.quat[3 * n + g]};
+      float s[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s[k] = expf(map.log_scale[k * n + g]);
+      const float qi = rsqrtf(fmaxf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3], 1e-30f));
+      float Rg[3][3];
+      quat_to_rot(q[0] * qi, q[1] * qi, q[2] * qi, q[3] * qi, Rg);
+      float sh[3 * K];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) sh[3 * k + ch] = sh_coeff<BF16>(map.sh_dc, map.sh_rest, n, g, k, ch);
+      float g_mu[3], g_s[3], g_R[3][3], g_o;  // parameter sums: not formed without PARAMS
+      float4* ad = ws.adjoints + 3 * (int64_t)e;
+      entry_chain<DEG, false>(
+          load_cam(cams, v), cfg, ws.width, ws.height, mu, s, Rg, ws.records[3 * (int64_t)e],
+          ws.records[3 * (int64_t)e + 1], ad[0], ad[1], ad[2], [&](int k, int ch) { return sh[3 * k + ch]; },
+          [](int, float) {}, g_mu, g_s, g_R, g_o, want_pose, pose);
+      // consume: leave the adjoint area zero for the next backward of this projection
+      ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (!want_pose) continue;
+    const int v0 = __shfl_sync(kFull, v, 0);
+    if (__all_sync(kFull, !act || v == v0)) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pose[k] += __shfl_xor_sync(kFull, pose[k], off);
+      }
+      if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) add_pose(v0, k, pose[k]);
+    } else if (act) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) add_pose(v, k, pose[k]);
+    }
+  }
+  __syncthreads();
+  if (!want_pose) return;
+  for (int i = threadIdx.x; i < 6 * kPoseEntryViews; i += kPoseEntryThreads)
+    if (s_pose[i] != 0.f) atomicAdd(a.grad_pose + 6 * vlo + i, s_pose[i]);
+}
+
+template <int DEG, bool BF16>
+static cudaError_t launch_pose_bwd_entries(const gs_map& map, const gs_camera* cams, const gs_config& cfg,
+                                           const Ws& ws, const BwdArgs& a, cudaStream_t st) {
+  trace_begin(kKPreprocessBwd, st);
+  k_pose_bwd_entries<DEG, BF16><<<(unsigned)sm_count() * 8, kPoseEntryThreads, 0, st>>>(map, cams, cfg, ws, a);
+  trace_end(st);
+  return cudaGetLastError();
+}
+
 template <int DEG, bool BF16, bool PARAMS>
 static cudaError_t launch_pre_bwd_t(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                     const BwdArgs& a, cudaStream_t st) {
@@ -804,7 +919,7 @@ template <int DEG, bool BF16>
 static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                                   const BwdArgs& a, cudaStream_t st) {
   return a.grad_mean ? launch_pre_bwd_t<DEG, BF16, true>(map, cams, cfg, ws, a, st)
-                     : launch_pre_bwd_t<DEG, BF16, false>(map, cams, cfg, ws, a, st);
+                     : launch_pose_bwd_entries<DEG, BF16>(map, cams, cfg, ws, a, st);
 }
 
 cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st) {

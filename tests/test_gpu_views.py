@@ -29,3 +29,28 @@ def test_forty_views_in_one_batch_match_two_batches_of_twenty():
             assert float((a - b).abs().max()) <= IMG_TOL
     # the scene is seen: some pixels of every view are covered
     assert bool((full.opac.flatten(1).amax(1) > 0.1).all())
+
+
+@pytest.mark.parametrize("n", [3000, 24])
+def test_pose_only_backward_over_many_small_views(n):
+    """The pose-only backward runs one thread per sorted visible entry, each CTA
+    over a contiguous share of them.  With 300 small views the batch has more
+    views than the full backward keeps in shared memory, and with a map of 24
+    Gaussians a share of 256 entries spans many views, past the ones it sums
+    in shared memory.  The pose gradient of the pose-only backward equals that
+    of the full one, view by view."""
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
+    V, H, W = 300, 24, 32
+    w = synth.mapping(n=n, width=W, height=H, focal=20.0, n_views=V, sh_degree=1)
+    gm = GaussianMap.from_host(w.gmap)
+    cams = cameras_tensor(w.cams)
+    rast = Rasterizer(gm.n, V, W, H)
+    out = rast.render(gm, cams)
+    tgt = torch.as_tensor(w.tgt_rgb, device="cuda")
+    full = rast.backward(gm, cams, out, tgt_rgb=tgt, w_rgb=1.0)
+    pose_only = rast.backward(gm, cams, out, tgt_rgb=tgt, w_rgb=1.0, params=False)
+    assert rast.status()[0] == 0
+    a, b = pose_only.pose.double(), full.pose.double()
+    assert int((b.abs().amax(1) > 0).sum()) > V // 10  # views that see something
+    scale = b.abs().amax(1, keepdim=True).clamp_min(1e-30)
+    assert float(((a - b).abs() / scale).max()) <= 1e-4
