@@ -373,9 +373,29 @@ __device__ __forceinline__ Ellipse make_ellipse(float4 r0, float4 r1) {
   return e;
 }
 
+// Pixel-centre columns [xl, xr] inside the ellipse on two pixel rows, whose
+// centres are yc.x and yc.y (y + 0.5), clamped to the image; ok[k] is false
+// if row k holds none.  The arithmetic runs on packed FP32 pairs, each half
+// rounded exactly as row_tiles rounds it, so both take the same decisions.
+// Written without branches so that the lanes of a warp stay converged across
+// the 16 rows of a tile row.
+__device__ __forceinline__ void row_px2(const Ellipse& e, float2 yc, float wm1, float2* xl, float2* xr, bool ok[2]) {
+  const float2 dy = __fadd2_rn(yc, make_float2(-e.my, -e.my));
+  const float2 disc = __ffma2_rn(__fmul2_rn(make_float2(-e.det, -e.det), dy), dy, make_float2(e.aq, e.aq));
+  const float2 dpos = make_float2(fmaxf(disc.x, 1e-30f), fmaxf(disc.y, 1e-30f));
+  const float2 half = __fmul2_rn(__fmul2_rn(dpos, make_float2(rsqrtf(dpos.x), rsqrtf(dpos.y))),
+                                 make_float2(e.inv_a, e.inv_a));
+  const float2 cm = __ffma2_rn(make_float2(-e.b_a, -e.b_a), dy, make_float2(e.mxm, e.mxm));
+  const float2 a = __fadd2_rn(cm, make_float2(-half.x, -half.y)), b = __fadd2_rn(cm, half);
+  const float l0 = ceilf(a.x), l1 = ceilf(a.y), r0 = floorf(b.x), r1 = floorf(b.y);
+  *xl = make_float2(fminf(fmaxf(l0, 0.f), wm1), fminf(fmaxf(l1, 0.f), wm1));
+  *xr = make_float2(fminf(fmaxf(r0, 0.f), wm1), fminf(fmaxf(r1, 0.f), wm1));
+  ok[0] = (disc.x >= 0.f) & (l0 <= r0) & (r0 >= 0.f) & (l0 <= wm1);
+  ok[1] = (disc.y >= 0.f) & (l1 <= r1) & (r1 >= 0.f) & (l1 <= wm1);
+}
+
 // Tile-column range [*tl, *tr] of pixel centres inside the ellipse on pixel
-// row y; false if the row holds none.  Written without branches so that the
-// lanes of a warp stay converged across the 16 rows of a tile row.
+// row y; false if the row holds none (the per-tile test of tile_kept()).
 __device__ __forceinline__ bool row_tiles(const Ellipse& e, int y, int width, int* tl, int* tr) {
   const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), e.my);
   const float disc = __fmaf_rn(-__fmul_rn(e.det, dy), dy, e.aq);
@@ -392,8 +412,11 @@ __device__ __forceinline__ bool row_tiles(const Ellipse& e, int y, int width, in
 }
 
 // Kept tiles of tile row ty: the columns [lo, hi] hull the 16 chords' tile
-// ranges; when the chords' ranges are disjoint (gap, rare: very thin tilted
-// ellipses) only the tiles that tile_kept() confirms belong to the set.
+// ranges.  The hull is kept in pixels; gap is set when a chord lies more
+// than 16 pixels beyond the hull of the rows before it, the only way the
+// chords' tile ranges can leave a tile between them (rare: very thin tilted
+// ellipses).  A span with gap set is conservative: only the tiles that
+// tile_kept() confirms belong to the set.
 struct RowSpan {
   int lo, hi;
   bool gap;
@@ -401,14 +424,28 @@ struct RowSpan {
 
 __device__ __forceinline__ RowSpan row_span(const Ellipse& e, int ty, int width, int height) {
   const int y0 = ty * kTile, y1 = min(height - 1, y0 + kTile - 1);
-  RowSpan s{1 << 30, -1, false};
-#pragma unroll 4
-  for (int y = y0; y <= y1; ++y) {
-    int tl, tr;
-    const bool ok = row_tiles(e, y, width, &tl, &tr);
-    s.gap |= ok & (s.hi >= 0) & ((tl > s.hi + 1) | (tr < s.lo - 1));
-    s.lo = ok ? min(s.lo, tl) : s.lo;
-    s.hi = ok ? max(s.hi, tr) : s.hi;
+  const float wm1 = (float)(width - 1);
+  float lo = 3.0e38f, hi = -1.f;  // hull of the rows' clamped pixel ranges
+  bool gap = false;
+  const float yc = (float)y0 + 0.5f;  // row centre, exact for any image row
+#pragma unroll
+  for (int r = 0; r < kTile; r += 2) {
+    float2 xl, xr;
+    bool ok[2];
+    row_px2(e, make_float2(yc + (float)r, yc + (float)(r + 1)), wm1, &xl, &xr, ok);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float l = k ? xl.y : xl.x, rr = k ? xr.y : xr.x;
+      const bool o = ok[k] & (y0 + r + k <= y1);
+      gap |= o & (hi >= 0.f) & ((l > hi + 16.f) | (rr < lo - 16.f));
+      lo = o ? fminf(lo, l) : lo;
+      hi = o ? fmaxf(hi, rr) : hi;
+    }
+  }
+  RowSpan s{1 << 30, -1, gap};
+  if (hi >= 0.f) {
+    s.lo = (int)lo >> 4;
+    s.hi = (int)hi >> 4;
   }
   return s;
 }
