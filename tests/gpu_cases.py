@@ -50,12 +50,13 @@ def gpu_tile_pairs(rast, view):
     return tiles, ids[pos]
 
 
-def compare_tiles(oracle, m, cam, rast, view, label=None):
+def compare_tiles(oracle, m, cam, rast, view, label=None, cfg=None):
     """Bit-exact tile lists / order outside the oracle's threshold margin:
     every pair the oracle marks as within 1e-4 (relative, in q) of the
     culling threshold is left out on both sides, everything else must match
-    in content and order.  Returns the number of margin pairs seen."""
-    ot, og, om = oracle.tiles(m, cam)
+    in content and order.  Returns the number of margin pairs seen.  cfg: the
+    rasterizer constants both sides use (the oracle's defaults when None)."""
+    ot, og, om = oracle.tiles(m, cam, cfg=cfg)
     gt, gg = gpu_tile_pairs(rast, view)
     n = np.int64(max(int(m["logit_opacity"].shape[0]), 1))
     code = lambda t, g: t.astype(np.int64) * n + g.astype(np.int64)

@@ -14,8 +14,8 @@ import pytest
 import torch
 
 from paper_2507_04004_b300 import synth
-from tests.gpu_cases import (GRAD_TOL, IMG_TOL, assert_grads_close, compare_tiles, gpu_render, grads_to_numpy,
-                             host_map, rel_err)
+from tests.gpu_cases import (GRAD_TOL, IMG_TOL, assert_grads_close, compare_tiles, gpu_render, gpu_tile_pairs,
+                             grads_to_numpy, host_map, rel_err, report)
 from tests.oracle_cases import logit, one_gaussian_map
 
 pytestmark = pytest.mark.gpu
@@ -158,6 +158,53 @@ def test_offscreen_gaussians_reaching_into_the_image(oracle):
     assert np.isin(np.nonzero(outside)[0], og).sum() > 300  # many off-screen centres do reach in
     for view, cam in enumerate(cams):
         compare_tiles(oracle, m, cam, rast, view, label=f"off-screen centres view {view}")
+
+
+def test_needle_ellipses_with_tile_gaps(oracle):
+    """Needle-thin Gaussians (no dilation, minor scales e^-9) lying within a few
+    degrees of the image rows: a chord on one pixel row and the next can then
+    lie whole tiles apart, so a tile row's kept tiles are not contiguous and
+    the culling confirms each tile of such a row item on its own.  The tiles
+    between the chords, which the hull of a tile row's chords would keep, must
+    be left out.  With a singular conic FP32 cannot reproduce FP64's decisions
+    at every pixel-centre border, so the lists are compared up to a small
+    fraction of pairs (with the default dilation the same scene's lists are
+    equal)."""
+    rng = np.random.default_rng(91)
+    W, H, f, n = 320, 96, 150.0, 3000
+    g = synth.random_map(rng, n, (-1.0, -0.3, 3.0), (1.0, 0.3, 6.0), 1)
+    g.log_scale[0] = np.log(rng.uniform(0.4, 1.5, n)).astype(np.float32)
+    g.log_scale[1:] = -9.0
+    th = rng.uniform(0.004, 0.06, n) * rng.choice([-1.0, 1.0], n)
+    g.quat[:] = np.stack([np.cos(th / 2), np.zeros(n), np.zeros(n), np.sin(th / 2)]).astype(np.float32)
+    g.logit_opacity[:] = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    cams = [synth.camera(np.eye(3), np.zeros(3), f, f, W / 2, H / 2, W, H)]
+    m = host_map(g)
+    cfg = dict(oracle.DEFAULT_CONFIG, dilation=0.0)
+    ot, og, om = oracle.tiles(m, cams[0], cfg=cfg)
+    tx = (W + 15) // 16
+    rows = {}
+    for t, gi in zip(ot.tolist(), og.tolist()):
+        rows.setdefault((gi, t // tx), set()).add(t % tx)
+    # tiles inside a row item's hull that no chord reaches (by the oracle)
+    between = {(ty * tx + c) * n + gi for (gi, ty), cols in rows.items()
+               for c in range(min(cols), max(cols) + 1) if c not in cols}
+    assert len(between) > 1000
+    rast, gm, ct, out = gpu_render(g, cams, config=dict(dilation=0.0))
+    assert rast.status()[0] == 0
+    gt, gg = gpu_tile_pairs(rast, 0)
+    got = set((gt.astype(np.int64) * n + gg).tolist())
+    want = set((ot.astype(np.int64) * n + og).tolist())
+    margin = set((ot[om != 0].astype(np.int64) * n + og[om != 0]).tolist())
+    in_between = len(got & between)
+    differ = len((got ^ want) - margin)
+    report(f"needle ellipses, no dilation: {len(between)} tiles between chords, {in_between} of them in the GPU's "
+           f"lists; {differ} of {len(want)} pairs differ from the FP64 lists")
+    assert in_between <= len(between) // 100
+    assert differ <= len(want) // 100
+    # with the default dilation the same needles' lists are bit-exact
+    rast2, _, _, _ = gpu_render(g, cams)
+    compare_tiles(oracle, m, cams[0], rast2, 0, label="needle ellipses, default dilation")
 
 
 @pytest.mark.parametrize("sh_bf16,degenerate", [(False, 0.0), (True, 0.01)])
