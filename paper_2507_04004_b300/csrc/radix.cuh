@@ -100,6 +100,9 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixScratch rs, D
   constexpr int NW = kRadixThreads / 32;
   __shared__ uint32_t s_wcnt[NW][256];  // per warp: count of each digit, then its first slot in the tile
   __shared__ uint32_t s_base[256];      // first output slot of each digit's run of this tile
+  __shared__ uint32_t s_local[256];     // first slot of each digit's run inside the tile
+  __shared__ uint32_t s_wsum[NW];
+  __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];  // the tile in digit order
   __shared__ uint32_t s_ticket;
   if (*rs.status != 0) return;
   const uint64_t n = *rs.n;
@@ -175,6 +178,17 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixScratch rs, D
       }
       // first slot of the digit: all entries of lower digits, then earlier tiles
       s_base[dd] = excl;
+      // the digit's first slot inside the tile: exclusive scan of the tile's counts
+      const uint32_t inc = warp_incl_scan(run, lane);
+      if (lane == 31) s_wsum[warp] = inc;
+      s_local[dd] = inc - run;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t add = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) add += w < warp ? s_wsum[w] : 0u;
+      s_local[threadIdx.x] += add;
     }
     __syncthreads();
     // exclusive scan of the pass's digit counts (one warp), added to s_base
@@ -187,17 +201,27 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_pass(RadixScratch rs, D
       for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] += run; run += c8[q]; }
     }
     __syncthreads();
+    // the tile in digit order in shared memory, then written out in that
+    // order: consecutive threads write consecutive slots of a digit's run
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-      const uint64_t i = base + 32 * j + lane;
-      if (i >= n) continue;
-      const uint64_t pos = (uint64_t)s_base[d[j]] + s_wcnt[warp][d[j]] + r[j];
+      if (base + 32 * j + lane >= n) continue;
+      const uint32_t lp = s_local[d[j]] + s_wcnt[warp][d[j]] + r[j];
+      s_key[lp] = k[j];
+      s_val[lp] = v[j];
+    }
+    __syncthreads();
+    const uint32_t cnt = (uint32_t)min((uint64_t)kSortTile, n - (uint64_t)t * kSortTile);
+    for (uint32_t i = threadIdx.x; i < cnt; i += kRadixThreads) {
+      const uint32_t kk = s_key[i], vv = s_val[i];
+      const uint32_t dd = dg(kk, vv, pass);
+      const uint64_t pos = (uint64_t)s_base[dd] + (i - s_local[dd]);
       if (pos < n) {
-        key_out[pos] = k[j];
-        val_out[pos] = v[j];
+        key_out[pos] = kk;
+        val_out[pos] = vv;
       }
     }
-    __syncthreads();  // s_wcnt and s_base are reused by the next tile
+    __syncthreads();  // shared arrays are reused by the next tile
   }
 }
 

@@ -56,7 +56,7 @@ def compare_tiles(oracle, m, cam, rast, view, label=None, cfg=None):
     culling threshold is left out on both sides, everything else must match
     in content and order.  Returns the number of margin pairs seen.  cfg: the
     rasterizer constants both sides use (the oracle's defaults when None)."""
-    ot, og, om = oracle.tiles(m, cam, cfg=cfg)
+    ot, og, om = oracle.tiles(m, cam) if cfg is None else oracle.tiles(m, cam, cfg=cfg)
     gt, gg = gpu_tile_pairs(rast, view)
     n = np.int64(max(int(m["logit_opacity"].shape[0]), 1))
     code = lambda t, g: t.astype(np.int64) * n + g.astype(np.int64)
