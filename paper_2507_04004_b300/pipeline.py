@@ -119,8 +119,10 @@ class MappingStep:
 
     def upload(self, kf: HostKeyframes) -> dict:
         """Queue the copy of one batch (pinned host tensors, kept alive by the
-        caller until the batch's step has run) and its unpacking on the copy
-        stream."""
+        caller until the batch's step has run) on the copy stream.  The batch
+        is unpacked by its step, on the compute stream: run on the copy stream,
+        the unpacking's CTAs would share the SMs with the step's kernels and
+        delay them by more than the unpacking takes on its own."""
         V, H, W = self.rast.views, self.rast.height, self.rast.width
         m = kf.depth_idx.numel()
         if tuple(kf.rgb8.shape) != (V, 3, H, W) or kf.depth_offsets.numel() != V + 1 or m > V * H * W:
@@ -135,13 +137,14 @@ class MappingStep:
             slot["val"][:m].copy_(kf.depth_val, non_blocking=True)
             slot["offsets"].copy_(kf.depth_offsets, non_blocking=True)
             slot["cams"].copy_(kf.cams, non_blocking=True)
-            N.gs_unpack_keyframes(slot["rgb8"], V, H, W, slot["rgb"], slot["idx"], slot["val"], slot["offsets"],
-                                  slot["depth"], cs.cuda_stream)
             slot["ready"].record(cs)
         self.h2d_bytes = kf.nbytes()
         return slot
 
     def _work(self, slot: dict) -> None:
+        V, H, W = self.rast.views, self.rast.height, self.rast.width
+        N.gs_unpack_keyframes(slot["rgb8"], V, H, W, slot["rgb"], slot["idx"], slot["val"], slot["offsets"],
+                              slot["depth"], torch.cuda.current_stream(self.rast.device).cuda_stream)
         g = self.grads
         g.zero_()
         self.rast.render(self.gmap, slot["cams"], check=False, out=self.out)

@@ -46,6 +46,23 @@ def test_unpack_is_exact(V, H, W):
     np.testing.assert_array_equal(dep, depth)
 
 
+def test_unpack_misaligned_buffers():
+    """Buffers off the 16-byte boundary take the byte-at-a-time path, with the
+    same values."""
+    rng = np.random.default_rng(8)
+    V, H, W = 2, 37, 53
+    rgb8 = rng.integers(0, 256, (V, 3, H, W), dtype=np.uint8)
+    n = rgb8.size
+    src = torch.zeros(n + 1, dtype=torch.uint8, device="cuda")
+    src[1:] = torch.as_tensor(rgb8.reshape(-1), device="cuda")
+    out = torch.full((n + 1,), -1.0, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    N.gs_unpack_keyframes(src[1:], V, H, W, out[1:], None, None, None, None, st)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out[1:].cpu().numpy(), rgb8.reshape(-1).astype(np.float32) / np.float32(255.0))
+    assert float(out[0]) == -1.0
+
+
 def test_unpack_without_depth_points_and_colour_only():
     rng = np.random.default_rng(3)
     rgb8 = rng.integers(0, 256, (2, 3, 9, 11), dtype=np.uint8)
