@@ -6,8 +6,8 @@ on their own stream, so the upload of the next batch overlaps the kernels of
 the current one.  A keyframe travels in the form a sensor delivers it: the
 camera image as 8-bit RGB, the LiDAR depth map as its valid pixels only
 ((pixel index, depth) pairs, a few percent of the image); ``gs_unpack_keyframes``
-expands both on the device, on the copy stream, into the FP32 planes the loss
-reads.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
+expands both on the device into the FP32 planes the loss reads, as the first
+work of the batch's step on the compute stream.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
 (projection, binning/sort, compositing, fused loss backward) over a batch of
 keyframes and returns the per-view loss as a pinned host tensor; its device
 work is replayed from one CUDA graph per upload slot (captured on first use),
