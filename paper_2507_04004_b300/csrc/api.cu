@@ -73,6 +73,9 @@ Ws resolve_ws(const gs_workspace* w, const gs_layout& L) {
   ws.vis_key = u32(L.vis_key);
   ws.sort_key = u32(L.sort_key);
   ws.sort_val = u32(L.sort_val);
+  // the sort's last pass writes the entry buffer (passes - 1) & 1, which
+  // k_entry_order reads: the other one holds the sorted list from then on
+  ws.sorted = ws.sort_val + (size_t)(depth_sort_passes(w->frame.n_views) & 1) * (size_t)w->frame.n_views * (size_t)w->n;
   ws.radix_status = u32(L.radix_status);
   ws.view_start = u32(L.view_start);
   ws.gauss_list = u32(L.gauss_list);

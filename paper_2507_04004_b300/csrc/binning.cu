@@ -173,7 +173,9 @@ struct DepthDigit {
 
 
 // Runs of equal (view, depth key) put in Gaussian-index order, the sorted
-// entries written to ws.visible; first sorted entry of every view.
+// entries written to ws.sorted; first sorted entry of every view.  (The
+// projection-order list in ws.visible is kept: the pose-only backward walks
+// it.)
 __global__ void __launch_bounds__(256) k_entry_order(Ws ws, const uint32_t* __restrict__ key,
                                                      const uint32_t* __restrict__ val) {
   if (ws.counters[kStatus] != 0) return;
@@ -190,14 +192,14 @@ __global__ void __launch_bounds__(256) k_entry_order(Ws ws, const uint32_t* __re
     auto same = [&](uint64_t j) { return key[j] == k && val[j] / N == v; };
     const bool prev = i > 0 && same(i - 1), next = i + 1 < n && same(i + 1);
     if (!prev && !next) {
-      ws.visible[i] = e;
+      ws.sorted[i] = e;
     } else {
       uint64_t s = i, t = i + 1;
       while (s > 0 && same(s - 1)) --s;
       while (t < n && same(t)) ++t;
       uint32_t rank = 0;
       for (uint64_t j = s; j < t; ++j) rank += val[j] < e ? 1u : 0u;
-      ws.visible[s + rank] = e;
+      ws.sorted[s + rank] = e;
     }
     const int64_t vp = i > 0 ? (int64_t)(val[i - 1] / N) : -1;
     for (int64_t u = vp + 1; u <= (int64_t)v; ++u) ws.view_start[u] = (uint32_t)i;
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_entry_rows(Ws ws) {
     for (int t = lane; t <= ny; t += 32) cnt[t] = 0;
     __syncwarp();
     for (uint32_t i = i0 + lane; i < i1; i += 32) {
-      const uint2 r = ws.rects[ws.visible[i]];
+      const uint2 r = ws.rects[ws.sorted[i]];
       atomicAdd(cnt + (r.x >> 16), 1u);
       atomicSub(cnt + (r.y >> 16) + 1, 1u);
     }
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
     uint32_t ne = 0;  // next round's entry and box, loaded ahead
     uint2 nr = make_uint2(1u, 0u);
     if (i0 + lane < i1) {
-      ne = ws.visible[i0 + lane];
+      ne = ws.sorted[i0 + lane];
       nr = ws.rects[ne];
     }
     for (uint32_t r0 = i0; r0 < i1; r0 += 32) {
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_scatter(Ws ws) {
       const uint32_t y0 = nr.x >> 16;
       const uint32_t c = r0 + lane < i1 ? (nr.y >> 16) - y0 + 1 : 0u;
       if (r0 + 32 + lane < i1) {
-        ne = ws.visible[r0 + 32 + lane];
+        ne = ws.sorted[r0 + 32 + lane];
         nr = ws.rects[ne];
       }
       warp_stable_scatter(
@@ -519,7 +521,7 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
 
   // 1. entries sorted by (view, depth key), then index inside equal keys
   const int64_t E = (int64_t)ws.views * ws.n;
-  const int passes = 4 + (ws.views > 1 ? (ws.views > 256 ? 2 : 1) : 0);
+  const int passes = depth_sort_passes(ws.views);
   // the sort's host view of its scratch (device pointers and the entry count's slot)
   RadixScratch rs;
   rs.n = ws.counters + kVisibleCount;

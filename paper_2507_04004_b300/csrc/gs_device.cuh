@@ -24,16 +24,22 @@ constexpr int kWorkClasses = 64;  // classes of the blend backward's work list
 static_assert(kWorkClasses % 32 == 0, "work classes are scanned 32 at a time");
 constexpr int kBwdBatch = 128;  // Gaussians staged in shared memory per batch by the backward blend
 
+// Passes of the binning's LSD radix sort of the visible entries: four on the
+// 32-bit depth key, then one or two on the view (none for a single view).
+__host__ __device__ inline int depth_sort_passes(int views) { return 4 + (views > 1 ? (views > 256 ? 2 : 1) : 0); }
+
 // Device view of the workspace parts (pointers resolved from gs_layout).
 struct Ws {
   uint32_t* counters;     // see CounterSlot
   float4* records;        // [V*N][3]
   uint2* rects;           // [V*N]
   float4* adjoints;       // [V*N][3]
-  uint32_t* visible;      // [V*N] visible entries v*N + g: projection order, then (view, depth key, index) order
+  uint32_t* visible;      // [V*N] visible entries v*N + g, projection order
   uint32_t* vis_key;      // [V*N] depth key bits of each visible entry, projection order
   uint32_t* sort_key;     // [2][V*N] radix-sort buffers (keys)
   uint32_t* sort_val;     // [2][V*N] radix-sort buffers (entries)
+  uint32_t* sorted;       // [V*N] visible entries in (view, depth key, index) order: the entry buffer of
+                          // sort_val the sort's last pass leaves free (depth_sort_passes)
   uint32_t* radix_status; // [6][256] digit counts of the sort's passes, then [6][radix_tiles_max][256] tile status
   uint32_t* view_start;   // [V + 1] first sorted visible entry of each view
   uint32_t* gauss_list;   // [N] Gaussians visible in at least one view

@@ -805,23 +805,24 @@ __global__ void __launch_bounds__(256, 2) k_preprocess_bwd(gs_map map, const gs_
 }
 
 // Pose-only projection backward (the map held fixed, e.g. camera tracking):
-// one thread per visible (view, Gaussian) entry, in the binning's sorted
-// order, so that a view's entries come in one run and every thread has one
-// entry's work.  (A thread per Gaussian walks the views that see it, which
-// differ from lane to lane when the cameras sit inside the map.)  A CTA takes
-// a contiguous share of the entries.  A warp whose 32 entries share one view
-// reduces their pose terms with shuffles, else each lane adds its own.  The
-// CTA's sums of the first kPoseEntryViews views of its share are kept in
-// shared memory and added to grad_pose once; any later view of the share
-// gets global atomics.
-constexpr int kPoseEntryViews = 64;
+// one thread per visible (view, Gaussian) entry, in the projection's order of
+// the entries (ws.visible).  That order holds, per warp of the projection, the
+// entries of 32 consecutive Gaussians view by view, so neighbouring threads
+// gather the parameters, records and adjoints of neighbouring Gaussians, and
+// every thread has one entry's work.  (A thread per Gaussian walks the views
+// that see it, which differ from lane to lane when the cameras sit inside the
+// map; the depth-sorted order scatters the gathers.)  A warp sums its
+// entries' pose terms over each run of one view with a segmented shuffle
+// reduction; the run's first lane adds the sums to the CTA's per-view sums in
+// shared memory (to grad_pose directly beyond kPoseSmemViews views), which
+// are added to grad_pose once per CTA.
 constexpr int kPoseEntryThreads = 256;
 
 template <int DEG, bool BF16>
 __global__ void __launch_bounds__(kPoseEntryThreads) k_pose_bwd_entries(gs_map map, const gs_camera* __restrict__ cams,
                                                                       gs_config cfg, Ws ws, BwdArgs a) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  __shared__ float s_pose[6 * kPoseEntryViews];
+  __shared__ float s_pose[6 * kPoseSmemViews];
   if (ws.counters[kStatus] != 0) return;
   const int64_t n = ws.n;
   const uint32_t nvis = ws.counters[kVisibleCount];
@@ -830,15 +831,12 @@ __global__ void __launch_bounds__(kPoseEntryThreads) k_pose_bwd_entries(gs_map m
   const uint64_t i0 = (uint64_t)blockIdx.x * per;
   if (i0 >= nvis) return;  // the whole CTA
   const uint64_t i1 = min((uint64_t)nvis, i0 + per);
-  const int vlo = (int)(ws.visible[i0] / (uint64_t)n);
   const bool want_pose = a.grad_pose != nullptr;
-  for (int i = threadIdx.x; i < 6 * kPoseEntryViews; i += kPoseEntryThreads) s_pose[i] = 0.f;
+  const bool pose_smem = ws.views <= kPoseSmemViews;
+  if (pose_smem)
+    for (int i = threadIdx.x; i < 6 * ws.views; i += kPoseEntryThreads) s_pose[i] = 0.f;
   __syncthreads();
-  auto add_pose = [&](int v, int k, float val) {
-    if (val == 0.f) return;
-    if (v - vlo < kPoseEntryViews) atomicAdd(&s_pose[6 * (v - vlo) + k], val);
-    else atomicAdd(a.grad_pose + 6 * v + k, val);
-  };
+  const int lane = threadIdx.x & 31;
   for (uint64_t b = i0; b < i1; b += kPoseEntryThreads) {
     const uint64_t i = b + threadIdx.x;
     const bool act = i < i1;
@@ -870,32 +868,35 @@ __global__ void __launch_bounds__(kPoseEntryThreads) k_pose_bwd_entries(gs_map m
       ad[0] = ad[1] = ad[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (!want_pose) continue;
-    const int v0 = __shfl_sync(kFull, v, 0);
-    if (__all_sync(kFull, !act || v == v0)) {
+    // runs of one view among the warp's lanes: lane l's run ends at the first
+    // lane j >= l whose next lane holds another view (or j = 31)
+    const int vn = __shfl_down_sync(kFull, v, 1);
+    const unsigned ends = __ballot_sync(kFull, lane == 31 || vn != v);
+    const int last = __ffs(ends & ~((1u << lane) - 1u)) - 1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) pose[k] += __shfl_xor_sync(kFull, pose[k], off);
+        const float y = __shfl_down_sync(kFull, pose[k], d);
+        if (lane + d <= last) pose[k] += y;
       }
-      if ((threadIdx.x & 31) == 0)
+    const bool head = lane == 0 || ((ends >> (lane - 1)) & 1u);
+    if (head)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) add_pose(v0, k, pose[k]);
-    } else if (act) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) add_pose(v, k, pose[k]);
-    }
+      for (int k = 0; k < 6; ++k)
+        if (pose[k] != 0.f) atomicAdd((pose_smem ? s_pose : a.grad_pose) + 6 * v + k, pose[k]);
   }
   __syncthreads();
-  if (!want_pose) return;
-  for (int i = threadIdx.x; i < 6 * kPoseEntryViews; i += kPoseEntryThreads)
-    if (s_pose[i] != 0.f) atomicAdd(a.grad_pose + 6 * vlo + i, s_pose[i]);
+  if (!want_pose || !pose_smem) return;
+  for (int i = threadIdx.x; i < 6 * ws.views; i += kPoseEntryThreads)
+    if (s_pose[i] != 0.f) atomicAdd(a.grad_pose + i, s_pose[i]);
 }
 
 template <int DEG, bool BF16>
 static cudaError_t launch_pose_bwd_entries(const gs_map& map, const gs_camera* cams, const gs_config& cfg,
                                            const Ws& ws, const BwdArgs& a, cudaStream_t st) {
   trace_begin(kKPreprocessBwd, st);
-  k_pose_bwd_entries<DEG, BF16><<<(unsigned)sm_count() * 8, kPoseEntryThreads, 0, st>>>(map, cams, cfg, ws, a);
+  k_pose_bwd_entries<DEG, BF16><<<(unsigned)sm_count() * 4, kPoseEntryThreads, 0, st>>>(map, cams, cfg, ws, a);
   trace_end(st);
   return cudaGetLastError();
 }
