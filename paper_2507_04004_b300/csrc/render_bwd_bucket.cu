@@ -205,8 +205,13 @@ __global__ void __launch_bounds__(32 * kBkWarps, 6) k_render_bwd_bucket(gs_confi
     float q0 = 0.f, q2 = 0.f;
     float2 Tst = f2(0.f), Ast = f2(0.f);
     const uint32_t steps = m + 31u;
-    for (uint32_t s = 0; s < steps; ++s) {
-      if ((s & 31u) == 0) {
+    // steps in unrolled groups of eight: a chunk of 32 starts only at the first of a group
+    for (uint32_t s0 = 0; s0 < steps; s0 += 8) {
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u) {
+      const uint32_t s = s0 + u;
+      if (s >= steps) break;
+      if (u == 0 && (s & 31u) == 0) {
         const int buf = (int)((s >> 5) & 1u);
         cp_async_wait_all();  // this lane's copies of the chunk (issued 32 steps ago)
         __syncwarp();
@@ -278,6 +283,7 @@ __global__ void __launch_bounds__(32 * kBkWarps, 6) k_render_bwd_bucket(gs_confi
         Tst = T;
         Ast = A;
       }
+    }
     }
     if (g_ok) {
       // the same 2D adjoints as the pixel-parallel kernel's flush
