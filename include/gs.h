@@ -227,6 +227,21 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
                         float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out,
                         gs_stream_t stream);
 
+/* gs_render_bwd with the fused loss's colour targets given as the camera's
+ * 8-bit images: tgt_rgb8 [V][3][H][W] uint8 (device; required), target value
+ * c / 255 correctly rounded, which is exactly what gs_unpack_keyframes writes,
+ * so the gradients and loss are those of gs_render_bwd on the unpacked planes.
+ * The loss reads 3 bytes per pixel instead of 12, and no FP32 colour plane is
+ * written first.  Every other argument, the work and the errors are
+ * gs_render_bwd's. */
+gs_status gs_render_bwd_rgb8(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                             const gs_workspace* ws, const float* rgb, const float* depth, const float* opac,
+                             const float* t_final, const uint32_t* n_contrib, const uint8_t* tgt_rgb8,
+                             const float* tgt_depth, float w_rgb, float w_depth, const float* dl_drgb,
+                             const float* dl_ddepth, const float* dl_dopac, float* grad_mean, float* grad_log_scale,
+                             float* grad_quat, float* grad_logit_opacity, float* grad_sh_dc, float* grad_sh_rest,
+                             float* grad_pose, float* loss_out, gs_stream_t stream);
+
 /* Per-Gaussian backward (Sec. "Per-Gaussian Backpropagation"), an
  * alternative to the pixel-parallel blend backward inside gs_render_bwd with
  * the same results: the depth-sorted Gaussians of each tile are cut into
@@ -353,7 +368,10 @@ gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_par
  * if depth_idx is given, depth [V][H][W] is cleared and, for view v, the
  * entries depth_offsets[v] .. depth_offsets[v + 1] - 1 of (depth_idx = pixel
  * y W + x, depth_val) are written (indices outside the image are skipped).
- * All pointers device; depth_* may be NULL (colour only). */
+ * All pointers device; depth_* may be NULL (colour only); rgb8 and rgb may
+ * both be NULL when depth is given (depth only: the caller's loss reads the
+ * 8-bit colour itself, as gs_render_bwd_rgb8 does).  GS_ERR_ARG when only one
+ * of rgb8 / rgb is given or there is nothing to unpack. */
 gs_status gs_unpack_keyframes(const uint8_t* rgb8_dev, int32_t n_views, int32_t height, int32_t width,
                               float* rgb_dev, const int32_t* depth_idx_dev, const float* depth_val_dev,
                               const int32_t* depth_offsets_dev, float* depth_dev, gs_stream_t stream);

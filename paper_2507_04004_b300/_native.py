@@ -15,7 +15,7 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_
 GS_NOALLOC_SCRATCH_BYTES = 64 << 20  # size of gs_render_fwd_noalloc's device array
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
+            "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_render_bwd_rgb8", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
             "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
             "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
             "gs_expand_select", "gs_expand_init", "gs_morton_scratch_bytes", "gs_morton_order", "gs_permute_rows",
@@ -97,6 +97,7 @@ def lib():
         L.gs_blend_counts.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace), P, P]
         L.gs_render_bwd.argtypes = ([C.POINTER(gs_map), P, C.POINTER(gs_config), C.POINTER(gs_workspace)]
                                     + [P] * 7 + [F, F] + [P] * 3 + [P] * 8 + [P])
+        L.gs_render_bwd_rgb8.argtypes = L.gs_render_bwd.argtypes
         L.gs_bucket_workspace_size.argtypes = [C.POINTER(gs_workspace)]
         L.gs_bucket_workspace_size.restype = C.c_size_t
         L.gs_render_fwd_checkpointed.argtypes = [C.POINTER(gs_config), C.POINTER(gs_workspace)] + [P] * 7
@@ -137,6 +138,7 @@ def lib():
         L.gs_status_str.restype = C.c_char_p
         L.gs_version.restype = C.c_char_p
         for name in ("gs_read_status", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_blend_counts", "gs_render_bwd",
+                     "gs_render_bwd_rgb8",
                      "gs_render_fwd_checkpointed", "gs_render_bwd_buckets",
                      "gs_pose_jacobian", "gs_workspace_layout", "gs_dssim", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose",
                      "gs_sparse_adam", "gs_expand_select", "gs_expand_init", "gs_unpack_keyframes",
@@ -198,6 +200,16 @@ def gs_render_bwd(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth,
     check("gs_render_bwd", lib().gs_render_bwd(
         C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac), _ptr(t_final),
         _ptr(n_contrib), _ptr(tgt_rgb), _ptr(tgt_depth), C.c_float(w_rgb), C.c_float(w_depth), _ptr(dl_drgb),
+        _ptr(dl_ddepth), _ptr(dl_dopac), _ptr(grad_mean), _ptr(grad_log_scale), _ptr(grad_quat), _ptr(grad_logit),
+        _ptr(grad_sh_dc), _ptr(grad_sh_rest), _ptr(grad_pose), _ptr(loss), C.c_void_p(stream)))
+
+
+def gs_render_bwd_rgb8(m: gs_map, cams, cfg: gs_config, ws: gs_workspace, rgb, depth, opac, t_final, n_contrib,
+                       tgt_rgb8, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale,
+                       grad_quat, grad_logit, grad_sh_dc, grad_sh_rest, grad_pose, loss, stream: int) -> None:
+    check("gs_render_bwd_rgb8", lib().gs_render_bwd_rgb8(
+        C.byref(m), _ptr(cams), C.byref(cfg), C.byref(ws), _ptr(rgb), _ptr(depth), _ptr(opac), _ptr(t_final),
+        _ptr(n_contrib), _ptr(tgt_rgb8), _ptr(tgt_depth), C.c_float(w_rgb), C.c_float(w_depth), _ptr(dl_drgb),
         _ptr(dl_ddepth), _ptr(dl_dopac), _ptr(grad_mean), _ptr(grad_log_scale), _ptr(grad_quat), _ptr(grad_logit),
         _ptr(grad_sh_dc), _ptr(grad_sh_rest), _ptr(grad_pose), _ptr(loss), C.c_void_p(stream)))
 

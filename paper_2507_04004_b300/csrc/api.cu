@@ -239,7 +239,7 @@ static gs_status bwd_args(const gs_map* map, const gs_camera* cams_dev, const gs
                           float w_depth, const float* dl_drgb, const float* dl_ddepth, const float* dl_dopac,
                           float* grad_mean, float* grad_log_scale, float* grad_quat, float* grad_logit_opacity,
                           float* grad_sh_dc, float* grad_sh_rest, float* grad_pose, float* loss_out, gs_layout* L,
-                          BwdArgs* out) {
+                          BwdArgs* out, const uint8_t* tgt_rgb8 = nullptr) {
   gs_status s = check_ws(ws, L);
   if (s != GS_OK) return s;
   if ((s = check_map(map, ws)) != GS_OK) return s;
@@ -253,13 +253,14 @@ static gs_status bwd_args(const gs_map* map, const gs_camera* cams_dev, const gs
   } else if (!grad_pose) {
     return GS_ERR_ARG;
   }
-  if (tgt_rgb) {
+  if (tgt_rgb && tgt_rgb8) return GS_ERR_ARG;
+  if (tgt_rgb || tgt_rgb8) {
     if (!rgb) return GS_ERR_ARG;
     if (tgt_depth && w_depth != 0.f && (!depth || !opac)) return GS_ERR_ARG;
   }
   BwdArgs a;
   a.rgb = rgb; a.depth = depth; a.opac = opac; a.t_final = t_final; a.n_contrib = n_contrib;
-  a.tgt_rgb = tgt_rgb; a.tgt_depth = tgt_depth; a.w_rgb = w_rgb; a.w_depth = w_depth;
+  a.tgt_rgb = tgt_rgb; a.tgt_rgb8 = tgt_rgb8; a.tgt_depth = tgt_depth; a.w_rgb = w_rgb; a.w_depth = w_depth;
   a.dl_drgb = dl_drgb; a.dl_ddepth = dl_ddepth; a.dl_dopac = dl_dopac;
   a.grad_mean = grad_mean; a.grad_log_scale = grad_log_scale; a.grad_quat = grad_quat;
   a.grad_logit = grad_logit_opacity; a.grad_sh_dc = grad_sh_dc; a.grad_sh_rest = grad_sh_rest;
@@ -280,6 +281,24 @@ gs_status gs_render_bwd(const gs_map* map, const gs_camera* cams_dev, const gs_c
   const gs_status s = bwd_args(map, cams_dev, cfg, ws, rgb, depth, opac, t_final, n_contrib, tgt_rgb, tgt_depth,
                                w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale, grad_quat,
                                grad_logit_opacity, grad_sh_dc, grad_sh_rest, grad_pose, loss_out, &L, &a);
+  if (s != GS_OK) return s;
+  return cuda_status(launch_render_bwd(*map, cams_dev, *cfg, resolve_ws(ws, L), a,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_render_bwd_rgb8(const gs_map* map, const gs_camera* cams_dev, const gs_config* cfg,
+                             const gs_workspace* ws, const float* rgb, const float* depth, const float* opac,
+                             const float* t_final, const uint32_t* n_contrib, const uint8_t* tgt_rgb8,
+                             const float* tgt_depth, float w_rgb, float w_depth, const float* dl_drgb,
+                             const float* dl_ddepth, const float* dl_dopac, float* grad_mean, float* grad_log_scale,
+                             float* grad_quat, float* grad_logit_opacity, float* grad_sh_dc, float* grad_sh_rest,
+                             float* grad_pose, float* loss_out, gs_stream_t stream) {
+  if (!tgt_rgb8) return GS_ERR_ARG;
+  gs_layout L;
+  BwdArgs a;
+  const gs_status s = bwd_args(map, cams_dev, cfg, ws, rgb, depth, opac, t_final, n_contrib, nullptr, tgt_depth,
+                               w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, grad_mean, grad_log_scale, grad_quat,
+                               grad_logit_opacity, grad_sh_dc, grad_sh_rest, grad_pose, loss_out, &L, &a, tgt_rgb8);
   if (s != GS_OK) return s;
   return cuda_status(launch_render_bwd(*map, cams_dev, *cfg, resolve_ws(ws, L), a,
                                        reinterpret_cast<cudaStream_t>(stream)));
@@ -359,7 +378,8 @@ gs_status gs_sparse_adam(const gs_workspace* ws, int32_t sh_degree, const gs_par
 gs_status gs_unpack_keyframes(const uint8_t* rgb8_dev, int32_t n_views, int32_t height, int32_t width,
                               float* rgb_dev, const int32_t* depth_idx_dev, const float* depth_val_dev,
                               const int32_t* depth_offsets_dev, float* depth_dev, gs_stream_t stream) {
-  if (!rgb8_dev || !rgb_dev || n_views < 1 || height < 1 || width < 1) return GS_ERR_ARG;
+  if (!rgb8_dev != !rgb_dev || n_views < 1 || height < 1 || width < 1) return GS_ERR_ARG;
+  if (!rgb8_dev && !depth_dev) return GS_ERR_ARG;  // nothing to unpack
   if (depth_idx_dev && (!depth_val_dev || !depth_offsets_dev || !depth_dev)) return GS_ERR_ARG;
   return cuda_status(launch_unpack_keyframes(rgb8_dev, n_views, height, width, rgb_dev, depth_idx_dev, depth_val_dev,
                                              depth_offsets_dev, depth_dev, reinterpret_cast<cudaStream_t>(stream)));

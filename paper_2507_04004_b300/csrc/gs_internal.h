@@ -54,6 +54,8 @@ struct BwdArgs {
   const float *rgb, *depth, *opac, *t_final;
   const uint32_t* n_contrib;
   const float *tgt_rgb, *tgt_depth;
+  const uint8_t* tgt_rgb8;  // 8-bit colour targets (c / 255) in place of tgt_rgb, or null
+  bool fused() const { return tgt_rgb != nullptr || tgt_rgb8 != nullptr; }
   float w_rgb, w_depth;
   const float *dl_drgb, *dl_ddepth, *dl_dopac;
   float *grad_mean, *grad_log_scale, *grad_quat, *grad_logit, *grad_sh_dc, *grad_sh_rest, *grad_pose, *loss;

@@ -72,11 +72,22 @@ __device__ __forceinline__ void group8_reduce_scatter10(const float v[10], int s
   *y1 = (b0 ? 0.f : x[1]) + __shfl_xor_sync(kFull, b0 ? x[1] : 0.f, 1);
 }
 
+// A colour byte c as the target value c / 255, correctly rounded: the
+// reciprocal product q = c r (r = 1/255 rounded) with one residual
+// correction q + (c - 255 q) r by fused multiply-adds (Markstein's method).
+// For the 256 byte values this equals the IEEE quotient exactly (checked
+// against the host's division for every c), with no division in the kernel.
+__device__ __forceinline__ float byte_unit(uint8_t b) {
+  const float c = (float)b, r = 1.f / 255.f;
+  const float q = __fmul_rn(c, r);
+  return __fmaf_rn(__fmaf_rn(-q, 255.f, c), r, q);
+}
+
 // One (view, tile) item of the blend backward.  DEP: the pixel adjoints of
 // depth and opacity may be nonzero (a depth loss or the caller's depth /
 // opacity adjoints); without them (colour-only losses, e.g. tracking) they
 // and their terms are left out at compile time.
-template <bool FUSED, bool DEP, int PPT>
+template <bool FUSED, bool DEP, int PPT, bool U8>
 __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, const BwdArgs& a, const int64_t tile) {
   constexpr int NT = 256 / PPT;  // threads per tile
   constexpr int NW = NT / 32;    // warps per tile
@@ -127,12 +138,14 @@ __device__ __forceinline__ void bwd_tile(const gs_config& cfg, const Ws& ws, con
     T[k] = a.t_final[v * HW + p];
     last[k] = min(a.n_contrib[v * HW + p], cnt);  // never walk past the tile's list
     if (FUSED) {
+      // the colour target: FP32 planes, or (U8) the 8-bit images as c / 255
+      auto tgt = [&](int64_t i) { return U8 ? byte_unit(a.tgt_rgb8[i]) : a.tgt_rgb[i]; };
       const float inv3hw = a.w_rgb / (3.f * (float)HW);
-      float r = a.rgb[(3 * (int64_t)v + 0) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 0) * HW + p];
+      float r = a.rgb[(3 * (int64_t)v + 0) * HW + p] - tgt((3 * (int64_t)v + 0) * HW + p);
       gC0[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
-      r = a.rgb[(3 * (int64_t)v + 1) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 1) * HW + p];
+      r = a.rgb[(3 * (int64_t)v + 1) * HW + p] - tgt((3 * (int64_t)v + 1) * HW + p);
       gC1[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
-      r = a.rgb[(3 * (int64_t)v + 2) * HW + p] - a.tgt_rgb[(3 * (int64_t)v + 2) * HW + p];
+      r = a.rgb[(3 * (int64_t)v + 2) * HW + p] - tgt((3 * (int64_t)v + 2) * HW + p);
       gC2[k] = inv3hw * (float)((r > 0.f) - (r < 0.f)); loss += inv3hw * fabsf(r);
       if (DEP && a.tgt_depth && a.w_depth != 0.f) {
         const float ds = a.tgt_depth[v * HW + p];
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(kWorkThreads) k_tile_work(Ws ws, const uint32_
 // sequence of the classes' items, longest class first (the hardware starts
 // CTAs in index order); when the lists do not hold every item once (not
 // filled since the last binning), item b is tile b.
-template <bool FUSED, bool DEP, int PPT>
+template <bool FUSED, bool DEP, int PPT, bool U8>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 / (256 / PPT) / 2)
     k_render_bwd(gs_config cfg, Ws ws, BwdArgs a) {
   __shared__ uint32_t s_item;
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? (DEP ? 16 : 18) : 2048 /
     if (lane == 0) s_item = total == (uint32_t)items ? item : (uint32_t)blockIdx.x;
   }
   __syncthreads();
-  bwd_tile<FUSED, DEP, PPT>(cfg, ws, a, (int64_t)s_item);
+  bwd_tile<FUSED, DEP, PPT, U8>(cfg, ws, a, (int64_t)s_item);
 }
 
 // Chain of the 2D adjoints through the projection, per Gaussian over all
@@ -926,7 +939,7 @@ static cudaError_t launch_pre_bwd(const gs_map& map, const gs_camera* cams, cons
 cudaError_t launch_bwd_prologue(const Ws& ws, const BwdArgs& a, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(ws.view_stats, 0, (size_t)ws.views * 4 * sizeof(float), st);
   if (err != cudaSuccess) return err;
-  const bool fused = a.tgt_rgb != nullptr;
+  const bool fused = a.fused();
   const int64_t hw = (int64_t)ws.width * ws.height;
   if (fused && a.tgt_depth && a.w_depth != 0.f) {
     const int64_t nblk = (hw + 255) / 256;
@@ -952,17 +965,17 @@ cudaError_t launch_preprocess_bwd(const gs_map& map, const gs_camera* cams, cons
 
 // One CTA per work item; the hardware starts them in index order, which is
 // the work list's longest-first order.
-template <bool FUSED, bool DEP>
+template <bool FUSED, bool DEP, bool U8 = false>
 static cudaError_t launch_blend_bwd(const gs_config& cfg, const Ws& ws, const BwdArgs& a, int64_t items,
                                     cudaStream_t st) {
   if (items < 1) return cudaSuccess;
-  k_render_bwd<FUSED, DEP, kBwdPPT><<<(unsigned)items, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
+  k_render_bwd<FUSED, DEP, kBwdPPT, U8><<<(unsigned)items, 256 / kBwdPPT, 0, st>>>(cfg, ws, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs_config& cfg, const Ws& ws,
                               const BwdArgs& a, cudaStream_t st) {
-  const bool fused = a.tgt_rgb != nullptr;
+  const bool fused = a.fused();
   const int64_t items = (int64_t)ws.views * ws.tiles_per_view;
   const bool dep = (fused && a.tgt_depth && a.w_depth != 0.f) || a.dl_ddepth || a.dl_dopac;
   // per-view loss accumulators and valid-depth counts, then the work-list fill counts (adjacent in the layout)
@@ -977,7 +990,10 @@ cudaError_t launch_render_bwd(const gs_map& map, const gs_camera* cams, const gs
   trace_end(st);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   trace_begin(kKRenderBwd, st);
-  if (fused) {
+  if (fused && a.tgt_rgb8) {
+    if (dep) err = launch_blend_bwd<true, true, true>(cfg, ws, a, items, st);
+    else err = launch_blend_bwd<true, false, true>(cfg, ws, a, items, st);
+  } else if (fused) {
     if (dep) err = launch_blend_bwd<true, true>(cfg, ws, a, items, st);
     else err = launch_blend_bwd<true, false>(cfg, ws, a, items, st);
   } else {

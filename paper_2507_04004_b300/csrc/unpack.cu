@@ -49,10 +49,12 @@ cudaError_t launch_unpack_keyframes(const uint8_t* rgb8, int V, int H, int W, fl
   const int64_t hw = (int64_t)H * W;
   const int64_t n = (int64_t)V * 3 * hw;
   const unsigned grid = (unsigned)sm_count() * 8;
-  if (reinterpret_cast<uintptr_t>(rgb8) % 16 == 0 && reinterpret_cast<uintptr_t>(rgb) % 16 == 0)
-    k_unpack_rgb<true><<<grid, 256, 0, st>>>(rgb8, n, rgb);
-  else
-    k_unpack_rgb<false><<<grid, 256, 0, st>>>(rgb8, n, rgb);
+  if (rgb8) {  // colour planes (none when the loss reads the 8-bit images itself)
+    if (reinterpret_cast<uintptr_t>(rgb8) % 16 == 0 && reinterpret_cast<uintptr_t>(rgb) % 16 == 0)
+      k_unpack_rgb<true><<<grid, 256, 0, st>>>(rgb8, n, rgb);
+    else
+      k_unpack_rgb<false><<<grid, 256, 0, st>>>(rgb8, n, rgb);
+  }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess || !depth) return err;
   if ((err = cudaMemsetAsync(depth, 0, (size_t)V * hw * sizeof(float), st)) != cudaSuccess) return err;

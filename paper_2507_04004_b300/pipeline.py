@@ -5,9 +5,10 @@ depth maps live in pinned host memory and are moved with asynchronous copies
 on their own stream, so the upload of the next batch overlaps the kernels of
 the current one.  A keyframe travels in the form a sensor delivers it: the
 camera image as 8-bit RGB, the LiDAR depth map as its valid pixels only
-((pixel index, depth) pairs, a few percent of the image); ``gs_unpack_keyframes``
-expands both on the device into the FP32 planes the loss reads, as the first
-work of the batch's step on the compute stream.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
+((pixel index, depth) pairs, a few percent of the image).  The fused loss
+reads the 8-bit images as they arrived (``gs_render_bwd_rgb8``);
+``gs_unpack_keyframes`` expands the depth pairs into the FP32 depth map the
+loss reads, as the first work of the batch's step on the compute stream.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
 (projection, binning/sort, compositing, fused loss backward) over a batch of
 keyframes and returns the per-view loss as a pinned host tensor; its device
 work is replayed from one CUDA graph per upload slot (captured on first use),
@@ -106,7 +107,7 @@ class MappingStep:
                 idx=torch.empty(V * H * W, dtype=torch.int32, device=dev),
                 val=torch.empty(V * H * W, dtype=torch.float32, device=dev),
                 offsets=torch.empty(V + 1, dtype=torch.int32, device=dev),
-                rgb=torch.empty(V, 3, H, W, device=dev), depth=torch.empty(V, H, W, device=dev),
+                depth=torch.empty(V, H, W, device=dev),
                 cams=torch.empty(V, 16, device=dev), ready=torch.cuda.Event(), free=torch.cuda.Event()))
         f = dict(device=dev, dtype=torch.float32)
         self.out = RenderOut(torch.empty(V, 3, H, W, **f), torch.empty(V, H, W, **f), torch.empty(V, H, W, **f),
@@ -143,12 +144,13 @@ class MappingStep:
 
     def _work(self, slot: dict) -> None:
         V, H, W = self.rast.views, self.rast.height, self.rast.width
-        N.gs_unpack_keyframes(slot["rgb8"], V, H, W, slot["rgb"], slot["idx"], slot["val"], slot["offsets"],
-                              slot["depth"], torch.cuda.current_stream(self.rast.device).cuda_stream)
+        # the depth map only: the fused loss reads the 8-bit colour itself (gs_render_bwd_rgb8)
+        N.gs_unpack_keyframes(None, V, H, W, None, slot["idx"], slot["val"], slot["offsets"], slot["depth"],
+                              torch.cuda.current_stream(self.rast.device).cuda_stream)
         g = self.grads
         g.zero_()
         self.rast.render(self.gmap, slot["cams"], check=False, out=self.out)
-        self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=slot["rgb"], tgt_depth=slot["depth"],
+        self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=slot["rgb8"], tgt_depth=slot["depth"],
                            w_rgb=self.w_rgb, w_depth=self.w_depth, grads=g)
 
     def step(self, slot: dict) -> torch.Tensor:

@@ -278,7 +278,7 @@ class Rasterizer:
                  w_rgb: float = 1.0, w_depth: float = 0.0, dl_drgb=None, dl_ddepth=None, dl_dopac=None,
                  grads: Grads | None = None, pose: bool = True, params: bool = True) -> Grads:
         """Adds dL/dparams into ``grads`` (zeros when None) for the fused loss
-        (``tgt_rgb`` given; ``dl_*`` given as well add further loss terms) or
+        (``tgt_rgb`` given, FP32 or the 8-bit images; ``dl_*`` given as well add further loss terms) or
         the external pixel adjoints ``dl_*`` alone.  ``params=False``: the
         pose gradient (and loss) only, the map held fixed."""
         g = grads if grads is not None else self.new_grads(gmap)
@@ -287,7 +287,12 @@ class Rasterizer:
                 tgt_rgb, tgt_depth, w_rgb, w_depth, dl_drgb, dl_ddepth, dl_dopac, pg(g.mean), pg(g.log_scale),
                 pg(g.quat), pg(g.logit_opacity), pg(g.sh_dc), pg(g.sh_rest) if gmap.sh_degree > 0 else None,
                 g.pose if pose else None, g.loss)
-        if self.backward_mode == "bucket":
+        if tgt_rgb is not None and tgt_rgb.dtype == torch.uint8:
+            # 8-bit colour targets (c / 255) read by the fused loss itself
+            if self.backward_mode == "bucket":
+                raise ValueError("8-bit colour targets need the pixel-parallel backward")
+            N.gs_render_bwd_rgb8(*args, self._stream())
+        elif self.backward_mode == "bucket":
             N.gs_render_bwd_buckets(*args, self.bucket_ws, self._stream())
         else:
             N.gs_render_bwd(*args, self._stream())

@@ -20,7 +20,7 @@ def native():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "gs.h")).read()
-    return sorted(set(re.findall(r"\b(gs_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declarations_are_exported(native):

@@ -82,6 +82,52 @@ def test_unpack_rejects_bad_arguments():
         N.gs_unpack_keyframes(x, 1, 1, 1, f, torch.zeros(1, dtype=torch.int32, device="cuda"), None, None, None, 0)
 
 
+def test_unpack_depth_only():
+    """With no colour buffers the call writes the depth map alone (the loss then
+    reads the 8-bit colour itself); one colour buffer without the other is an
+    argument error."""
+    rng = np.random.default_rng(4)
+    V, H, W = 2, 13, 17
+    depth = np.where(rng.random((V, H, W)) < 0.1, rng.uniform(0.3, 9.0, (V, H, W)), 0.0).astype(np.float32)
+    idx, val, offs = pack_sparse_depth(depth)
+    d = lambda a: torch.as_tensor(a, device="cuda")
+    dep = torch.full((V, H, W), -1.0, device="cuda")
+    N.gs_unpack_keyframes(None, V, H, W, None, d(idx), d(val), d(offs), dep, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dep.cpu().numpy(), depth)
+    with pytest.raises(N.GsError):
+        N.gs_unpack_keyframes(torch.zeros(3, dtype=torch.uint8, device="cuda"), 1, 1, 1, None, d(idx), d(val),
+                              d(offs), dep, 0)
+
+
+def test_backward_with_8bit_colour_targets():
+    """gs_render_bwd_rgb8 reads the 8-bit images and takes c / 255 as the
+    target: its loss and gradients are those of gs_render_bwd on the same
+    targets as FP32 planes (up to the summation order of float atomics)."""
+    from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
+    w = synth.mapping(n=20_000, width=160, height=96, focal=90.0, n_views=2, sh_degree=2)
+    gm = GaussianMap.from_host(w.gmap)
+    V, H, W = 2, 96, 160
+    rast = Rasterizer(gm.n, V, W, H)
+    cams = cameras_tensor(w.cams)
+    out = rast.render(gm, cams)
+    tgt, depth = _batch(21, w)
+    tgt8 = torch.as_tensor(synth.to_uint8(tgt), device="cuda")
+    assert np.array_equal(tgt8.cpu().numpy().astype(np.float32) / np.float32(255.0), tgt)
+    kw = dict(tgt_depth=torch.as_tensor(depth, device="cuda"), w_rgb=w.w_rgb, w_depth=w.w_depth)
+    g32 = rast.backward(gm, cams, out, tgt_rgb=torch.as_tensor(tgt, device="cuda"), **kw)
+    g8 = rast.backward(gm, cams, out, tgt_rgb=tgt8, **kw)
+    assert rast.status()[0] == 0
+    np.testing.assert_allclose(g8.loss.cpu().numpy(), g32.loss.cpu().numpy(), rtol=1e-6)
+    for k in ("mean", "log_scale", "quat", "logit_opacity", "sh_dc", "sh_rest", "pose"):
+        a, b = getattr(g8, k).cpu().numpy(), getattr(g32, k).cpu().numpy()
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=k)
+    bucket = Rasterizer(gm.n, V, W, H, backward="bucket")
+    out_b = bucket.render(gm, cams)
+    with pytest.raises(ValueError):
+        bucket.backward(gm, cams, out_b, tgt_rgb=tgt8, **kw)
+
+
 def _batch(seed, w):
     rng = np.random.default_rng(seed)
     V, _, H, W = w.tgt_rgb.shape
