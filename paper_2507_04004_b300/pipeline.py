@@ -96,6 +96,9 @@ class MappingStep:
     def __init__(self, rast: Rasterizer, gmap: GaussianMap, w_rgb: float, w_depth: float, graphs: bool = True):
         self.rast, self.gmap, self.w_rgb, self.w_depth = rast, gmap, float(w_rgb), float(w_depth)
         self.graphs = bool(graphs)
+        # the pixel-parallel backward reads the 8-bit colour itself; the bucket
+        # backward takes the FP32 planes, which the step then unpacks as well
+        self.rgb8_loss = rast.backward_mode == "pixel"
         V, H, W = rast.views, rast.height, rast.width
         dev = rast.device
         self.copy_stream = torch.cuda.Stream(device=dev)
@@ -107,6 +110,7 @@ class MappingStep:
                 idx=torch.empty(V * H * W, dtype=torch.int32, device=dev),
                 val=torch.empty(V * H * W, dtype=torch.float32, device=dev),
                 offsets=torch.empty(V + 1, dtype=torch.int32, device=dev),
+                rgb=None if self.rgb8_loss else torch.empty(V, 3, H, W, device=dev),
                 depth=torch.empty(V, H, W, device=dev),
                 cams=torch.empty(V, 16, device=dev), ready=torch.cuda.Event(), free=torch.cuda.Event()))
         f = dict(device=dev, dtype=torch.float32)
@@ -144,13 +148,16 @@ class MappingStep:
 
     def _work(self, slot: dict) -> None:
         V, H, W = self.rast.views, self.rast.height, self.rast.width
-        # the depth map only: the fused loss reads the 8-bit colour itself (gs_render_bwd_rgb8)
-        N.gs_unpack_keyframes(None, V, H, W, None, slot["idx"], slot["val"], slot["offsets"], slot["depth"],
+        # the depth map (and the colour planes only for the bucket backward: the
+        # pixel-parallel one reads the 8-bit colour itself, gs_render_bwd_rgb8)
+        rgb8 = None if self.rgb8_loss else slot["rgb8"]
+        N.gs_unpack_keyframes(rgb8, V, H, W, slot["rgb"], slot["idx"], slot["val"], slot["offsets"], slot["depth"],
                               torch.cuda.current_stream(self.rast.device).cuda_stream)
         g = self.grads
         g.zero_()
         self.rast.render(self.gmap, slot["cams"], check=False, out=self.out)
-        self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=slot["rgb8"], tgt_depth=slot["depth"],
+        tgt = slot["rgb8"] if self.rgb8_loss else slot["rgb"]
+        self.rast.backward(self.gmap, slot["cams"], self.out, tgt_rgb=tgt, tgt_depth=slot["depth"],
                            w_rgb=self.w_rgb, w_depth=self.w_depth, grads=g)
 
     def step(self, slot: dict) -> torch.Tensor:

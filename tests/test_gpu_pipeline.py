@@ -136,15 +136,16 @@ def _batch(seed, w):
     return tgt, depth
 
 
-@pytest.mark.parametrize("graphs", [True, False])
-def test_mapping_step_matches_device_resident_pass(graphs):
+@pytest.mark.parametrize("graphs,backward", [(True, "pixel"), (False, "pixel"), (True, "bucket")])
+def test_mapping_step_matches_device_resident_pass(graphs, backward):
     """The host-fed step (eager, or replayed from a CUDA graph per upload
-    slot) gives the loss and gradients of the device-resident pass."""
+    slot; the pixel backward reading the 8-bit colour, the bucket backward the
+    unpacked planes) gives the loss and gradients of the device-resident pass."""
     from paper_2507_04004_b300.raster import GaussianMap, Rasterizer, cameras_tensor
     w = synth.mapping(n=20_000, width=160, height=96, focal=90.0, n_views=2, sh_degree=2)
     gm = GaussianMap.from_host(w.gmap)
     V, H, W = 2, 96, 160
-    rast = Rasterizer(gm.n, V, W, H)
+    rast = Rasterizer(gm.n, V, W, H, backward=backward)
     cams = cameras_tensor(w.cams)
     rast.project_and_sort(gm, cams, check=True)
     batches = [_batch(s, w) for s in (11, 12)]
