@@ -7,8 +7,9 @@
 // entries are sorted once, and everything after that is a stable scatter:
 //   1. stable LSD radix sort of the visible entries by (view, depth key) -
 //      four 8-bit passes on the key, one or two on the view, one kernel per
-//      pass - then runs of equal keys put in index order (k_radix_*,
-//      k_entry_order);
+//      pass, the digit counts taken beside the scan of the (view, tile row)
+//      buckets - then runs of equal keys put in index order
+//      (k_counts_and_buckets, k_radix_pass, k_entry_order);
 //   2. stable scatter of the sorted entries into (view, tile row) buckets,
 //      one "row item" per tile row of an entry's box (k_entry_rows,
 //      k_unit_scan, k_rows_scatter);
@@ -33,52 +34,58 @@ constexpr int kScanThreads = 1024;
 constexpr int kUnitWarps = 8;  // warps (units in flight) per CTA of the unit kernels
 
 
-// Exclusive scan of count(i), i < n, by one CTA of kScanThreads: start[i] =
+// Exclusive scan of count(i), i < n, by one CTA of NT threads: start[i] =
 // sum of counts before i; returns the 64-bit total (to every thread).  Each
-// warp owns a contiguous segment and walks it 32 counts at a time.
-template <typename F>
+// warp owns a contiguous segment and walks it kScanLoads x 32 counts at a
+// time (that many loads in flight per lane: one CTA's scan is bound by the
+// round trips of its loads).
+constexpr int kScanLoads = 8;
+template <int NT, typename F>
 __device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
-  constexpr int NW = kScanThreads / 32;
+  constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0 && NW <= 32, "one warp scans the warps' sums");
+  constexpr int L = kScanLoads;
   __shared__ unsigned long long wbase[NW + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t seg = (n + NW - 1) / NW;
   const int64_t b = min(n, (int64_t)warp * seg), e = min(n, b + seg);
   unsigned long long s = 0;
-  for (int64_t i0 = b; i0 < e; i0 += 128) {  // four loads in flight per lane
-    unsigned long long c[4];
+  for (int64_t i0 = b; i0 < e; i0 += 32 * L) {
+    unsigned long long c[L];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < L; ++j) {
       const int64_t i = i0 + 32 * j + lane;
       c[j] = i < e ? count(i) : 0u;
     }
-    s += c[0] + c[1] + c[2] + c[3];
+#pragma unroll
+    for (int j = 0; j < L; ++j) s += c[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   if (lane == 0) wbase[warp] = s;
   __syncthreads();
   if (warp == 0) {
-    const unsigned long long v = wbase[lane];  // NW == 32
+    const unsigned long long v = lane < NW ? wbase[lane] : 0ull;
     unsigned long long inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(kFull, inc, o);
       if (lane >= o) inc += y;
     }
-    wbase[lane] = inc - v;
+    if (lane < NW) wbase[lane] = inc - v;
     if (lane == 31) wbase[NW] = inc;
   }
   __syncthreads();
   unsigned long long run = wbase[warp];
-  for (int64_t i00 = b; i00 < e; i00 += 128) {  // four loads in flight per lane, then four scans
-    unsigned long long cc[4];
+  for (int64_t i00 = b; i00 < e; i00 += 32 * L) {  // L loads in flight per lane, then L scans
+    unsigned long long cc[L];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < L; ++j) {
       const int64_t i = i00 + 32 * j + lane;
       cc[j] = i < e ? count(i) : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < L; ++j) {
       const int64_t i = i00 + 32 * j + lane;
       const unsigned long long c = cc[j];
       unsigned long long inc = c;
@@ -101,13 +108,15 @@ __device__ unsigned long long block_scan(F count, uint32_t* start, int64_t n) {
 
 // Units of n_seg segments of cnt(s) items (unit_count / unit_start): first[s]
 // = first unit of segment s (first[n_seg] = total), seg[u] = segment of unit
-// u, *total_out = total.  One CTA; more than max_units units (not expected:
-// the workspace is sized for the capacities checked before) flag an error.
-template <typename F>
+// u, *total_out = total.  One CTA of NT threads; more than max_units units
+// (not expected: the workspace is sized for the capacities checked before)
+// flag an error.  Each warp writes the unit lists of 32 segments at a time,
+// 32 consecutive units per store.
+template <int NT, typename F>
 __device__ void build_units(F cnt, int64_t n_seg, int unit_cap, int64_t max_units, uint32_t* first, uint32_t* seg,
                             uint32_t* total_out, uint32_t* status) {
   auto nu = [&](int64_t s) { return unit_count(cnt(s), unit_cap); };
-  const unsigned long long total = block_scan(nu, first, n_seg);
+  const unsigned long long total = block_scan<NT>(nu, first, n_seg);
   if (threadIdx.x == 0) {
     first[n_seg] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     *total_out = total > (unsigned long long)max_units ? 0u : (uint32_t)total;
@@ -115,36 +124,58 @@ __device__ void build_units(F cnt, int64_t n_seg, int unit_cap, int64_t max_unit
   }
   __syncthreads();
   if (total > (unsigned long long)max_units) return;
-  for (int64_t s = threadIdx.x; s < n_seg; s += blockDim.x) {
-    const uint32_t f = first[s], k = nu(s);
-    for (uint32_t j = 0; j < k; ++j) seg[f + j] = (uint32_t)s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t s0 = (int64_t)warp * 32; s0 < n_seg; s0 += NT) {
+    uint32_t f = 0, k = 0;  // lane l: first unit and unit count of segment s0 + l
+    if (s0 + lane < n_seg) {
+      f = first[s0 + lane];
+      k = nu(s0 + lane);
+    }
+    const int nq = (int)min((int64_t)32, n_seg - s0);
+    for (int q = 0; q < nq; ++q) {
+      const uint32_t fq = __shfl_sync(kFull, f, q), kq = __shfl_sync(kFull, k, q);
+      for (uint32_t j = lane; j < kq; j += 32) seg[fq + j] = (uint32_t)(s0 + q);
+    }
   }
 }
 
 // ---------------------------------------------------------------- buckets
-// Bucket (view, tile row) ranges of the row items, capacity check, row units.
-__global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
+// Bucket (view, tile row) ranges of the row items, capacity check, row units:
+// one CTA of NT threads.
+template <int NT>
+__device__ void scan_buckets(const Ws& ws) {
   // The projection leaves each view's row-item counts as differences over the
   // tile rows (+1 at an entry's first row, -1 after its last, modulo 2^32):
-  // a running sum per view, one warp per view, turns them into counts.
+  // a running sum per view, one warp per view, turns them into counts (up to
+  // 8 x 32 rows loaded at once).
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int v = warp; v < ws.views; v += kScanThreads / 32) {
-      uint32_t* c = ws.bucket_count + (int64_t)v * ws.tiles_y;
+    const int ny = ws.tiles_y;
+    for (int v = warp; v < ws.views; v += NT / 32) {
+      uint32_t* c = ws.bucket_count + (int64_t)v * ny;
       uint32_t carry = 0;
-      for (int t0 = 0; t0 < ws.tiles_y; t0 += 32) {
-        const int ty = t0 + lane;
-        uint32_t x = warp_incl_scan(ty < ws.tiles_y ? c[ty] : 0u, lane) + carry;
-        if (ty < ws.tiles_y) c[ty] = x;
-        carry = __shfl_sync(kFull, x, 31);
+      for (int t00 = 0; t00 < ny; t00 += 8 * 32) {
+        uint32_t x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int ty = t00 + 32 * q + lane;
+          x[q] = ty < ny ? c[ty] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (t00 + 32 * q >= ny) break;
+          const int ty = t00 + 32 * q + lane;
+          const uint32_t inc = warp_incl_scan(x[q], lane) + carry;
+          if (ty < ny) c[ty] = inc;
+          carry = __shfl_sync(kFull, inc, 31);
+        }
       }
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < 6 * 256; i += kScanThreads) ws.radix_status[i] = 0;  // the sort's digit counts
   const int64_t nb = (int64_t)ws.views * ws.tiles_y;
   const uint32_t* bc = ws.bucket_count;
-  const unsigned long long total = block_scan([&](int64_t i) { return bc[i]; }, ws.bucket_start, nb);
+  const unsigned long long total = block_scan<NT>([&](int64_t i) { return bc[i]; }, ws.bucket_start, nb);
   if (threadIdx.x == 0) {
     ws.counters[kRowCount] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     if (total > (unsigned long long)ws.cap) {
@@ -153,8 +184,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_buckets(Ws ws) {
     }
   }
   if (total > (unsigned long long)ws.cap) return;
-  build_units([&](int64_t s) { return bc[s]; }, nb, kRowUnit, ws.units_r_max, ws.unit_first_r, ws.unit_seg_r,
-              ws.counters + kRowUnits, ws.counters + kStatus);
+  build_units<NT>([&](int64_t s) { return bc[s]; }, nb, kRowUnit, ws.units_r_max, ws.unit_first_r, ws.unit_seg_r,
+                  ws.counters + kRowUnits, ws.counters + kStatus);
 }
 
 // ---------------------------------------------------------------- entry sort
@@ -169,6 +200,20 @@ struct DepthDigit {
     return (pass == 4 ? v : v >> 8) & 255u;
   }
 };
+
+// The depth sort's digit counts (all CTAs but the last) beside the bucket
+// scan (the last CTA).  The two are independent, so the single-CTA scan runs
+// next to the counting instead of as a launch of its own before it.  A
+// capacity error the scan raises meanwhile leaves the counts harmless: the
+// sort's passes and everything after them check the status word first.
+__global__ void __launch_bounds__(kRadixThreads) k_counts_and_buckets(Ws ws, RadixScratch rs, DepthDigit dg,
+                                                                      int passes) {
+  if (blockIdx.x + 1 == gridDim.x) {
+    scan_buckets<kRadixThreads>(ws);
+    return;
+  }
+  radix_counts(rs, dg, passes, ws.vis_key, ws.visible, blockIdx.x, gridDim.x - 1);
+}
 
 
 
@@ -211,8 +256,8 @@ __global__ void __launch_bounds__(256) k_entry_order(Ws ws, const uint32_t* __re
 __global__ void __launch_bounds__(kScanThreads) k_entry_units(Ws ws) {
   if (ws.counters[kStatus] != 0) return;
   const uint32_t* vs = ws.view_start;
-  build_units([&](int64_t s) { return vs[s + 1] - vs[s]; }, ws.views, kEntryUnit, ws.units_e_max, ws.unit_first_e,
-              ws.unit_seg_e, ws.counters + kEntryUnits, ws.counters + kStatus);
+  build_units<kScanThreads>([&](int64_t s) { return vs[s + 1] - vs[s]; }, ws.views, kEntryUnit, ws.units_e_max,
+                            ws.unit_first_e, ws.unit_seg_e, ws.counters + kEntryUnits, ws.counters + kStatus);
 }
 
 // ---------------------------------------------------------------- stable scatters
@@ -445,7 +490,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Ws ws) {
   if (ws.counters[kStatus] != 0) return;
   const uint32_t* tc = ws.tile_count;
   const unsigned long long total =
-      block_scan([&](int64_t i) { return tc[i]; }, ws.tile_start, (int64_t)ws.views * ws.tiles_per_view);
+      block_scan<kScanThreads>([&](int64_t i) { return tc[i]; }, ws.tile_start, (int64_t)ws.views * ws.tiles_per_view);
   if (threadIdx.x == 0) {
     ws.counters[kPairsNeeded] = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     if (total > (unsigned long long)ws.cap) ws.counters[kStatus] = (uint32_t)GS_ERR_CAPACITY;
@@ -515,9 +560,6 @@ __global__ void __launch_bounds__(32 * kUnitWarps) k_rows_emit(Ws ws) {
 cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   cudaError_t err;
   auto done = [&](void) { trace_end(st); return cudaGetLastError(); };
-  trace_begin(kKScanBuckets, st);
-  k_scan_buckets<<<1, kScanThreads, 0, st>>>(ws);
-  if ((err = done()) != cudaSuccess) return err;
 
   // 1. entries sorted by (view, depth key), then index inside equal keys
   const int64_t E = (int64_t)ws.views * ws.n;
@@ -531,8 +573,10 @@ cudaError_t launch_bin_sort(const Ws& ws, cudaStream_t st) {
   rs.tickets = ws.counters + kRadixTicket;
   rs.tiles_max = ws.radix_tiles_max;
   const DepthDigit dg{(uint32_t)ws.n};
+  // digit counts from zero; with them the bucket ranges and row units
+  if ((err = cudaMemsetAsync(ws.radix_status, 0, 6 * 256 * sizeof(uint32_t), st)) != cudaSuccess) return err;
   trace_begin(kKDepthHist, st);
-  k_radix_counts<<<sm_count() * 4, kRadixThreads, 0, st>>>(rs, dg, passes, ws.vis_key, ws.visible);
+  k_counts_and_buckets<<<sm_count() * 4 + 1, kRadixThreads, 0, st>>>(ws, rs, dg, passes);
   if ((err = done()) != cudaSuccess) return err;
   const uint32_t* key = ws.vis_key;
   const uint32_t* val = ws.visible;

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256, 3) k_project(gs_map map, const gs_camera*
           float4* adj = ws.adjoints + 3 * e;
           adj[0] = adj[1] = adj[2] = make_float4(0.f, 0.f, 0.f, 0.f);
           // the entry's tile rows ty0..ty1 counted as a difference, +1 at ty0
-          // and -1 after ty1 (k_scan_buckets sums them per view): two atomics
+          // and -1 after ty1 (the bucket scan sums them per view): two atomics
           // however many rows the box spans
           uint32_t* bc = (smem_buckets ? s_bucket : ws.bucket_count) + v * ws.tiles_y;
           atomicAdd(bc + ty0, 1u);

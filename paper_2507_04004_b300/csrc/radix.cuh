@@ -61,17 +61,18 @@ struct RadixScratch {
   int64_t tiles_max;
 };
 
-// Digit counts of every pass over all items; clears the tile status words
-// the passes will use.
+// Digit counts of every pass over all items (added to the zeroed counts);
+// clears the tile status words the passes will use.  Work of CTA `cta` of
+// `ncta` CTAs of kRadixThreads threads.
 template <class Digit>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_counts(RadixScratch rs, Digit dg, int passes,
-                                                                const uint32_t* __restrict__ key,
-                                                                const uint32_t* __restrict__ val) {
+__device__ __forceinline__ void radix_counts(const RadixScratch& rs, Digit dg, int passes,
+                                             const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
+                                             uint32_t cta, uint32_t ncta) {
   __shared__ uint32_t h[6][256];
   if (*rs.status != 0) return;
   const uint64_t n = *rs.n;
   const uint64_t ntiles = (n + kSortTile - 1) / kSortTile;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)cta * kRadixThreads + threadIdx.x, stride = (uint64_t)ncta * kRadixThreads;
   for (int p = 0; p < passes; ++p) {
     uint32_t* st = rs.tiles + (int64_t)p * rs.tiles_max * 256;
     for (uint64_t i = tid; i < ntiles * 256; i += stride) st[i] = 0;
@@ -88,6 +89,13 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_counts(RadixScratch rs,
     const uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(g + i, c);
   }
+}
+
+template <class Digit>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_counts(RadixScratch rs, Digit dg, int passes,
+                                                                const uint32_t* __restrict__ key,
+                                                                const uint32_t* __restrict__ val) {
+  radix_counts(rs, dg, passes, key, val, blockIdx.x, gridDim.x);
 }
 
 // One LSD pass: stable scatter of the items by the pass's digit.
