@@ -15,13 +15,12 @@ GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_
 GS_NOALLOC_SCRATCH_BYTES = 64 << 20  # size of gs_render_fwd_noalloc's device array
 
 EXPORTED = ("gs_workspace_size", "gs_workspace_layout", "gs_read_status", "gs_project", "gs_bin_sort",
-            "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_render_bwd_rgb8", "gs_bucket_workspace_size", "gs_render_fwd_checkpointed",
-            "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc", "gs_dssim_scratch_bytes",
-            "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual", "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes",
-            "gs_expand_select", "gs_expand_init", "gs_morton_scratch_bytes", "gs_morton_order", "gs_permute_rows",
-            "gs_sort_wait_probe_bytes", "gs_sort_wait_probe", "gs_trace_start",
-            "gs_trace_stop",
-            "gs_kernel_name", "gs_status_str", "gs_version")
+            "gs_render_fwd", "gs_blend_counts", "gs_render_bwd", "gs_render_bwd_rgb8", "gs_bucket_workspace_size",
+            "gs_render_fwd_checkpointed", "gs_render_bwd_buckets", "gs_pose_jacobian", "gs_render_fwd_noalloc",
+            "gs_dssim_scratch_bytes", "gs_dssim", "gs_unpack_keyframes", "gs_pose_apply", "gs_pose_residual",
+            "gs_adam_pose", "gs_sparse_adam", "gs_expand_scratch_bytes", "gs_expand_select", "gs_expand_init",
+            "gs_morton_scratch_bytes", "gs_morton_order", "gs_permute_rows", "gs_sort_wait_probe_bytes",
+            "gs_sort_wait_probe", "gs_trace_start", "gs_trace_stop", "gs_kernel_name", "gs_status_str", "gs_version")
 
 
 class gs_camera(C.Structure):
