@@ -106,7 +106,7 @@ class Dist:
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons."""
+    """nvidia-smi sampling (every 50 ms) of SM clocks and throttle reasons."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -116,7 +116,7 @@ class ClockSampler:
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -144,7 +144,7 @@ class ClockSampler:
             except ValueError:
                 continue
             allr.append(rec)
-            if t0 - 0.25 <= rec["ts"] <= t1 + 0.25:
+            if t0 - 0.05 <= rec["ts"] <= t1 + 0.05:
                 inside.append(rec)
         use = inside if inside else allr
         if not use:
