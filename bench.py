@@ -271,8 +271,9 @@ def run_reference(args):
 def run_e2e(args, d, rast, gm, w, px_step):
     """Same metric through the public API from host buffers: every step
     uploads its keyframes (8-bit images, LiDAR depth pairs, cameras) from
-    pinned memory on a copy stream (double-buffered), unpacks them there, and
-    reads the loss back."""
+    pinned memory on a copy stream (double-buffered), expands the depth pairs
+    as the first work of its graph on the compute stream, and reads the loss
+    back."""
     import torch
 
     from paper_2507_04004_b300 import synth

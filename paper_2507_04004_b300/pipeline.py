@@ -8,7 +8,8 @@ camera image as 8-bit RGB, the LiDAR depth map as its valid pixels only
 ((pixel index, depth) pairs, a few percent of the image).  The fused loss
 reads the 8-bit images as they arrived (``gs_render_bwd_rgb8``);
 ``gs_unpack_keyframes`` expands the depth pairs into the FP32 depth map the
-loss reads, as the first work of the batch's step on the compute stream.  Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
+loss reads, as the first work of the batch's step on the compute stream.
+Each :meth:`MappingStep.step` runs one fwd+bwd pass of the rasterizer
 (projection, binning/sort, compositing, fused loss backward) over a batch of
 keyframes and returns the per-view loss as a pinned host tensor; its device
 work is replayed from one CUDA graph per upload slot (captured on first use),
